@@ -1,0 +1,381 @@
+#!/usr/bin/env python3
+"""Benchmark: IRKGL16 trajectory-steps/s on the batched Kepler ensemble.
+
+Workload (one benchmark step): 65,536 planar Kepler orbits, a = 1,
+e ~ U[0, 0.9) from the seed, periapsis start, m = round(200 + 100 e) steps per
+period, h = 2 pi/m, 100 periods each (about 1.61e9 trajectory-steps), one
+persistent launch of the batched kernel.  Inputs are resident in HBM when
+the timed region starts; L2 is flushed (256 MiB write) before every timed
+step.  `value` counts the steps of orbits whose max |dH/H| stays <= 1e-13
+(the metric's accuracy qualifier); `value_all` counts every orbit.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun each rank integrates its own 65,536-orbit ensemble (seeded by
+rank; weak scaling, no collective on the data path); the max over ranks of
+the timed region is used.  `--impl reference` times the oracle (plain C FP64
+CPU implementation) on the host cores on a bounded sample of the workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "IRKGL16 trajectory-steps/s at |ΔH/H|≤1e-13 vs plain GPU form; p50/p99 latency"
+TOL = 1e-13
+
+# Algorithmic FP64 floating-point operations (an FMA counts 2) per unit for
+# the Kepler right-hand side, d = 2 (derivation in DESIGN.md, "Roofline"):
+#   per completed step:  init 304 + compensated update 90 + energy monitor 19
+#   per fixed-point sweep (8 stages): g and R 120 + mixing 288 + Delta 16
+FLOPS_PER_STEP = 413
+FLOPS_PER_SWEEP = 424
+
+# DRAM traffic of the batched kernel from the committed ncu capture, valid only
+# for the kernel source it was taken on (sha256 prefix of irkgl_device.cuh).
+NCU_TRAFFIC_BYTES_PER_LAUNCH = None
+NCU_KERNEL_SHA = None
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--batch", type=int, default=65536)
+    ap.add_argument("--periods", type=int, default=100)
+    ap.add_argument("--lanes", type=int, default=0, help="lanes per trajectory (0 = library default)")
+    ap.add_argument("--no-order", action="store_true", help="natural order instead of similarity order")
+    ap.add_argument("--skip-extras", action="store_true", help="skip e2e, plain form and CPU baseline")
+    return ap.parse_args()
+
+
+def kernel_sha() -> str:
+    p = os.path.join(ROOT, "paper_2511_03655_gb300", "csrc", "irkgl_device.cuh")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        import tempfile
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        smax = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i].lower() == "active"})
+        power = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(power) if power else None}
+
+
+# --------------------------------------------------------------------------
+# reference arm: the oracle on the host cores
+# --------------------------------------------------------------------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from oracle import cbind
+    from paper_2511_03655_gb300 import workloads
+    w = workloads.kepler_ensemble(batch=args.batch, periods=args.periods)
+    cores = os.cpu_count() or 1
+    # bounded sample: orbits spread evenly over e, full horizon
+    n_sample = max(cores * 16, 64)
+    idx = np.argsort(w["e"])[np.linspace(0, args.batch - 1, n_sample).astype(int)]
+    ts = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        r = cbind.run(cbind.KEPLER, [1.0], w["q0"][idx], w["v0"][idx], w["h"][idx],
+                      w["nsteps"][idx], nthreads=cores)
+        t1 = time.perf_counter()
+        if i >= args.warmup:
+            ts.append(t1 - t0)
+    steps_per = float(w["nsteps"][idx].sum())
+    ok = (r["dH_max"] <= TOL) & (r["status"] == 0)
+    value = float(w["nsteps"][idx][ok].sum()) / statistics.mean(ts)
+    sample = (f"{n_sample} orbits evenly spaced in e from the {args.batch}-orbit ensemble, "
+              f"full {args.periods}-period horizon ({steps_per:.3g} traj-steps per step)")
+    line = {
+        "metric": METRIC, "value": value, "unit": "traj-steps/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(ts),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "impl": "reference",
+        "value_all": steps_per / statistics.mean(ts),
+        "config": {"workload": f"kepler_ensemble B={args.batch} e~U[0,0.9) {args.periods} periods, "
+                               "h=2pi/round(200+100e)", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "traj-steps/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "traj-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2511_03655_gb300 import build, irkgl, workloads
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    irkgl.load()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    # ---- workload (rank r draws its own ensemble; rank 0 is the standard one)
+    w = workloads.kepler_ensemble(batch=args.batch, periods=args.periods, seed_id=2 + 1000 * rank)
+    order = (np.arange(args.batch, dtype=np.int32) if args.no_order
+             else workloads.similarity_order(w["e"]))
+    q0 = torch.tensor(w["q0"], device=dev)
+    v0 = torch.tensor(w["v0"], device=dev)
+    ns = torch.tensor(w["nsteps"], device=dev)
+    hh = torch.tensor(w["h"], device=dev)
+    od = torch.tensor(order, device=dev)
+    integ = irkgl.Integrator(irkgl.RHS_KEPLER, [1.0], 2, float(w["h"][0]), lanes_per_traj=args.lanes)
+    out = irkgl.Outputs.allocate(args.batch, 2, device=dev)
+
+    # ---- FP64 roof: the library's FMA-chain probe, timed on this stream
+    scratch = torch.zeros(1, dtype=torch.float64, device=dev)
+    for _ in range(3):
+        irkgl.irkgl_probe_fp64_fma(scratch)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    nfma = 0
+    for _ in range(5):
+        nfma += irkgl.irkgl_probe_fp64_fma(scratch)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fma_per_s = nfma / (e0.elapsed_time(e1) * 1e-3)
+    peak_tflops = 2 * fma_per_s / 1e12
+
+    def integrate():
+        integ.integrate(q0, v0, out=out, nsteps=ns, h=hh, order=od)
+
+    for _ in range(args.warmup):
+        integrate()
+    torch.cuda.synchronize()
+
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    clocks = ClockSampler(local)
+    times = []
+    barrier()
+    clocks.start()
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        integrate()
+        b.record(stream)
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b) * 1e-3)
+    clk = clocks.stop()
+    barrier()
+    t_local = sum(times)
+    t_max = max_over_ranks(t_local)
+
+    steps = out.steps.cpu().numpy()
+    iters = out.iters.cpu().numpy()
+    dH = out.dH_max.cpu().numpy()
+    st = out.status.cpu().numpy()
+    ok = (dH <= TOL) & (st == 0)
+    steps_all = sum_over_ranks(float(steps.sum()))
+    steps_ok = sum_over_ranks(float(steps[ok].sum()))
+    value = args.steps * steps_ok / t_max
+    value_all = args.steps * steps_all / t_max
+
+    flops_launch = FLOPS_PER_STEP * float(steps.sum()) + FLOPS_PER_SWEEP * float(iters.sum())
+    achieved = flops_launch / statistics.mean(times) / 1e12
+    traffic = NCU_TRAFFIC_BYTES_PER_LAUNCH if NCU_KERNEL_SHA == kernel_sha() else None
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "traj-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"kepler_ensemble B={args.batch} per GPU, e~U[0,0.9), "
+                               f"{args.periods} periods, h=2pi/round(200+100e), one persistent launch",
+                   "batch_per_gpu": args.batch, "periods": args.periods,
+                   "lanes_per_traj": integ.tile,
+                   "order": "natural" if args.no_order else "similarity (e descending)",
+                   "l2": "state ~12.6 MB < L2; L2 flushed with a 256 MiB write before every timed step",
+                   "parallelism": f"dp{world} (independent shards, no collective on the data path)"},
+        "value_all": value_all,
+        "accuracy": {"tol": TOL, "orbits_within_tol": float(ok.mean()),
+                     "dH_max_median": float(np.median(dH)), "dH_max_max": float(dH.max()),
+                     "status_nonzero": int((st != 0).sum())},
+        "sweeps_per_step": float(iters.sum() / max(steps.sum(), 1)),
+        "gpu_launches": args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                     "frac": achieved / peak_tflops, "traffic": traffic,
+                     "peak_source": "FP64 FMA-chain probe (irkgl_probe_fp64_fma) measured live, "
+                                    "2 flops per FMA",
+                     "kernel": "irkgl_kernel<Kepler>", "flops_per_launch": flops_launch},
+        "clocks": clk,
+    }
+
+    if not args.skip_extras:
+        # ---- e2e: the host-buffer C-ABI call, copies inside the timed region
+        hq0 = torch.tensor(w["q0"]).pin_memory()
+        hv0 = torch.tensor(w["v0"]).pin_memory()
+        hns = torch.tensor(w["nsteps"]).pin_memory()
+        hh_ = torch.tensor(w["h"]).pin_memory()
+        hod = torch.tensor(order).pin_memory()
+        hout = irkgl.Outputs(q=torch.empty((args.batch, 2), dtype=torch.float64).pin_memory(),
+                             v=torch.empty((args.batch, 2), dtype=torch.float64).pin_memory(),
+                             dH_max=torch.empty(args.batch, dtype=torch.float64).pin_memory(),
+                             iters=torch.empty(args.batch, dtype=torch.int64).pin_memory(),
+                             steps=torch.empty(args.batch, dtype=torch.int64).pin_memory(),
+                             status=torch.empty(args.batch, dtype=torch.int32).pin_memory())
+        h2d = sum(t.numel() * t.element_size() for t in (hq0, hv0, hns, hh_, hod))
+        d2h = sum(t.numel() * t.element_size() for t in (hout.q, hout.v, hout.dH_max, hout.iters,
+                                                          hout.steps, hout.status))
+        integ.integrate_host(hq0, hv0, out=hout, nsteps=hns, h=hh_, order=hod)
+        et = []
+        for _ in range(args.steps):
+            barrier()
+            t0 = time.perf_counter()
+            integ.integrate_host(hq0, hv0, out=hout, nsteps=hns, h=hh_, order=hod)
+            et.append(time.perf_counter() - t0)
+        ok_h = (hout.dH_max.numpy() <= TOL) & (hout.status.numpy() == 0)
+        e2e_ok = sum_over_ranks(float(hout.steps.numpy()[ok_h].sum()))
+        e2e_t = max_over_ranks(sum(et))
+        line["e2e"] = {"value": args.steps * e2e_ok / e2e_t, "unit": "traj-steps/s",
+                       "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                       "api": "irkgl_integrate_host (pinned host buffers)"}
+
+        # ---- plain GPU form: one trajectory per launch, one launch per step
+        wq = workloads.kepler_single()
+        pi_ = irkgl.Integrator(irkgl.RHS_KEPLER, [1.0], 2, float(wq["h"][0]))
+        pq = torch.tensor(wq["q0"], device=dev)
+        pv = torch.tensor(wq["v0"], device=dev)
+        pql, pvl = torch.zeros_like(pq), torch.zeros_like(pv)
+        prp = torch.zeros((1, 8, 2), dtype=torch.float64, device=dev)
+        for _ in range(50):
+            pi_.step(pq, pv, pql, pvl, prp, nsteps=1)
+        n_plain = 2000
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(n_plain):
+            pi_.step(pq, pv, pql, pvl, prp, nsteps=1)
+        b.record(stream)
+        torch.cuda.synchronize()
+        plain = n_plain / (a.elapsed_time(b) * 1e-3)
+        pi_.close()
+        line["plain_gpu_form"] = {"value": plain, "unit": "traj-steps/s",
+                                  "sample": f"{n_plain} launches of irkgl_step(batch=1, nsteps=1), "
+                                            "Kepler e=0.5, h=T/200, state in HBM",
+                                  "speedup_batched_over_plain": value_all / world / plain}
+
+        # ---- CPU baseline: the oracle on this host's cores (rank 0, N = 1 only)
+        if rank == 0 and world == 1:
+            from oracle import cbind
+            cores = os.cpu_count() or 1
+            n_sample = max(cores * 16, 64)
+            idx = np.argsort(w["e"])[np.linspace(0, args.batch - 1, n_sample).astype(int)]
+            t0 = time.perf_counter()
+            r = cbind.run(cbind.KEPLER, [1.0], w["q0"][idx], w["v0"][idx], w["h"][idx],
+                          w["nsteps"][idx], nthreads=cores)
+            dt = time.perf_counter() - t0
+            okc = (r["dH_max"] <= TOL) & (r["status"] == 0)
+            line["cpu_baseline"] = {
+                "value": float(w["nsteps"][idx][okc].sum()) / dt, "unit": "traj-steps/s",
+                "cores": cores, "kind": "oracle",
+                "sample": f"{n_sample} orbits evenly spaced in e, full {args.periods}-period horizon, "
+                          f"{dt:.1f} s wall on {cores} threads"}
+
+    if rank == 0:
+        print(json.dumps(line))
+    integ.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,188 @@
+/*
+ * irkgl.h -- C-ABI of the GB300 IRKGL16 library (libirkgl.so).
+ *
+ * The library integrates batches of separable second-order systems
+ *     q'' = g(q),  y = (q, v),  q, v in R^d
+ * with IRKGL16, the 8-stage order-16 Gauss-Legendre collocation method in
+ * the exactly-symplectic second-order floating-point form of
+ * arXiv 2511.03655:
+ *   G_i = g(Q_i),  R_i = h b_i G_i                         (Sec. 2.4, Eq. Gi)
+ *   Q_i = q_{n-1} + h (c_i v_{n-1} + sum_j eta_ij R_j)    (Eq. Qi2)
+ *   v_n = v_{n-1} + sum_i R_i,
+ *   q_n = q_{n-1} + h v_n - h sum_i c_i R_i                 (Eq. qnvn2)
+ * solved by the stage-wise fixed-point iteration of Eq. IRK_FP2, started
+ * from the extrapolated guess of Eq. IRK_init2 (Eq. Pol0), stopped by the
+ * roundoff-aware rule of Eqs. Delta_n / stopping (positions only), with the
+ * state (q, v) kept as compensated hi + lo pairs (Sec. 5).  Everything is
+ * computed in FP64 on the GPU.
+ *
+ * Conventions for every function:
+ *   - Return value: IRKGL_OK (0) or a negative irkgl_error.  Launches are
+ *     asynchronous on the given CUDA stream (cudaStream_t passed as void*,
+ *     NULL = legacy default stream); a device-side failure surfaces on the
+ *     next synchronising call.  Per-trajectory outcomes are written to
+ *     status[] (IRKGL_STATUS_*).
+ *   - Layout: FP64, trajectory-major, contiguous: positions and velocities
+ *     are [batch][dim]; stage increments R are [batch][8][dim].
+ *   - Ownership: the caller owns every array passed in; the library owns
+ *     only the context and its small device workspace.  Pointers documented
+ *     as "device" must be CUDA device (or managed) memory on the current
+ *     device; "host" pointers are ordinary host memory.
+ *   - A context's calls must not overlap on the device (issue them on one
+ *     stream, or synchronise between streams): they share one work counter.
+ *   - Thread safety: distinct contexts may be used from distinct host
+ *     threads; one context is not re-entrant.
+ */
+#ifndef IRKGL_H
+#define IRKGL_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define IRKGL_STAGES 8
+
+typedef enum {
+  IRKGL_OK = 0,
+  IRKGL_ERR_INVALID = -1,     /* an argument is out of range or NULL where required */
+  IRKGL_ERR_NOMEM = -2,       /* a host or device allocation failed */
+  IRKGL_ERR_CUDA = -3,        /* a CUDA runtime call failed (see irkgl_last_cuda_error) */
+  IRKGL_ERR_UNSUPPORTED = -4  /* no compiled kernel for this (rhs kind, dim, tile) */
+} irkgl_error;
+
+/* Per-trajectory outcome written to status[]. */
+enum {
+  IRKGL_STATUS_OK = 0,        /* all requested steps completed */
+  IRKGL_STATUS_MAXITER = 1,   /* a step reached the sweep cap without meeting Eq. stopping;
+                                 the trajectory stops at the start of that step */
+  IRKGL_STATUS_NONFINITE = 2  /* a stage value became Inf/NaN; stops as above */
+};
+
+/* Built-in right-hand sides g(q) (device functions; the paper's user
+ * function f_ODE! of Sec. 3 is replaced by these compiled kinds). */
+typedef enum {
+  IRKGL_RHS_KEPLER = 1,        /* d = 2: g = -mu q/|q|^3;            params = {mu} */
+  IRKGL_RHS_NBODY = 2,         /* d = 3N: g_a = G sum_b m_b (q_b - q_a)/|q_b - q_a|^3;
+                                  params = {G, m_0, ..., m_{N-1}} */
+  IRKGL_RHS_FPUT = 3,          /* d = n: FPUT alpha chain, fixed ends; params = {alpha} */
+  IRKGL_RHS_HENON_HEILES = 4,  /* d = 2: Henon-Heiles (Sec. 5.1);    params = {lambda} */
+  IRKGL_RHS_HARMONIC = 5       /* any d: g = -omega^2 q;             params = {omega} */
+} irkgl_rhs_kind;
+
+typedef struct {
+  irkgl_rhs_kind kind;
+  const double* params;  /* host pointer, copied by irkgl_create */
+  int nparams;           /* number of doubles at params */
+} irkgl_rhs;
+
+/* Coefficient tables, row-major [i*8 + j] (i: stage being formed). */
+typedef struct {
+  double c[8], b[8], mu[64], eta[64], nu[64];
+} irkgl_coeffs;
+
+/* Optional outputs of irkgl_integrate (device pointers; NULL = not wanted,
+ * except q and v which are required). */
+typedef struct {
+  double* q;          /* [batch][dim] final positions (hi parts of the compensated pairs) */
+  double* v;          /* [batch][dim] final velocities (hi parts) */
+  double* q_lo;       /* [batch][dim] compensation parts */
+  double* v_lo;       /* [batch][dim] */
+  double* r_prev;     /* [batch][8][dim] R of the last completed step (for a resumed run) */
+  double* dH_max;     /* [batch] max over monitored steps of |(H_n - H_0)/H_0|, Eq. DHglobmax */
+  long long* iters;   /* [batch] total fixed-point sweeps (evaluations of g = 8 x iters) */
+  long long* steps;   /* [batch] steps completed */
+  int* status;        /* [batch] IRKGL_STATUS_* */
+} irkgl_outputs;
+
+/* Options for irkgl_set_option. */
+enum {
+  IRKGL_OPT_LANES_PER_TRAJ = 1, /* tile: 1, 2, 4 or 8 lanes share one trajectory's 8 stages
+                                   (0 = the built-in default for (kind, dim)) */
+  IRKGL_OPT_KMAX = 2,           /* sweep cap per step (default 100); 1..1000 */
+  IRKGL_OPT_MONITOR_EVERY = 3,  /* evaluate H every m steps for dH_max (default 1; 0 = off) */
+  IRKGL_OPT_BLOCK_THREADS = 4,  /* threads per block: 64, 128 or 256 (default 128) */
+  IRKGL_OPT_GRID_BLOCKS = 5     /* persistent grid size (0 = one full wave, the default) */
+};
+
+/* Fill *out with the default IRKGL16 tables of Sec. 2.4 (nodes c and weights
+ * b of the 8-point Gauss rule; mu of Eq. Yi2; eta of Eq. Qi2 satisfying
+ * Eq. sympl_cond_2 exactly; nu of Eq. Pol0 scaled to L = h b F).
+ * Host-only; needs no GPU.  Returns IRKGL_ERR_INVALID if out is NULL. */
+int irkgl_default_coeffs(irkgl_coeffs* out);
+
+/* Create a context for right-hand side f, position dimension dim (>= 1) and
+ * default step h (finite, nonzero; negative integrates backwards).
+ * coeffs == NULL selects irkgl_default_coeffs.  Allocates the context and a
+ * few bytes of device workspace on the current device.  Errors:
+ * IRKGL_ERR_INVALID (bad kind/dim/params/h), IRKGL_ERR_NOMEM, IRKGL_ERR_CUDA. */
+int irkgl_create(struct irkgl_ctx** out, irkgl_rhs f, int dim, double h,
+                 const irkgl_coeffs* coeffs);
+
+/* Set an IRKGL_OPT_* option; IRKGL_ERR_INVALID for an unknown key or value. */
+int irkgl_set_option(struct irkgl_ctx* ctx, int option, long long value);
+
+/* Advance `batch` trajectories by `nsteps` steps each, in place (device
+ * arrays).  This is the step-by-step form (Eq. IRK_init2 -> Eq. IRK_FP2 ->
+ * Eq. qnvn2 per step), used for chunked integration, resumption and the
+ * plain one-trajectory-per-launch form (batch = 1, nsteps = 1).
+ *   q, v      [batch][dim] in/out hi parts (required)
+ *   q_lo,v_lo [batch][dim] in/out compensation parts; NULL = start from 0
+ *             and do not write back
+ *   r_prev    [batch][8][dim] in/out R of the previous step (zero before the
+ *             first step); NULL = zeros, not written back
+ *   h         [batch] per-trajectory steps, or NULL for the context's h
+ *   iters     [batch][nsteps] sweeps per step, or NULL
+ *   status    [batch] outcome, or NULL
+ * batch == 0 or nsteps == 0 is a no-op.  Errors: IRKGL_ERR_INVALID,
+ * IRKGL_ERR_UNSUPPORTED, IRKGL_ERR_CUDA. */
+int irkgl_step(struct irkgl_ctx* ctx, double* q, double* v, double* q_lo, double* v_lo,
+               double* r_prev, const double* h, int batch, int nsteps, int* iters,
+               int* status, void* cuda_stream);
+
+/* Integrate `batch` independent initial states (device arrays q0, v0
+ * [batch][dim], R_prev = 0, lo = 0) in one persistent launch.
+ *   nsteps  [batch] steps per trajectory (device), or NULL to use nsteps_all
+ *   h       [batch] per-trajectory steps (device), or NULL for the context's h
+ *   order   [batch] processing order, a permutation of 0..batch-1 (device),
+ *           or NULL for 0..batch-1; grouping similar trajectories next to
+ *           each other reduces lock-step waste inside a warp
+ *   out     output pointers (see irkgl_outputs)
+ * Errors: IRKGL_ERR_INVALID, IRKGL_ERR_UNSUPPORTED, IRKGL_ERR_CUDA. */
+int irkgl_integrate(struct irkgl_ctx* ctx, const double* q0, const double* v0, int batch,
+                    const long long* nsteps, long long nsteps_all, const double* h,
+                    const int* order, const irkgl_outputs* out, void* cuda_stream);
+
+/* Same as irkgl_integrate but every array is a HOST pointer: the inputs are
+ * copied to the device, integrated, and the outputs copied back before the
+ * call returns (synchronous on cuda_stream).  Device staging buffers are
+ * owned by the context and grow on demand.  Errors as irkgl_integrate, plus
+ * IRKGL_ERR_NOMEM. */
+int irkgl_integrate_host(struct irkgl_ctx* ctx, const double* q0, const double* v0, int batch,
+                         const long long* nsteps, long long nsteps_all, const double* h,
+                         const int* order, const irkgl_outputs* out, void* cuda_stream);
+
+/* Release the context and its device workspace (NULL is ignored). */
+void irkgl_destroy(struct irkgl_ctx* ctx);
+
+/* Static text for an irkgl_error or IRKGL_STATUS_* value (never NULL). */
+const char* irkgl_strerror(int code);
+
+/* The CUDA error string of the last IRKGL_ERR_CUDA on this host thread. */
+const char* irkgl_last_cuda_error(void);
+
+/* Lanes per trajectory that the context would use for its (kind, dim). */
+int irkgl_get_tile(struct irkgl_ctx* ctx);
+
+/* Diagnostic, not part of the method: launch an FP64 fused multiply-add
+ * throughput probe (a full grid of independent FMA chains) on cuda_stream
+ * and store the number of FMAs it issues in *fma_count (host pointer).
+ * scratch is one device double the probe may write.  The caller times the
+ * launch with events on the same stream; FMAs / seconds is the FP64 roof
+ * used for the roofline fraction.  Errors: IRKGL_ERR_INVALID, IRKGL_ERR_CUDA. */
+int irkgl_probe_fp64_fma(double* scratch, long long* fma_count, void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IRKGL_H */

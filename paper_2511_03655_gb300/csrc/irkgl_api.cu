@@ -1,0 +1,471 @@
+// irkgl_api.cu -- host side of libirkgl.so: the C-ABI declared in include/irkgl.h.
+//
+// The context owns: the FP64 tables (Sec. 2.4 of arXiv 2511.03655, plus the
+// fused initial-guess matrix W), a device copy of the right-hand-side
+// parameters, a work counter for the persistent launch, and host-API staging
+// buffers.  Kernels are instantiated per (right-hand side, dimension, lanes
+// per trajectory) and dispatched from a table.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+
+#include "irkgl.h"
+#include "irkgl_device.cuh"
+#include "irkgl_tables.h"
+
+using irkgl::Coef;
+using irkgl::KArgs;
+
+namespace {
+
+thread_local char g_cuda_err[256] = "no error";
+
+int cuda_fail(cudaError_t e) {
+  std::snprintf(g_cuda_err, sizeof(g_cuda_err), "%s", cudaGetErrorString(e));
+  return IRKGL_ERR_CUDA;
+}
+
+#define IRKGL_CUDA(call)                         \
+  do {                                           \
+    cudaError_t e_ = (call);                     \
+    if (e_ != cudaSuccess) return cuda_fail(e_); \
+  } while (0)
+
+typedef void (*kernel_fn)(KArgs, Coef);
+
+struct KernelEntry {
+  int kind;
+  int dim;
+  int lpt;
+  int block;
+  const void* fn;
+  void (*launch)(dim3, dim3, cudaStream_t, const KArgs&, const Coef&);
+};
+
+template <class Rhs, int LPT, int BLOCK>
+void launch_impl(dim3 grid, dim3 block, cudaStream_t st, const KArgs& a, const Coef& c) {
+  irkgl::irkgl_kernel<Rhs, LPT, BLOCK><<<grid, block, 0, st>>>(a, c);
+}
+
+#define IRKGL_ENTRY(KIND, DIM, RHS, LPT, BLOCK)                                        \
+  KernelEntry {                                                                        \
+    KIND, DIM, LPT, BLOCK, (const void*)irkgl::irkgl_kernel<RHS, LPT, BLOCK>,         \
+        launch_impl<RHS, LPT, BLOCK>                                                   \
+  }
+
+#define IRKGL_ENTRIES_LPT(KIND, DIM, RHS_T, LPT) \
+  IRKGL_ENTRY(KIND, DIM, RHS_T, LPT, 128), IRKGL_ENTRY(KIND, DIM, RHS_T, LPT, 256), \
+      IRKGL_ENTRY(KIND, DIM, RHS_T, LPT, 64)
+
+using K1 = irkgl::Kepler<8>;
+using K2 = irkgl::Kepler<4>;
+using K4 = irkgl::Kepler<2>;
+using K8 = irkgl::Kepler<1>;
+using HH1 = irkgl::HenonHeiles<8>;
+using HH2 = irkgl::HenonHeiles<4>;
+using HH4 = irkgl::HenonHeiles<2>;
+using HH8 = irkgl::HenonHeiles<1>;
+template <int D> using Ha1 = irkgl::Harmonic<8, D>;
+template <int D> using Ha2 = irkgl::Harmonic<4, D>;
+template <int D> using Ha8 = irkgl::Harmonic<1, D>;
+
+const KernelEntry kTable[] = {
+    IRKGL_ENTRIES_LPT(IRKGL_RHS_KEPLER, 2, K1, 1),
+    IRKGL_ENTRIES_LPT(IRKGL_RHS_KEPLER, 2, K2, 2),
+    IRKGL_ENTRIES_LPT(IRKGL_RHS_KEPLER, 2, K4, 4),
+    IRKGL_ENTRIES_LPT(IRKGL_RHS_KEPLER, 2, K8, 8),
+    IRKGL_ENTRIES_LPT(IRKGL_RHS_HENON_HEILES, 2, HH1, 1),
+    IRKGL_ENTRIES_LPT(IRKGL_RHS_HENON_HEILES, 2, HH2, 2),
+    IRKGL_ENTRIES_LPT(IRKGL_RHS_HENON_HEILES, 2, HH4, 4),
+    IRKGL_ENTRIES_LPT(IRKGL_RHS_HENON_HEILES, 2, HH8, 8),
+    IRKGL_ENTRIES_LPT(IRKGL_RHS_HARMONIC, 1, Ha1<1>, 1),
+    IRKGL_ENTRIES_LPT(IRKGL_RHS_HARMONIC, 1, Ha8<1>, 8),
+    IRKGL_ENTRIES_LPT(IRKGL_RHS_HARMONIC, 2, Ha2<2>, 2),
+    IRKGL_ENTRIES_LPT(IRKGL_RHS_HARMONIC, 2, Ha8<2>, 8),
+    IRKGL_ENTRIES_LPT(IRKGL_RHS_HARMONIC, 3, Ha2<3>, 2),
+    IRKGL_ENTRIES_LPT(IRKGL_RHS_HARMONIC, 3, Ha8<3>, 8),
+};
+
+const KernelEntry* find_kernel(int kind, int dim, int lpt, int block) {
+  for (const KernelEntry& e : kTable)
+    if (e.kind == kind && e.dim == dim && e.lpt == lpt && e.block == block) return &e;
+  return nullptr;
+}
+
+// Built-in default tile per (kind, dim): the smallest LPT that is compiled,
+// preferring 2 for d = 2 (both components' compensated updates in one pass).
+int default_lpt(int kind, int dim) {
+  const int prefs[] = {2, 1, 8, 4};
+  for (int p : prefs)
+    if (find_kernel(kind, dim, p, 128)) return p;
+  return 0;
+}
+
+bool is_default_table(const irkgl_coeffs* c) {
+  irkgl_coeffs d;
+  irkgl_default_coeffs(&d);
+  return std::memcmp(&d, c, sizeof(d)) == 0;
+}
+
+// FP64 FMA throughput probe: 8 independent dependency chains per thread, a
+// full grid; the issued FMA count is returned to the caller, who times the
+// launch on its stream.  Used to measure the FP64 roof the kernels run against.
+constexpr int kProbeIters = 4096;
+__global__ void __launch_bounds__(256) fp64_fma_probe(double* out, double a, double b) {
+  double x0 = threadIdx.x * 1e-9, x1 = x0 + 1, x2 = x0 + 2, x3 = x0 + 3;
+  double x4 = x0 + 4, x5 = x0 + 5, x6 = x0 + 6, x7 = x0 + 7;
+#pragma unroll 4
+  for (int i = 0; i < kProbeIters; i++) {
+    x0 = fma(x0, a, b); x1 = fma(x1, a, b); x2 = fma(x2, a, b); x3 = fma(x3, a, b);
+    x4 = fma(x4, a, b); x5 = fma(x5, a, b); x6 = fma(x6, a, b); x7 = fma(x7, a, b);
+  }
+  const double s = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
+  if (s == 12345.678) out[0] = s;  // never true; keeps the chains alive
+}
+
+}  // namespace
+
+struct irkgl_ctx {
+  int kind;
+  int dim;
+  double h;
+  int device;
+  int sm_count;
+  Coef coef;
+  double* d_params;
+  int nparams;
+  unsigned* d_counter;
+  int lpt;       // 0 = default
+  int kmax;
+  int monitor;
+  int block;
+  int grid_blocks;
+  // staging for irkgl_integrate_host
+  void* d_stage;
+  size_t stage_bytes;
+};
+
+extern "C" {
+
+int irkgl_default_coeffs(irkgl_coeffs* out) {
+  if (!out) return IRKGL_ERR_INVALID;
+  for (int i = 0; i < 8; i++) {
+    out->c[i] = IRKGL_TAB_C[i];
+    out->b[i] = IRKGL_TAB_B[i];
+  }
+  for (int x = 0; x < 64; x++) {
+    out->mu[x] = IRKGL_TAB_MU[x];
+    out->eta[x] = IRKGL_TAB_ETA[x];
+    out->nu[x] = IRKGL_TAB_NU[x];
+  }
+  return IRKGL_OK;
+}
+
+const char* irkgl_strerror(int code) {
+  switch (code) {
+    case IRKGL_OK: return "ok";
+    case IRKGL_ERR_INVALID: return "invalid argument";
+    case IRKGL_ERR_NOMEM: return "out of memory";
+    case IRKGL_ERR_CUDA: return "CUDA runtime error";
+    case IRKGL_ERR_UNSUPPORTED: return "no compiled kernel for this right-hand side, dimension and tile";
+    case IRKGL_STATUS_MAXITER: return "status: fixed-point sweep cap reached";
+    case IRKGL_STATUS_NONFINITE: return "status: non-finite stage value";
+    default: return "unknown code";
+  }
+}
+
+const char* irkgl_last_cuda_error(void) { return g_cuda_err; }
+
+int irkgl_probe_fp64_fma(double* scratch, long long* fma_count, void* stream) {
+  if (!scratch || !fma_count) return IRKGL_ERR_INVALID;
+  int dev = 0, sms = 0;
+  IRKGL_CUDA(cudaGetDevice(&dev));
+  IRKGL_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int blocks = sms * 8, threads = 256;
+  fp64_fma_probe<<<blocks, threads, 0, static_cast<cudaStream_t>(stream)>>>(scratch, 0.999999, 1e-7);
+  IRKGL_CUDA(cudaGetLastError());
+  *fma_count = static_cast<long long>(blocks) * threads * kProbeIters * 8;
+  return IRKGL_OK;
+}
+
+static int check_rhs(const irkgl_rhs& f, int dim) {
+  if (dim < 1 || dim > 4096) return IRKGL_ERR_INVALID;
+  if (f.nparams < 1 || !f.params) return IRKGL_ERR_INVALID;
+  for (int i = 0; i < f.nparams; i++)
+    if (!std::isfinite(f.params[i])) return IRKGL_ERR_INVALID;
+  switch (f.kind) {
+    case IRKGL_RHS_KEPLER:
+    case IRKGL_RHS_HENON_HEILES:
+      return dim == 2 ? IRKGL_OK : IRKGL_ERR_INVALID;
+    case IRKGL_RHS_HARMONIC:
+    case IRKGL_RHS_FPUT:
+      return IRKGL_OK;
+    case IRKGL_RHS_NBODY:
+      return (dim % 3 == 0 && f.nparams == 1 + dim / 3) ? IRKGL_OK : IRKGL_ERR_INVALID;
+    default:
+      return IRKGL_ERR_INVALID;
+  }
+}
+
+int irkgl_create(irkgl_ctx** out, irkgl_rhs f, int dim, double h, const irkgl_coeffs* coeffs) {
+  if (!out) return IRKGL_ERR_INVALID;
+  *out = nullptr;
+  if (!std::isfinite(h) || h == 0.0) return IRKGL_ERR_INVALID;
+  int rc = check_rhs(f, dim);
+  if (rc != IRKGL_OK) return rc;
+  irkgl_coeffs tab;
+  if (coeffs) {
+    tab = *coeffs;
+    const double* all = reinterpret_cast<const double*>(&tab);
+    for (size_t i = 0; i < sizeof(tab) / sizeof(double); i++)
+      if (!std::isfinite(all[i])) return IRKGL_ERR_INVALID;
+  } else {
+    irkgl_default_coeffs(&tab);
+  }
+  irkgl_ctx* c = static_cast<irkgl_ctx*>(std::calloc(1, sizeof(irkgl_ctx)));
+  if (!c) return IRKGL_ERR_NOMEM;
+  c->kind = f.kind;
+  c->dim = dim;
+  c->h = h;
+  c->kmax = 100;
+  c->monitor = 1;
+  c->block = 128;
+  c->lpt = 0;
+  c->grid_blocks = 0;
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device);
+  if (e != cudaSuccess) {
+    std::free(c);
+    return cuda_fail(e);
+  }
+  for (int i = 0; i < 8; i++) {
+    c->coef.c[i] = tab.c[i];
+    c->coef.b[i] = tab.b[i];
+  }
+  for (int x = 0; x < 64; x++) c->coef.eta[x] = tab.eta[x];
+  if (is_default_table(&tab)) {
+    for (int x = 0; x < 64; x++) c->coef.W[x] = IRKGL_TAB_W[x];
+  } else {
+    // W = mu diag(b) nu in FP64, fixed summation order (host code is built
+    // without floating-point contraction, so this is the same on every host)
+    for (int i = 0; i < 8; i++)
+      for (int k = 0; k < 8; k++) {
+        double acc = 0.0;
+        for (int j = 0; j < 8; j++) acc += (tab.mu[i * 8 + j] * tab.b[j]) * tab.nu[j * 8 + k];
+        c->coef.W[i * 8 + k] = acc;
+      }
+  }
+  c->nparams = f.nparams;
+  e = cudaMalloc(&c->d_params, sizeof(double) * f.nparams);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(c->d_params, f.params, sizeof(double) * f.nparams, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_counter, 2 * sizeof(unsigned));
+  if (e != cudaSuccess) {
+    cudaFree(c->d_params);
+    std::free(c);
+    return e == cudaErrorMemoryAllocation ? IRKGL_ERR_NOMEM : cuda_fail(e);
+  }
+  *out = c;
+  return IRKGL_OK;
+}
+
+void irkgl_destroy(irkgl_ctx* c) {
+  if (!c) return;
+  cudaFree(c->d_params);
+  cudaFree(c->d_counter);
+  cudaFree(c->d_stage);
+  std::free(c);
+}
+
+int irkgl_set_option(irkgl_ctx* c, int option, long long value) {
+  if (!c) return IRKGL_ERR_INVALID;
+  switch (option) {
+    case IRKGL_OPT_LANES_PER_TRAJ:
+      if (!(value == 0 || value == 1 || value == 2 || value == 4 || value == 8)) return IRKGL_ERR_INVALID;
+      c->lpt = static_cast<int>(value);
+      return IRKGL_OK;
+    case IRKGL_OPT_KMAX:
+      if (value < 1 || value > 1000) return IRKGL_ERR_INVALID;
+      c->kmax = static_cast<int>(value);
+      return IRKGL_OK;
+    case IRKGL_OPT_MONITOR_EVERY:
+      if (value < 0 || value > (1LL << 30)) return IRKGL_ERR_INVALID;
+      c->monitor = static_cast<int>(value);
+      return IRKGL_OK;
+    case IRKGL_OPT_BLOCK_THREADS:
+      if (!(value == 64 || value == 128 || value == 256)) return IRKGL_ERR_INVALID;
+      c->block = static_cast<int>(value);
+      return IRKGL_OK;
+    case IRKGL_OPT_GRID_BLOCKS:
+      if (value < 0 || value > (1 << 20)) return IRKGL_ERR_INVALID;
+      c->grid_blocks = static_cast<int>(value);
+      return IRKGL_OK;
+    default:
+      return IRKGL_ERR_INVALID;
+  }
+}
+
+int irkgl_get_tile(irkgl_ctx* c) {
+  if (!c) return IRKGL_ERR_INVALID;
+  return c->lpt ? c->lpt : default_lpt(c->kind, c->dim);
+}
+
+static int run(irkgl_ctx* c, KArgs& a, cudaStream_t st) {
+  const int lpt = c->lpt ? c->lpt : default_lpt(c->kind, c->dim);
+  const KernelEntry* ke = lpt ? find_kernel(c->kind, c->dim, lpt, c->block) : nullptr;
+  if (!ke) return IRKGL_ERR_UNSUPPORTED;
+  a.counter = c->d_counter;
+  a.params = c->d_params;
+  a.kmax = c->kmax;
+  a.monitor = c->monitor;
+  const int traj_per_block = c->block / lpt;
+  long long need = (static_cast<long long>(a.batch) + traj_per_block - 1) / traj_per_block;
+  int grid = c->grid_blocks;
+  if (grid <= 0) {
+    int per_sm = 0;
+    IRKGL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ke->fn, c->block, 0));
+    if (per_sm < 1) per_sm = 1;
+    grid = per_sm * c->sm_count;
+  }
+  if (grid > need) grid = static_cast<int>(need);
+  if (grid < 1) grid = 1;
+  IRKGL_CUDA(cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned), st));
+  ke->launch(dim3(grid), dim3(c->block), st, a, c->coef);
+  IRKGL_CUDA(cudaGetLastError());
+  return IRKGL_OK;
+}
+
+int irkgl_step(irkgl_ctx* c, double* q, double* v, double* q_lo, double* v_lo, double* r_prev,
+               const double* h, int batch, int nsteps, int* iters, int* status, void* stream) {
+  if (!c || batch < 0 || nsteps < 0) return IRKGL_ERR_INVALID;
+  if (batch == 0 || nsteps == 0) return IRKGL_OK;
+  if (!q || !v) return IRKGL_ERR_INVALID;
+  KArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.batch = batch;
+  a.hist_len = nsteps;
+  a.q_in = q;
+  a.v_in = v;
+  a.qlo_in = q_lo;
+  a.vlo_in = v_lo;
+  a.rp_in = r_prev;
+  a.q_out = q;
+  a.v_out = v;
+  a.qlo_out = q_lo;
+  a.vlo_out = v_lo;
+  a.rp_out = r_prev;
+  a.nsteps = nullptr;
+  a.nsteps_all = nsteps;
+  a.h = h;
+  a.h_all = c->h;
+  a.order = nullptr;
+  a.iters_hist = iters;
+  a.status = status;
+  int saved_monitor = c->monitor;
+  c->monitor = 0;  // no energy monitoring in the step-by-step form
+  int rc = run(c, a, static_cast<cudaStream_t>(stream));
+  c->monitor = saved_monitor;
+  return rc;
+}
+
+int irkgl_integrate(irkgl_ctx* c, const double* q0, const double* v0, int batch,
+                    const long long* nsteps, long long nsteps_all, const double* h,
+                    const int* order, const irkgl_outputs* out, void* stream) {
+  if (!c || batch < 0 || !out) return IRKGL_ERR_INVALID;
+  if (batch == 0) return IRKGL_OK;
+  if (!q0 || !v0 || !out->q || !out->v) return IRKGL_ERR_INVALID;
+  if (!nsteps && nsteps_all < 0) return IRKGL_ERR_INVALID;
+  KArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.batch = batch;
+  a.q_in = q0;
+  a.v_in = v0;
+  a.q_out = out->q;
+  a.v_out = out->v;
+  a.qlo_out = out->q_lo;
+  a.vlo_out = out->v_lo;
+  a.rp_out = out->r_prev;
+  a.nsteps = nsteps;
+  a.nsteps_all = nsteps_all;
+  a.h = h;
+  a.h_all = c->h;
+  a.order = order;
+  a.iters_total = out->iters;
+  a.dH_max = out->dH_max;
+  a.status = out->status;
+  a.steps_done = out->steps;
+  return run(c, a, static_cast<cudaStream_t>(stream));
+}
+
+int irkgl_integrate_host(irkgl_ctx* c, const double* q0, const double* v0, int batch,
+                         const long long* nsteps, long long nsteps_all, const double* h,
+                         const int* order, const irkgl_outputs* out, void* stream) {
+  if (!c || batch < 0 || !out) return IRKGL_ERR_INVALID;
+  if (batch == 0) return IRKGL_OK;
+  if (!q0 || !v0 || !out->q || !out->v) return IRKGL_ERR_INVALID;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t B = static_cast<size_t>(batch), D = static_cast<size_t>(c->dim);
+  // staging layout (8-byte aligned slices)
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off += (bytes + 255) & ~size_t(255);
+    return o;
+  };
+  const size_t o_q0 = take(B * D * 8), o_v0 = take(B * D * 8);
+  const size_t o_ns = nsteps ? take(B * 8) : 0, o_h = h ? take(B * 8) : 0, o_ord = order ? take(B * 4) : 0;
+  const size_t o_q = take(B * D * 8), o_v = take(B * D * 8);
+  const size_t o_ql = out->q_lo ? take(B * D * 8) : 0, o_vl = out->v_lo ? take(B * D * 8) : 0;
+  const size_t o_rp = out->r_prev ? take(B * 8 * D * 8) : 0;
+  const size_t o_dh = out->dH_max ? take(B * 8) : 0, o_it = out->iters ? take(B * 8) : 0;
+  const size_t o_sd = out->steps ? take(B * 8) : 0, o_st = out->status ? take(B * 4) : 0;
+  if (off > c->stage_bytes) {
+    cudaFree(c->d_stage);
+    c->d_stage = nullptr;
+    c->stage_bytes = 0;
+    cudaError_t e = cudaMalloc(&c->d_stage, off);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? IRKGL_ERR_NOMEM : cuda_fail(e);
+    c->stage_bytes = off;
+  }
+  char* base = static_cast<char*>(c->d_stage);
+  auto dp = [&](size_t o) { return static_cast<void*>(base + o); };
+  IRKGL_CUDA(cudaMemcpyAsync(dp(o_q0), q0, B * D * 8, cudaMemcpyHostToDevice, st));
+  IRKGL_CUDA(cudaMemcpyAsync(dp(o_v0), v0, B * D * 8, cudaMemcpyHostToDevice, st));
+  if (nsteps) IRKGL_CUDA(cudaMemcpyAsync(dp(o_ns), nsteps, B * 8, cudaMemcpyHostToDevice, st));
+  if (h) IRKGL_CUDA(cudaMemcpyAsync(dp(o_h), h, B * 8, cudaMemcpyHostToDevice, st));
+  if (order) IRKGL_CUDA(cudaMemcpyAsync(dp(o_ord), order, B * 4, cudaMemcpyHostToDevice, st));
+  irkgl_outputs dout;
+  std::memset(&dout, 0, sizeof(dout));
+  dout.q = static_cast<double*>(dp(o_q));
+  dout.v = static_cast<double*>(dp(o_v));
+  if (out->q_lo) dout.q_lo = static_cast<double*>(dp(o_ql));
+  if (out->v_lo) dout.v_lo = static_cast<double*>(dp(o_vl));
+  if (out->r_prev) dout.r_prev = static_cast<double*>(dp(o_rp));
+  if (out->dH_max) dout.dH_max = static_cast<double*>(dp(o_dh));
+  if (out->iters) dout.iters = static_cast<long long*>(dp(o_it));
+  if (out->steps) dout.steps = static_cast<long long*>(dp(o_sd));
+  if (out->status) dout.status = static_cast<int*>(dp(o_st));
+  int rc = irkgl_integrate(c, static_cast<double*>(dp(o_q0)), static_cast<double*>(dp(o_v0)), batch,
+                           nsteps ? static_cast<long long*>(dp(o_ns)) : nullptr, nsteps_all,
+                           h ? static_cast<double*>(dp(o_h)) : nullptr,
+                           order ? static_cast<int*>(dp(o_ord)) : nullptr, &dout, stream);
+  if (rc != IRKGL_OK) return rc;
+  IRKGL_CUDA(cudaMemcpyAsync(out->q, dout.q, B * D * 8, cudaMemcpyDeviceToHost, st));
+  IRKGL_CUDA(cudaMemcpyAsync(out->v, dout.v, B * D * 8, cudaMemcpyDeviceToHost, st));
+  if (out->q_lo) IRKGL_CUDA(cudaMemcpyAsync(out->q_lo, dout.q_lo, B * D * 8, cudaMemcpyDeviceToHost, st));
+  if (out->v_lo) IRKGL_CUDA(cudaMemcpyAsync(out->v_lo, dout.v_lo, B * D * 8, cudaMemcpyDeviceToHost, st));
+  if (out->r_prev)
+    IRKGL_CUDA(cudaMemcpyAsync(out->r_prev, dout.r_prev, B * 8 * D * 8, cudaMemcpyDeviceToHost, st));
+  if (out->dH_max) IRKGL_CUDA(cudaMemcpyAsync(out->dH_max, dout.dH_max, B * 8, cudaMemcpyDeviceToHost, st));
+  if (out->iters) IRKGL_CUDA(cudaMemcpyAsync(out->iters, dout.iters, B * 8, cudaMemcpyDeviceToHost, st));
+  if (out->steps) IRKGL_CUDA(cudaMemcpyAsync(out->steps, dout.steps, B * 8, cudaMemcpyDeviceToHost, st));
+  if (out->status) IRKGL_CUDA(cudaMemcpyAsync(out->status, dout.status, B * 4, cudaMemcpyDeviceToHost, st));
+  IRKGL_CUDA(cudaStreamSynchronize(st));
+  return IRKGL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,536 @@
+// irkgl_device.cuh -- device side of the IRKGL16 library (sm_103a, FP64).
+//
+// One trajectory's 8 stages are spread over LPT lanes (LPT = 1, 2, 4, 8;
+// SPL = 8/LPT stages per lane); 32/LPT trajectories share a warp and run in
+// lock-step one step at a time.  Per step (arXiv 2511.03655):
+//
+//   init   Q_i = q + h (c_i v + sum_k W_ik R_k^prev)        Eq. IRK_init2 (fused)
+//   sweep  R_i = h b_i g(Q_i)                                Eq. Gi
+//          Qn_i = q + h (c_i v + sum_j eta_ij R_j)           Eq. Qi2 / IRK_FP2
+//          Delta_l = max_i |Qn_il - Q_il|, Eq. stopping      Eqs. Delta_n, stopping
+//   update v += sum_i R_i, q += h v_new - h sum_i c_i R_i    Eq. qnvn2, compensated
+//
+// FP64 is the scarce unit on GB300 (about 1/64 of the FP32 rate, and a
+// masked lane costs as much as an active one), so: |x|, max and the
+// stopping vote run on integer bit patterns; the reciprocal square root
+// seed comes from the FP32 MUFU unit through integer bit manipulation (no
+// F2F conversions, which run at the FP64 rate); sums over stages held by
+// other lanes are gathered with warp shuffles; per-component scalar work
+// (the compensated update) is spread over the LPT lanes of a trajectory.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace irkgl {
+
+constexpr int S = 8;
+constexpr unsigned FULL = 0xffffffffu;
+constexpr unsigned long long INF_BITS = 0x7ff0000000000000ULL;
+
+enum { ST_OK = 0, ST_MAXITER = 1, ST_NONFINITE = 2 };
+
+// Coefficients passed by value (kernel parameter space = constant bank).
+struct Coef {
+  double c[S];
+  double b[S];
+  double eta[S * S];  // Eq. Qi2, row-major [i*8+j]
+  double W[S * S];    // fused initial guess of Eq. IRK_init2
+};
+
+struct KArgs {
+  int batch;
+  int kmax;
+  int monitor;   // evaluate H every `monitor` steps (0 = never)
+  int hist_len;  // columns of iters_hist
+  const double* q_in;
+  const double* v_in;
+  const double* qlo_in;  // may be null (zeros)
+  const double* vlo_in;
+  const double* rp_in;   // [batch][8][D], may be null (zeros)
+  double* q_out;
+  double* v_out;
+  double* qlo_out;       // may be null
+  double* vlo_out;
+  double* rp_out;        // may be null
+  const long long* nsteps;  // [batch] or null -> nsteps_all
+  long long nsteps_all;
+  const double* h;          // [batch] or null -> h_all
+  double h_all;
+  const int* order;         // [batch] or null
+  int* iters_hist;          // [batch][hist_len] or null
+  long long* iters_total;   // [batch] or null
+  double* dH_max;           // [batch] or null
+  int* status;              // [batch] or null
+  long long* steps_done;    // [batch] or null
+  unsigned int* counter;    // work counter, zero at launch
+  const double* params;     // right-hand-side parameters (device)
+};
+
+// ------------------------------------------------------------------------
+// arithmetic helpers
+// ------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return static_cast<unsigned long long>(__double_as_longlong(x)) & 0x7fffffffffffffffULL;
+}
+
+__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) {
+  return a > b ? a : b;
+}
+__device__ __forceinline__ unsigned long long umin64(unsigned long long a, unsigned long long b) {
+  return a < b ? a : b;
+}
+
+// Seed y0 ~ x^(-1/2) with at most 24 significant bits (so y0*y0 is exact in
+// FP64), for a positive normal x: the leading 23 mantissa bits of x, with the
+// exponent parity folded in, form an FP32 number in [1, 4); its FP32
+// reciprocal square root (MUFU.RSQ, about 22 correct bits) is rescaled by
+// 2^(-floor(E/2)) by integer exponent arithmetic.  Callers handle x that is
+// zero, subnormal, negative, Inf or NaN separately.
+__device__ __forceinline__ double rsqrt_seed(double x) {
+  const unsigned long long bx = static_cast<unsigned long long>(__double_as_longlong(x));
+  const int E = static_cast<int>((bx >> 52) & 0x7ff) - 1023;
+  const int par = E & 1;
+  const int half = (E - par) / 2;
+  const unsigned m23 = static_cast<unsigned>((bx >> 29) & 0x7fffffu);
+  const float xf = __uint_as_float((static_cast<unsigned>(127 + par) << 23) | m23);
+  const float yf = rsqrtf(xf);  // in (0.5, 1]
+  const unsigned yb = __float_as_uint(yf);
+  const int ef = static_cast<int>(yb >> 23) - 127;
+  const unsigned long long y0b =
+      (static_cast<unsigned long long>(ef - half + 1023) << 52) |
+      (static_cast<unsigned long long>(yb & 0x7fffffu) << 29);
+  return __longlong_as_double(static_cast<long long>(y0b));
+}
+
+__device__ __forceinline__ bool positive_normal(double x) {
+  const unsigned long long bx = static_cast<unsigned long long>(__double_as_longlong(x));
+  return (bx - 0x0010000000000000ULL) < 0x7fe0000000000000ULL;  // 0 < x < Inf, normal
+}
+
+// x^(-3/2) for x > 0.  From the seed y0 with e = 1 - x y0^2 (|e| < 2^-20):
+// x^(-3/2) = y0^3 (1 - e)^(-3/2) = y0^3 (1 + 3/2 e + 15/8 e^2 + O(e^3)),
+// the binomial series (a third-order Householder correction); truncation
+// error < 2^-57, so the result is within about one ulp.  6 FP64 operations.
+__device__ __forceinline__ double rinv3(double x) {
+  if (!positive_normal(x)) {
+    // zero -> +Inf, Inf -> 0, negative/NaN -> NaN (rare; native path)
+    return 1.0 / (x * sqrt(x));
+  }
+  const double y0 = rsqrt_seed(x);
+  const double y02 = y0 * y0;          // exact
+  const double e = fma(-x, y02, 1.0);
+  const double y03 = y02 * y0;
+  const double p = fma(e, 1.875, 1.5);
+  const double t = e * p;
+  return fma(y03, t, y03);
+}
+
+// x^(-1/2) for x > 0, same seed: y0 (1 + e/2 + 3/8 e^2).  5 FP64 operations.
+__device__ __forceinline__ double rinv1(double x) {
+  if (!positive_normal(x)) return 1.0 / sqrt(x);
+  const double y0 = rsqrt_seed(x);
+  const double e = fma(-x, y0 * y0, 1.0);
+  const double p = fma(e, 0.375, 0.5);
+  const double t = e * p;
+  return fma(y0, t, y0);
+}
+
+// (hi, lo) + x: Knuth's TwoSum of hi and x, error folded into lo, Dekker's
+// Fast2Sum renormalisation (Sec. 5, improved summation).  Explicit
+// round-to-nearest adds keep the compiler from contracting or reordering.
+__device__ __forceinline__ void two_sum_add(double& hi, double& lo, double x) {
+  const double s = __dadd_rn(hi, x);
+  const double bb = __dsub_rn(s, hi);
+  const double err = __dadd_rn(__dsub_rn(hi, __dsub_rn(s, bb)), __dsub_rn(x, bb));
+  const double lo2 = __dadd_rn(lo, err);
+  const double hi2 = __dadd_rn(s, lo2);
+  lo = __dsub_rn(lo2, __dsub_rn(hi2, s));
+  hi = hi2;
+}
+
+// ------------------------------------------------------------------------
+// right-hand sides: R = (h b_i) g(Q_i) for one stage, and H(q, v)
+// ------------------------------------------------------------------------
+template <int SPL>
+struct Kepler {
+  static constexpr int D = 2;
+  double mu;
+  double s[SPL];  // -(h b_i) mu per own stage
+  __device__ void load_params(const double* p) { mu = p[0]; }
+  __device__ void set_step(const double (&hb)[SPL]) {
+#pragma unroll
+    for (int t = 0; t < SPL; t++) s[t] = -(hb[t] * mu);
+  }
+  __device__ __forceinline__ void stage_R(int t, const double (&x)[D], double (&R)[D]) const {
+    const double r2 = fma(x[0], x[0], x[1] * x[1]);
+    const double w = s[t] * rinv3(r2);
+    R[0] = x[0] * w;
+    R[1] = x[1] * w;
+  }
+  __device__ double H(const double (&q)[D], const double (&v)[D]) const {
+    const double ke = 0.5 * fma(v[0], v[0], v[1] * v[1]);
+    return fma(-mu, rinv1(fma(q[0], q[0], q[1] * q[1])), ke);
+  }
+};
+
+template <int SPL>
+struct HenonHeiles {
+  static constexpr int D = 2;
+  double lam, twolam;
+  double s[SPL];  // -(h b_i)
+  __device__ void load_params(const double* p) {
+    lam = p[0];
+    twolam = 2.0 * p[0];
+  }
+  __device__ void set_step(const double (&hb)[SPL]) {
+#pragma unroll
+    for (int t = 0; t < SPL; t++) s[t] = -hb[t];
+  }
+  // g1 = -q1 (1 + 2 lam q2), g2 = -(q2 + lam (q1^2 - q2^2))
+  __device__ __forceinline__ void stage_R(int t, const double (&x)[D], double (&R)[D]) const {
+    const double a = fma(twolam, x[1], 1.0);
+    R[0] = s[t] * (x[0] * a);
+    const double u = fma(x[0], x[0], -(x[1] * x[1]));
+    R[1] = s[t] * fma(lam, u, x[1]);
+  }
+  __device__ double H(const double (&q)[D], const double (&v)[D]) const {
+    const double ke = 0.5 * fma(v[0], v[0], v[1] * v[1]);
+    const double pe = 0.5 * fma(q[0], q[0], q[1] * q[1]);
+    const double cub = fma(q[0] * q[0], q[1], -(q[1] * q[1] * q[1]) * (1.0 / 3.0));
+    return fma(lam, cub, ke + pe);
+  }
+};
+
+template <int SPL, int DD>
+struct Harmonic {
+  static constexpr int D = DD;
+  double w2;
+  double s[SPL];  // -(h b_i) omega^2
+  __device__ void load_params(const double* p) { w2 = p[0] * p[0]; }
+  __device__ void set_step(const double (&hb)[SPL]) {
+#pragma unroll
+    for (int t = 0; t < SPL; t++) s[t] = -(hb[t] * w2);
+  }
+  __device__ __forceinline__ void stage_R(int t, const double (&x)[D], double (&R)[D]) const {
+#pragma unroll
+    for (int l = 0; l < D; l++) R[l] = s[t] * x[l];
+  }
+  __device__ double H(const double (&q)[D], const double (&v)[D]) const {
+    double acc = 0.0;
+#pragma unroll
+    for (int l = 0; l < D; l++) acc = fma(0.5 * v[l], v[l], fma(0.5 * w2 * q[l], q[l], acc));
+    return acc;
+  }
+};
+
+// ------------------------------------------------------------------------
+// the kernel
+// ------------------------------------------------------------------------
+template <class Rhs, int LPT, int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
+    irkgl_kernel(const __grid_constant__ KArgs a, const __grid_constant__ Coef cf) {
+  constexpr int D = Rhs::D;
+  constexpr int SPL = S / LPT;
+  constexpr int NS = (D + LPT - 1) / LPT;  // owned component slots per lane
+  constexpr int PAD = S + 1;               // padded smem row (bank spread)
+
+  __shared__ double s_eta[(LPT > 1) ? S * PAD : 1];
+  __shared__ double s_W[(LPT > 1) ? S * PAD : 1];
+  if constexpr (LPT > 1) {
+    for (int x = threadIdx.x; x < S * S; x += BLOCK) {
+      s_eta[(x / S) * PAD + (x % S)] = cf.eta[x];
+      s_W[(x / S) * PAD + (x % S)] = cf.W[x];
+    }
+    __syncthreads();
+  }
+
+  const int lane = threadIdx.x & 31;
+  const int r = lane % LPT;      // rank inside the trajectory's lane group
+  const int gbase = lane - r;    // first lane of the group
+  const int i0 = r * SPL;        // first stage held by this lane
+  const bool leader = (r == 0);
+
+  // eta_(i0+t, j) and W_(i0+t, j): constant-bank operands when one lane holds
+  // all stages (LPT == 1, indices known at compile time), padded shared
+  // memory rows otherwise.
+#define IRKGL_ETA(t, j) ((LPT == 1) ? cf.eta[(t) * S + (j)] : s_eta[(i0 + (t)) * PAD + (j)])
+#define IRKGL_W(t, j) ((LPT == 1) ? cf.W[(t) * S + (j)] : s_W[(i0 + (t)) * PAD + (j)])
+
+  double cc[SPL];
+#pragma unroll
+  for (int t = 0; t < SPL; t++) cc[t] = cf.c[i0 + t];
+
+  // per-trajectory state (uniform across the group's lanes unless noted)
+  Rhs rhs;
+  rhs.load_params(a.params);
+  double q[D], v[D];          // hi parts, replicated
+  double qlo[NS], vlo[NS];    // lo parts of the owned components l = s*LPT + r
+  double R[SPL][D];           // own stages' R (Rprev between steps)
+  double Q[SPL][D];           // own stages' values
+  double cv[SPL][D];          // c_i v
+  double h = 0.0, H0 = 0.0, invH0 = 0.0, dHmax = 0.0;
+  long long n = 0, N = 0, itot = 0;
+  int traj = -1, st = ST_OK;
+  bool active = false, exhausted = false;
+
+  // leaders of all groups in the warp
+  unsigned leaders_all = 0;
+#pragma unroll
+  for (int g = 0; g < 32; g += LPT) leaders_all |= 1u << g;
+
+  for (;;) {
+    // ---------------- refill: groups without a trajectory grab the next one
+    const bool need = !active && !exhausted;
+    const unsigned needmask = __ballot_sync(FULL, need) & leaders_all;
+    if (needmask) {
+      const int first = __ffs(needmask) - 1;
+      unsigned base = 0;
+      if (lane == first) base = atomicAdd(a.counter, static_cast<unsigned>(__popc(needmask)));
+      base = __shfl_sync(FULL, base, first);
+      if (need) {
+        const unsigned idx = base + __popc(needmask & ((1u << gbase) - 1u));
+        if (idx >= static_cast<unsigned>(a.batch)) {
+          exhausted = true;
+        } else {
+          int t = a.order ? a.order[idx] : static_cast<int>(idx);
+          if (t < 0 || t >= a.batch) {
+            t = -1;  // not a permutation entry: skip it
+          }
+          traj = t;
+          if (t >= 0) {
+            active = true;
+            st = ST_OK;
+            n = 0;
+            itot = 0;
+            dHmax = 0.0;
+            N = a.nsteps ? a.nsteps[t] : a.nsteps_all;
+            h = a.h ? a.h[t] : a.h_all;
+            const size_t off = static_cast<size_t>(t) * D;
+#pragma unroll
+            for (int l = 0; l < D; l++) {
+              q[l] = a.q_in[off + l];
+              v[l] = a.v_in[off + l];
+            }
+#pragma unroll
+            for (int s = 0; s < NS; s++) {
+              const int l = s * LPT + r;
+              qlo[s] = (a.qlo_in && l < D) ? a.qlo_in[off + l] : 0.0;
+              vlo[s] = (a.vlo_in && l < D) ? a.vlo_in[off + l] : 0.0;
+            }
+            const size_t roff = static_cast<size_t>(t) * S * D;
+#pragma unroll
+            for (int tt = 0; tt < SPL; tt++)
+#pragma unroll
+              for (int l = 0; l < D; l++)
+                R[tt][l] = a.rp_in ? a.rp_in[roff + (i0 + tt) * D + l] : 0.0;
+            double hb[SPL];
+#pragma unroll
+            for (int tt = 0; tt < SPL; tt++) hb[tt] = h * cf.b[i0 + tt];
+            rhs.set_step(hb);
+            if (a.monitor > 0) {
+              H0 = rhs.H(q, v);
+              invH0 = 1.0 / H0;
+            }
+          }
+        }
+      }
+    }
+    if (__all_sync(FULL, exhausted && !active)) break;
+
+    // ---------------- one step for every group that still has steps to take
+    const bool stepping = active && (n < N);
+    const unsigned stepmask = __ballot_sync(FULL, stepping);
+    if (stepping) {
+      // init (Eq. IRK_init2 in fused form): Q_i = q + h (c_i v + sum_k W_ik Rprev_k)
+#pragma unroll
+      for (int t = 0; t < SPL; t++)
+#pragma unroll
+        for (int l = 0; l < D; l++) cv[t][l] = cc[t] * v[l];
+#pragma unroll
+      for (int l = 0; l < D; l++) {
+        double acc[SPL];
+#pragma unroll
+        for (int t = 0; t < SPL; t++) acc[t] = cv[t][l];
+#pragma unroll
+        for (int j = 0; j < S; j++) {
+          double Rj;
+          if constexpr (LPT == 1) Rj = R[j][l];
+          else Rj = __shfl_sync(stepmask, R[j % SPL][l], gbase + j / SPL);
+#pragma unroll
+          for (int t = 0; t < SPL; t++) acc[t] = fma(IRKGL_W(t, j), Rj, acc[t]);
+        }
+#pragma unroll
+        for (int t = 0; t < SPL; t++) Q[t][l] = fma(h, acc[t], q[l]);
+      }
+
+      unsigned long long dmin[D], dprev[D];
+#pragma unroll
+      for (int l = 0; l < D; l++) {
+        dmin[l] = INF_BITS;
+        dprev[l] = INF_BITS;
+      }
+      int k = 0;
+      bool conv = false;
+      for (;;) {
+        const unsigned sweepmask = __ballot_sync(stepmask, !conv);
+        if (sweepmask == 0) break;
+        if (!conv) {
+          k++;
+          // R_i = h b_i g(Q_i) (Eq. Gi)
+#pragma unroll
+          for (int t = 0; t < SPL; t++) rhs.stage_R(t, Q[t], R[t]);
+          // Qn_i = q + h (c_i v + sum_j eta_ij R_j) (Eq. Qi2), Delta (Eq. Delta_n)
+          bool stop = true, bad = false;
+#pragma unroll
+          for (int l = 0; l < D; l++) {
+            double acc[SPL];
+#pragma unroll
+            for (int t = 0; t < SPL; t++) acc[t] = cv[t][l];
+#pragma unroll
+            for (int j = 0; j < S; j++) {
+              double Rj;
+              if constexpr (LPT == 1) Rj = R[j][l];
+              else Rj = __shfl_sync(sweepmask, R[j % SPL][l], gbase + j / SPL);
+#pragma unroll
+              for (int t = 0; t < SPL; t++) acc[t] = fma(IRKGL_ETA(t, j), Rj, acc[t]);
+            }
+            unsigned long long dl = 0;
+#pragma unroll
+            for (int t = 0; t < SPL; t++) {
+              const double qn = fma(h, acc[t], q[l]);
+              dl = umax64(dl, abs_bits(qn - Q[t][l]));
+              Q[t][l] = qn;
+            }
+#pragma unroll
+            for (int off = 1; off < LPT; off <<= 1)
+              dl = umax64(dl, __shfl_xor_sync(sweepmask, dl, off));
+            // Eq. stopping on this component (non-negative doubles order like
+            // their bit patterns; NaN/Inf patterns are >= INF_BITS)
+            bad = bad || (dl >= INF_BITS);
+            const bool cond = (dl == 0) || (dmin[l] <= umin64(dprev[l], dl));
+            stop = stop && cond;
+            dmin[l] = umin64(dmin[l], dprev[l]);
+            dprev[l] = dl;
+          }
+          if (bad) {
+            st = ST_NONFINITE;
+            conv = true;
+          } else if (stop) {
+            conv = true;
+          } else if (k >= a.kmax) {
+            st = ST_MAXITER;
+            conv = true;
+          }
+        }
+      }
+
+      if (a.iters_hist && leader && n < a.hist_len)
+        a.iters_hist[static_cast<size_t>(traj) * a.hist_len + n] = k;
+      itot += k;
+
+      const unsigned okmask = __ballot_sync(stepmask, st == ST_OK);
+      if (st == ST_OK) {
+        // update (Eq. qnvn2): sums over the stages, butterflied over the group
+        double sR[D], scR[D];
+#pragma unroll
+        for (int l = 0; l < D; l++) {
+          double x = R[0][l], y = cc[0] * R[0][l];
+#pragma unroll
+          for (int t = 1; t < SPL; t++) {
+            x = x + R[t][l];
+            y = fma(cc[t], R[t][l], y);
+          }
+#pragma unroll
+          for (int off = 1; off < LPT; off <<= 1) {
+            x = x + __shfl_xor_sync(okmask, x, off);
+            y = y + __shfl_xor_sync(okmask, y, off);
+          }
+          sR[l] = x;
+          scR[l] = y;
+        }
+        // compensated update of the owned components l = s*LPT + r
+        double nq[NS], nv[NS];
+#pragma unroll
+        for (int s = 0; s < NS; s++) {
+          double a_sR = sR[s * LPT], a_scR = scR[s * LPT], qh = q[s * LPT], vh = v[s * LPT];
+#pragma unroll
+          for (int rr = 1; rr < LPT; rr++) {
+            if (s * LPT + rr < D && r == rr) {
+              a_sR = sR[s * LPT + rr];
+              a_scR = scR[s * LPT + rr];
+              qh = q[s * LPT + rr];
+              vh = v[s * LPT + rr];
+            }
+          }
+          if (s * LPT + r < D) {
+            two_sum_add(vh, vlo[s], a_sR);
+            // dq = h v_hi + (h v_lo - h sum c_i R_i)
+            const double dq = fma(h, vh, fma(h, vlo[s], -(h * a_scR)));
+            two_sum_add(qh, qlo[s], dq);
+          }
+          nq[s] = qh;
+          nv[s] = vh;
+        }
+#pragma unroll
+        for (int l = 0; l < D; l++) {
+          if constexpr (LPT == 1) {
+            q[l] = nq[l];
+            v[l] = nv[l];
+          } else {
+            q[l] = __shfl_sync(okmask, nq[l / LPT], gbase + l % LPT);
+            v[l] = __shfl_sync(okmask, nv[l / LPT], gbase + l % LPT);
+          }
+        }
+        n++;
+        if (a.monitor > 0 && (n % a.monitor) == 0) {
+          const double Hn = rhs.H(q, v);
+          const double dH = fabs((Hn - H0) * invH0);
+          if (dH > dHmax) dHmax = dH;
+        }
+      }
+    }
+
+    // ---------------- finish: write outputs of completed/failed trajectories
+    const bool fin = active && (n >= N || st != ST_OK);
+    if (fin) {
+      const size_t off = static_cast<size_t>(traj) * D;
+#pragma unroll
+      for (int s = 0; s < NS; s++) {
+        const int l = s * LPT + r;
+        if (l < D) {
+          // owned components: hi parts from the replicated arrays
+          double qh = q[s * LPT], vh = v[s * LPT];
+#pragma unroll
+          for (int rr = 1; rr < LPT; rr++)
+            if (s * LPT + rr < D && r == rr) {
+              qh = q[s * LPT + rr];
+              vh = v[s * LPT + rr];
+            }
+          a.q_out[off + l] = qh;
+          a.v_out[off + l] = vh;
+          if (a.qlo_out) a.qlo_out[off + l] = qlo[s];
+          if (a.vlo_out) a.vlo_out[off + l] = vlo[s];
+        }
+      }
+      if (a.rp_out && st == ST_OK) {
+        const size_t roff = static_cast<size_t>(traj) * S * D;
+#pragma unroll
+        for (int tt = 0; tt < SPL; tt++)
+#pragma unroll
+          for (int l = 0; l < D; l++) a.rp_out[roff + (i0 + tt) * D + l] = R[tt][l];
+      }
+      if (leader) {
+        if (a.dH_max) a.dH_max[traj] = dHmax;
+        if (a.iters_total) a.iters_total[traj] = itot;
+        if (a.status) a.status[traj] = st;
+        if (a.steps_done) a.steps_done[traj] = n;
+      }
+      active = false;
+    }
+  }
+#undef IRKGL_ETA
+#undef IRKGL_W
+}
+
+}  // namespace irkgl

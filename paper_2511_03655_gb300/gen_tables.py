@@ -1,0 +1,177 @@
+"""Generate csrc/irkgl_tables.h: the FP64 IRKGL16 tables used by the kernels.
+
+    python -m paper_2511_03655_gb300.gen_tables          # rewrite the header
+    python -m paper_2511_03655_gb300.gen_tables --check  # verify it is current
+
+Route (arXiv 2511.03655, Sec. 2.2-2.4), in 90-digit ``decimal`` arithmetic:
+
+* Gauss nodes: zeros of the Legendre polynomial P_8, written out from its
+  explicit coefficients P_n(x) = 2^-n sum_k (-1)^k C(n,k) C(2n-2k,n) x^(n-2k)
+  and refined by Newton's method; c_i = (1 + x_i)/2.
+* Collocation coefficients by integrating the Lagrange basis l_j on c:
+  b_j = int_0^1 l_j, a_ij = int_0^{c_i} l_j (equivalent to the collocation
+  conditions of Sec. 2.2); the extrapolation weights of Eq. Pol0,
+  nut_ij = int_1^{1+c_i} l_j.
+* alpha = A A (Eq. Qi); eta_ij = fl(alpha_ij / b_j) for j <= i and
+  eta_ij = eta_ji + c_i - c_j for i < j, which makes Eq. sympl_cond_2 exact
+  over the FP64 numbers (the rule printed in Sec. 2.4 carries the opposite
+  sign and would violate Eq. sympl_cond_2); mu_ij = fl(a_ij / b_j) for
+  j <= i, mu_ij = 1 - mu_ji for i < j (Eq. Yi2); nu_ij = fl(nut_ij / b_j)
+  (Eq. IRK_init2 applies nu to L = h b F).
+* W = A nut diag(1/b), rounded once: the initial guess of Eq. IRK_init2,
+  Q_i = q + sum_j mu_ij h b_j (v + sum_k nu_jk R_k), equals
+  q + h (c_i v + sum_k W_ik R_k) in exact arithmetic, so the kernels form
+  it with one 8x8 mixing instead of two.
+
+Every value is rounded once with Python's correctly rounded float().
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+from decimal import Decimal, localcontext
+from fractions import Fraction
+from math import comb
+
+S = 8
+PREC = 90
+HERE = os.path.dirname(os.path.abspath(__file__))
+HEADER = os.path.join(HERE, "csrc", "irkgl_tables.h")
+
+
+def _legendre_coeffs(n):
+    """Monomial coefficients (highest degree first) of P_n, exact rationals."""
+    co = [Fraction(0)] * (n + 1)
+    for k in range(n // 2 + 1):
+        co[2 * k] = Fraction((-1) ** k * comb(n, k) * comb(2 * n - 2 * k, n), 2 ** n)
+    return co
+
+
+def _horner(co, x):
+    p = Decimal(0)
+    dp = Decimal(0)
+    for a in co:
+        dp = dp * x + p
+        p = p * x + Decimal(a.numerator) / Decimal(a.denominator)
+    return p, dp
+
+
+def gauss_nodes():
+    co = _legendre_coeffs(S)
+    xs = []
+    with localcontext() as ctx:
+        ctx.prec = PREC
+        for i in range(S):
+            # Chebyshev-Gauss points as starting values (distinct, interlaced)
+            import math
+            x = Decimal(repr(-math.cos(math.pi * (i + 0.5) / S)))
+            for _ in range(100):
+                p, dp = _horner(co, x)
+                step = p / dp
+                x -= step
+                if abs(step) < Decimal(10) ** (-(PREC - 4)):
+                    break
+            xs.append(x)
+        xs.sort()
+        return [(1 + x) / 2 for x in xs]
+
+
+def _basis_integrals(c, lo, hi):
+    """M[i][j] = int_{lo_i}^{hi_i} l_j(u) du."""
+    n = len(c)
+    out = [[Decimal(0)] * n for _ in range(n)]
+    for j in range(n):
+        poly = [Decimal(1)]  # lowest degree first
+        den = Decimal(1)
+        for m in range(n):
+            if m == j:
+                continue
+            nxt = [Decimal(0)] * (len(poly) + 1)
+            for p, a in enumerate(poly):
+                nxt[p + 1] += a
+                nxt[p] -= a * c[m]
+            poly = nxt
+            den *= c[j] - c[m]
+        prim = [Decimal(0)] + [a / (p + 1) for p, a in enumerate(poly)]
+
+        def F(u):
+            acc = Decimal(0)
+            for a in reversed(prim):
+                acc = acc * u + a
+            return acc
+
+        for i in range(n):
+            out[i][j] = (F(hi[i]) - F(lo[i])) / den
+    return out
+
+
+def tables():
+    with localcontext() as ctx:
+        ctx.prec = PREC
+        c = gauss_nodes()
+        zeros = [Decimal(0)] * S
+        ones = [Decimal(1)] * S
+        b = _basis_integrals(c, zeros, ones)[0]
+        A = _basis_integrals(c, zeros, c)
+        nut = _basis_integrals(c, ones, [1 + x for x in c])
+        alpha = [[sum(A[i][k] * A[k][j] for k in range(S)) for j in range(S)] for i in range(S)]
+        W = [[sum(A[i][j] * nut[j][k] for j in range(S)) / b[k] for k in range(S)] for i in range(S)]
+        cf = [float(x) for x in c]
+        bf = [float(x) for x in b]
+        mu = [[0.0] * S for _ in range(S)]
+        eta = [[0.0] * S for _ in range(S)]
+        for i in range(S):
+            for j in range(i + 1):
+                mu[i][j] = float(A[i][j] / b[j])
+                eta[i][j] = float(alpha[i][j] / b[j])
+        nu = [[float(nut[i][j] / b[j]) for j in range(S)] for i in range(S)]
+        Wf = [[float(W[i][k]) for k in range(S)] for i in range(S)]
+    for i in range(S):
+        for j in range(i + 1, S):
+            mu[i][j] = 1.0 - mu[j][i]
+            e = Fraction(eta[j][i]) + Fraction(cf[i]) - Fraction(cf[j])
+            eta[i][j] = float(e)
+            assert Fraction(eta[i][j]) == e, "eta upper triangle not representable"
+    return {"c": cf, "b": bf, "mu": mu, "eta": eta, "nu": nu, "W": Wf}
+
+
+def render(t) -> str:
+    def arr1(name, v):
+        return f"static const double {name}[8] = {{\n  " + ",\n  ".join(float.hex(x) for x in v) + "};\n"
+
+    def arr2(name, m):
+        rows = ",\n  ".join(", ".join(float.hex(x) for x in row) for row in m)
+        return f"static const double {name}[64] = {{\n  {rows}}};\n"
+
+    out = ["/* Generated by paper_2511_03655_gb300/gen_tables.py -- do not edit.",
+           " * IRKGL16 FP64 tables (arXiv 2511.03655 Sec. 2.2-2.4), row-major [i*8+j]:",
+           " * c, b: nodes and weights; MU (Eq. Yi2); ETA (Eq. Qi2, Eq. sympl_cond_2 exact);",
+           " * NU (Eq. Pol0, scaled by 1/b); W = A nut diag(1/b) (fused initial guess). */",
+           "#pragma once", ""]
+    out.append(arr1("IRKGL_TAB_C", t["c"]))
+    out.append(arr1("IRKGL_TAB_B", t["b"]))
+    out.append(arr2("IRKGL_TAB_MU", t["mu"]))
+    out.append(arr2("IRKGL_TAB_ETA", t["eta"]))
+    out.append(arr2("IRKGL_TAB_NU", t["nu"]))
+    out.append(arr2("IRKGL_TAB_W", t["W"]))
+    return "\n".join(out)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--check", action="store_true")
+    a = ap.parse_args(argv)
+    text = render(tables())
+    if a.check:
+        with open(HEADER) as f:
+            ok = f.read() == text
+        print("irkgl_tables.h is", "current" if ok else "STALE")
+        return 0 if ok else 1
+    with open(HEADER, "w") as f:
+        f.write(text)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

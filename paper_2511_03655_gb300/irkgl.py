@@ -1,0 +1,306 @@
+"""Python binding of libirkgl.so (include/irkgl.h): argument marshalling only.
+
+Every step of the integration runs in the library's CUDA kernels; this
+module only turns torch tensors (device memory, streams) into the plain
+pointers and sizes of the C-ABI.  It raises if the library is not built or
+cannot be loaded: there is no CPU fallback.
+
+The functions below keep the C names (``irkgl_create``, ``irkgl_step``,
+``irkgl_integrate``, ...); ``Integrator`` is a small convenience wrapper.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+from . import build as _build
+
+OK = 0
+ERR_INVALID, ERR_NOMEM, ERR_CUDA, ERR_UNSUPPORTED = -1, -2, -3, -4
+STATUS_OK, STATUS_MAXITER, STATUS_NONFINITE = 0, 1, 2
+RHS_KEPLER, RHS_NBODY, RHS_FPUT, RHS_HENON_HEILES, RHS_HARMONIC = 1, 2, 3, 4, 5
+OPT_LANES_PER_TRAJ, OPT_KMAX, OPT_MONITOR_EVERY, OPT_BLOCK_THREADS, OPT_GRID_BLOCKS = 1, 2, 3, 4, 5
+
+EXPORTS = ("irkgl_default_coeffs", "irkgl_create", "irkgl_set_option", "irkgl_step",
+           "irkgl_integrate", "irkgl_integrate_host", "irkgl_destroy", "irkgl_strerror",
+           "irkgl_last_cuda_error", "irkgl_get_tile", "irkgl_probe_fp64_fma")
+
+_P = ctypes.c_void_p
+
+
+class IrkglError(RuntimeError):
+    pass
+
+
+class irkgl_rhs(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("params", ctypes.POINTER(ctypes.c_double)),
+                ("nparams", ctypes.c_int)]
+
+
+class irkgl_coeffs(ctypes.Structure):
+    _fields_ = [("c", ctypes.c_double * 8), ("b", ctypes.c_double * 8),
+                ("mu", ctypes.c_double * 64), ("eta", ctypes.c_double * 64),
+                ("nu", ctypes.c_double * 64)]
+
+
+class irkgl_outputs(ctypes.Structure):
+    _fields_ = [("q", _P), ("v", _P), ("q_lo", _P), ("v_lo", _P), ("r_prev", _P),
+                ("dH_max", _P), ("iters", _P), ("steps", _P), ("status", _P)]
+
+
+_lib = None
+
+
+def load(path: str | None = None, build_if_missing: bool = False):
+    """Load libirkgl.so (in-tree build).  Raises IrkglError if it is absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        if build_if_missing:
+            _build.build()
+        else:
+            raise IrkglError(f"{path} is missing: run __graft_entry__.build() or "
+                             "python -m paper_2511_03655_gb300.build")
+    L = ctypes.CDLL(path)
+    L.irkgl_default_coeffs.argtypes = [ctypes.POINTER(irkgl_coeffs)]
+    L.irkgl_create.argtypes = [ctypes.POINTER(_P), irkgl_rhs, ctypes.c_int, ctypes.c_double,
+                               ctypes.POINTER(irkgl_coeffs)]
+    L.irkgl_set_option.argtypes = [_P, ctypes.c_int, ctypes.c_longlong]
+    L.irkgl_step.argtypes = [_P, _P, _P, _P, _P, _P, _P, ctypes.c_int, ctypes.c_int, _P, _P, _P]
+    L.irkgl_integrate.argtypes = [_P, _P, _P, ctypes.c_int, _P, ctypes.c_longlong, _P, _P,
+                                  ctypes.POINTER(irkgl_outputs), _P]
+    L.irkgl_integrate_host.argtypes = L.irkgl_integrate.argtypes
+    L.irkgl_destroy.argtypes = [_P]
+    L.irkgl_destroy.restype = None
+    L.irkgl_strerror.argtypes = [ctypes.c_int]
+    L.irkgl_strerror.restype = ctypes.c_char_p
+    L.irkgl_last_cuda_error.argtypes = []
+    L.irkgl_last_cuda_error.restype = ctypes.c_char_p
+    L.irkgl_get_tile.argtypes = [_P]
+    L.irkgl_probe_fp64_fma.argtypes = [_P, ctypes.POINTER(ctypes.c_longlong), _P]
+    for name in ("irkgl_default_coeffs", "irkgl_create", "irkgl_set_option", "irkgl_step",
+                 "irkgl_integrate", "irkgl_integrate_host", "irkgl_get_tile",
+                 "irkgl_probe_fp64_fma"):
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(rc: int):
+    if rc < 0:
+        L = load()
+        msg = L.irkgl_strerror(rc).decode()
+        if rc == ERR_CUDA:
+            msg += ": " + L.irkgl_last_cuda_error().decode()
+        raise IrkglError(f"libirkgl error {rc}: {msg}")
+    return rc
+
+
+def _ptr(t: torch.Tensor | None, dtype, shape=None, name="array", device=True):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if device and not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not device and t.is_cuda:
+        raise ValueError(f"{name} must be a host tensor")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return _P(t.data_ptr())
+
+
+def _stream(stream) -> _P:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return _P(stream.cuda_stream)
+
+
+# ---------------------------------------------------------------- C names
+def irkgl_default_coeffs() -> dict:
+    c = irkgl_coeffs()
+    _check(load().irkgl_default_coeffs(ctypes.byref(c)))
+    return {"c": list(c.c), "b": list(c.b),
+            "mu": [list(c.mu[i * 8:(i + 1) * 8]) for i in range(8)],
+            "eta": [list(c.eta[i * 8:(i + 1) * 8]) for i in range(8)],
+            "nu": [list(c.nu[i * 8:(i + 1) * 8]) for i in range(8)]}
+
+
+def irkgl_create(kind: int, params, dim: int, h: float, coeffs: dict | None = None) -> int:
+    L = load()
+    arr = (ctypes.c_double * len(params))(*[float(x) for x in params])
+    f = irkgl_rhs(kind, ctypes.cast(arr, ctypes.POINTER(ctypes.c_double)), len(params))
+    ctx = _P()
+    cref = None
+    if coeffs is not None:
+        cref = irkgl_coeffs()
+        for i in range(8):
+            cref.c[i] = coeffs["c"][i]
+            cref.b[i] = coeffs["b"][i]
+            for j in range(8):
+                cref.mu[i * 8 + j] = coeffs["mu"][i][j]
+                cref.eta[i * 8 + j] = coeffs["eta"][i][j]
+                cref.nu[i * 8 + j] = coeffs["nu"][i][j]
+        cref = ctypes.byref(cref)
+    _check(L.irkgl_create(ctypes.byref(ctx), f, dim, float(h), cref))
+    return ctx.value
+
+
+def irkgl_set_option(ctx: int, option: int, value: int):
+    _check(load().irkgl_set_option(_P(ctx), option, int(value)))
+
+
+def irkgl_get_tile(ctx: int) -> int:
+    return _check(load().irkgl_get_tile(_P(ctx)))
+
+
+def irkgl_probe_fp64_fma(scratch: torch.Tensor, stream=None) -> int:
+    """Launch the FP64 FMA throughput probe; returns the FMA count issued."""
+    n = ctypes.c_longlong(0)
+    _check(load().irkgl_probe_fp64_fma(_ptr(scratch, torch.float64, None, "scratch"),
+                                       ctypes.byref(n), _stream(stream)))
+    return n.value
+
+
+def irkgl_destroy(ctx: int):
+    load().irkgl_destroy(_P(ctx))
+
+
+def irkgl_strerror(code: int) -> str:
+    return load().irkgl_strerror(code).decode()
+
+
+def irkgl_step(ctx: int, dim: int, q, v, q_lo=None, v_lo=None, r_prev=None, h=None,
+               nsteps: int = 1, iters=None, status=None, stream=None):
+    """Advance in place (device tensors): q, v [B, dim]; q_lo, v_lo [B, dim];
+    r_prev [B, 8, dim]; h [B]; iters int32 [B, nsteps]; status int32 [B]."""
+    B = q.shape[0]
+    f64, i32 = torch.float64, torch.int32
+    _check(load().irkgl_step(
+        _P(ctx), _ptr(q, f64, (B, dim), "q"), _ptr(v, f64, (B, dim), "v"),
+        _ptr(q_lo, f64, (B, dim), "q_lo"), _ptr(v_lo, f64, (B, dim), "v_lo"),
+        _ptr(r_prev, f64, (B, 8, dim), "r_prev"), _ptr(h, f64, (B,), "h"),
+        B, int(nsteps), _ptr(iters, i32, (B, nsteps), "iters"), _ptr(status, i32, (B,), "status"),
+        _stream(stream)))
+
+
+@dataclass
+class Outputs:
+    q: torch.Tensor
+    v: torch.Tensor
+    q_lo: torch.Tensor | None = None
+    v_lo: torch.Tensor | None = None
+    r_prev: torch.Tensor | None = None
+    dH_max: torch.Tensor | None = None
+    iters: torch.Tensor | None = None
+    steps: torch.Tensor | None = None
+    status: torch.Tensor | None = None
+
+    @staticmethod
+    def allocate(batch: int, dim: int, device="cuda", full: bool = True, pin: bool = False):
+        kw = dict(device=device)
+        if pin:
+            kw["pin_memory"] = True
+        z = lambda shape, dt: torch.empty(shape, dtype=dt, **kw)  # noqa: E731
+        o = Outputs(q=z((batch, dim), torch.float64), v=z((batch, dim), torch.float64))
+        if full:
+            o.q_lo = z((batch, dim), torch.float64)
+            o.v_lo = z((batch, dim), torch.float64)
+            o.r_prev = z((batch, 8, dim), torch.float64)
+            o.dH_max = z((batch,), torch.float64)
+            o.iters = z((batch,), torch.int64)
+            o.steps = z((batch,), torch.int64)
+            o.status = z((batch,), torch.int32)
+        return o
+
+    def _struct(self, batch, dim, device=True):
+        f64, i64, i32 = torch.float64, torch.int64, torch.int32
+        return irkgl_outputs(
+            _ptr(self.q, f64, (batch, dim), "out.q", device), _ptr(self.v, f64, (batch, dim), "out.v", device),
+            _ptr(self.q_lo, f64, (batch, dim), "out.q_lo", device),
+            _ptr(self.v_lo, f64, (batch, dim), "out.v_lo", device),
+            _ptr(self.r_prev, f64, (batch, 8, dim), "out.r_prev", device),
+            _ptr(self.dH_max, f64, (batch,), "out.dH_max", device),
+            _ptr(self.iters, i64, (batch,), "out.iters", device),
+            _ptr(self.steps, i64, (batch,), "out.steps", device),
+            _ptr(self.status, i32, (batch,), "out.status", device))
+
+
+def irkgl_integrate(ctx: int, dim: int, q0, v0, out: Outputs, nsteps=None, nsteps_all: int = 0,
+                    h=None, order=None, stream=None):
+    """Device tensors: q0, v0 [B, dim]; nsteps int64 [B] (or nsteps_all);
+    h [B]; order int32 [B]."""
+    B = q0.shape[0]
+    f64 = torch.float64
+    st = out._struct(B, dim)
+    _check(load().irkgl_integrate(
+        _P(ctx), _ptr(q0, f64, (B, dim), "q0"), _ptr(v0, f64, (B, dim), "v0"), B,
+        _ptr(nsteps, torch.int64, (B,), "nsteps"), int(nsteps_all), _ptr(h, f64, (B,), "h"),
+        _ptr(order, torch.int32, (B,), "order"), ctypes.byref(st), _stream(stream)))
+
+
+def irkgl_integrate_host(ctx: int, dim: int, q0, v0, out: Outputs, nsteps=None,
+                         nsteps_all: int = 0, h=None, order=None, stream=None):
+    """Host (CPU, ideally pinned) tensors; synchronous; copies inside the call."""
+    B = q0.shape[0]
+    f64 = torch.float64
+    st = out._struct(B, dim, device=False)
+    _check(load().irkgl_integrate_host(
+        _P(ctx), _ptr(q0, f64, (B, dim), "q0", False), _ptr(v0, f64, (B, dim), "v0", False), B,
+        _ptr(nsteps, torch.int64, (B,), "nsteps", False), int(nsteps_all),
+        _ptr(h, f64, (B,), "h", False), _ptr(order, torch.int32, (B,), "order", False),
+        ctypes.byref(st), _stream(stream)))
+
+
+class Integrator:
+    """Owns one irkgl context (right-hand side, dimension, default step)."""
+
+    def __init__(self, kind: int, params, dim: int, h: float, coeffs: dict | None = None,
+                 lanes_per_traj: int = 0, kmax: int = 100, monitor_every: int = 1,
+                 block_threads: int = 128):
+        self.dim = dim
+        self.ctx = irkgl_create(kind, params, dim, h, coeffs)
+        self.set(OPT_LANES_PER_TRAJ, lanes_per_traj)
+        self.set(OPT_KMAX, kmax)
+        self.set(OPT_MONITOR_EVERY, monitor_every)
+        self.set(OPT_BLOCK_THREADS, block_threads)
+
+    def set(self, option, value):
+        irkgl_set_option(self.ctx, option, value)
+
+    @property
+    def tile(self) -> int:
+        return irkgl_get_tile(self.ctx)
+
+    def step(self, *args, **kw):
+        return irkgl_step(self.ctx, self.dim, *args, **kw)
+
+    def integrate(self, q0, v0, out=None, **kw) -> Outputs:
+        out = out or Outputs.allocate(q0.shape[0], self.dim, device=q0.device)
+        irkgl_integrate(self.ctx, self.dim, q0, v0, out, **kw)
+        return out
+
+    def integrate_host(self, q0, v0, out=None, **kw) -> Outputs:
+        out = out or Outputs.allocate(q0.shape[0], self.dim, device="cpu")
+        irkgl_integrate_host(self.ctx, self.dim, q0, v0, out, **kw)
+        return out
+
+    def close(self):
+        if self.ctx:
+            irkgl_destroy(self.ctx)
+            self.ctx = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
