@@ -181,6 +181,39 @@ int irkgl_get_tile(struct irkgl_ctx* ctx);
  * used for the roofline fraction.  Errors: IRKGL_ERR_INVALID, IRKGL_ERR_CUDA. */
 int irkgl_probe_fp64_fma(double* scratch, long long* fma_count, void* cuda_stream);
 
+/* Integration for callers that cannot allocate device memory.  (The paper
+ * has no counterpart: this is a deployment entry point.)
+ *
+ * Some callers cannot call cudaMalloc: applications that reserve nearly all
+ * device memory for their own pool up front, real-time or certified code
+ * that forbids allocation after start-up, and plug-ins that must not touch
+ * the device heap of the host application.  This call does the work of
+ * irkgl_create(f, dim, h, NULL) + irkgl_integrate(...) + irkgl_destroy with
+ * the default tables and options (default tile, 128 threads per block,
+ * sweep cap 100, energy monitor every step), and allocates nothing: no
+ * context, no cudaMalloc/cudaFree.  The caller passes every input and output
+ * (device pointers, as for irkgl_integrate; f.params is a host pointer).
+ *
+ * Its scratch (the persistent grid's work counter and a copy of f.params)
+ * is a fixed array of 64 doubles (512 bytes) inside the library, held by
+ * every GPU that loads the library until the process exits.  All calls
+ * share it and it keeps the last call's contents: each call clears the
+ * counter and rewrites the parameters before launching, so calls that
+ * overlap on the GPU race on it; serialise them (one stream, or ordering
+ * between streams).  The first call on a device looks up the array's device
+ * address for that device (cudaGetSymbolAddress); make that first call
+ * before any stream capture on that device.
+ *
+ * Errors: IRKGL_ERR_INVALID for the same argument errors as irkgl_create /
+ * irkgl_integrate, and when f.nparams > IRKGL_NOALLOC_MAX_PARAMS (the
+ * parameters must fit the fixed scratch); IRKGL_ERR_UNSUPPORTED;
+ * IRKGL_ERR_CUDA. */
+#define IRKGL_NOALLOC_MAX_PARAMS 63
+int irkgl_integrate_noalloc(irkgl_rhs f, int dim, double h, const double* q0, const double* v0,
+                            int batch, const long long* nsteps, long long nsteps_all,
+                            const double* h_per_traj, const int* order,
+                            const irkgl_outputs* out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

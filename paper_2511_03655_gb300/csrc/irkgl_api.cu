@@ -469,3 +469,123 @@ int irkgl_integrate_host(irkgl_ctx* c, const double* q0, const double* v0, int b
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Integration without any device allocation.
+//
+// Some callers cannot call cudaMalloc: hosts that reserve (nearly) all device
+// memory for their own pool allocator up front, real-time or certified code
+// that forbids allocation after start-up, and plug-ins that must not touch
+// the device heap of the application that loads them.  For them,
+// irkgl_integrate_noalloc runs the same batched kernel as irkgl_integrate
+// with default options, but its scratch (the work counter that hands
+// trajectories to the persistent grid, and the right-hand-side parameters)
+// lives in the file-scope array below instead of in a context.
+//
+// The array is fixed at 64 doubles (512 bytes) and belongs to the library
+// image: every GPU that loads the library holds it until the process exits.
+// All calls share it and it keeps the last call's contents; each call resets
+// the counter and rewrites the parameters before its launch, so calls that
+// overlap on the GPU (different streams without ordering, or different host
+// threads on one device) race on it and must be serialised by the caller.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kNoallocScratchDoubles = 64;  // word 0: work counter; words 1..63: parameters
+static __device__ __align__(256) double g_irkgl_noalloc_scratch[kNoallocScratchDoubles];
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[kNoallocMaxDevices] = {nullptr};
+
+// Device address of the scratch array on the current device, looked up once
+// per device (host code sees only a host-side stand-in for the symbol).
+int noalloc_scratch(double** out) {
+  int dev = 0;
+  IRKGL_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoallocMaxDevices) return IRKGL_ERR_INVALID;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    IRKGL_CUDA(cudaGetSymbolAddress(&p, g_irkgl_noalloc_scratch));
+    g_noalloc_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return IRKGL_OK;
+}
+
+}  // namespace
+
+extern "C" int irkgl_integrate_noalloc(irkgl_rhs f, int dim, double h, const double* q0,
+                                       const double* v0, int batch, const long long* nsteps,
+                                       long long nsteps_all, const double* h_per_traj,
+                                       const int* order, const irkgl_outputs* out,
+                                       void* stream) {
+  if (batch < 0 || !out) return IRKGL_ERR_INVALID;
+  if (!std::isfinite(h) || h == 0.0) return IRKGL_ERR_INVALID;
+  int rc = check_rhs(f, dim);
+  if (rc != IRKGL_OK) return rc;
+  if (f.nparams > IRKGL_NOALLOC_MAX_PARAMS) return IRKGL_ERR_INVALID;  // beyond the scratch capacity
+  if (batch == 0) return IRKGL_OK;
+  if (!q0 || !v0 || !out->q || !out->v) return IRKGL_ERR_INVALID;
+  if (!nsteps && nsteps_all < 0) return IRKGL_ERR_INVALID;
+  const int lpt = default_lpt(f.kind, dim);
+  const int block = 128;
+  const KernelEntry* ke = lpt ? find_kernel(f.kind, dim, lpt, block) : nullptr;
+  if (!ke) return IRKGL_ERR_UNSUPPORTED;
+
+  double* scratch = nullptr;
+  rc = noalloc_scratch(&scratch);
+  if (rc != IRKGL_OK) return rc;
+  int dev = 0, sms = 0, per_sm = 0;
+  IRKGL_CUDA(cudaGetDevice(&dev));
+  IRKGL_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  IRKGL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ke->fn, block, 0));
+  if (per_sm < 1) per_sm = 1;
+
+  Coef coef;
+  for (int i = 0; i < 8; i++) {
+    coef.c[i] = IRKGL_TAB_C[i];
+    coef.b[i] = IRKGL_TAB_B[i];
+  }
+  for (int x = 0; x < 64; x++) {
+    coef.eta[x] = IRKGL_TAB_ETA[x];
+    coef.W[x] = IRKGL_TAB_W[x];
+  }
+  KArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.batch = batch;
+  a.kmax = 100;
+  a.monitor = 1;
+  a.q_in = q0;
+  a.v_in = v0;
+  a.q_out = out->q;
+  a.v_out = out->v;
+  a.qlo_out = out->q_lo;
+  a.vlo_out = out->v_lo;
+  a.rp_out = out->r_prev;
+  a.nsteps = nsteps;
+  a.nsteps_all = nsteps_all;
+  a.h = h_per_traj;
+  a.h_all = h;
+  a.order = order;
+  a.iters_total = out->iters;
+  a.dH_max = out->dH_max;
+  a.status = out->status;
+  a.steps_done = out->steps;
+  a.counter = reinterpret_cast<unsigned*>(scratch);  // word 0, cleared below
+  a.params = scratch + 1;
+
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  IRKGL_CUDA(cudaMemsetAsync(scratch, 0, sizeof(double), st));
+  IRKGL_CUDA(cudaMemcpyAsync(scratch + 1, f.params, sizeof(double) * f.nparams,
+                             cudaMemcpyHostToDevice, st));
+  const int traj_per_block = block / lpt;
+  const long long need = (static_cast<long long>(batch) + traj_per_block - 1) / traj_per_block;
+  int grid = per_sm * sms;
+  if (grid > need) grid = static_cast<int>(need);
+  if (grid < 1) grid = 1;
+  ke->launch(dim3(grid), dim3(block), st, a, coef);
+  IRKGL_CUDA(cudaGetLastError());
+  return IRKGL_OK;
+}

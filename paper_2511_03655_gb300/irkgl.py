@@ -26,7 +26,9 @@ OPT_LANES_PER_TRAJ, OPT_KMAX, OPT_MONITOR_EVERY, OPT_BLOCK_THREADS, OPT_GRID_BLO
 
 EXPORTS = ("irkgl_default_coeffs", "irkgl_create", "irkgl_set_option", "irkgl_step",
            "irkgl_integrate", "irkgl_integrate_host", "irkgl_destroy", "irkgl_strerror",
-           "irkgl_last_cuda_error", "irkgl_get_tile", "irkgl_probe_fp64_fma")
+           "irkgl_last_cuda_error", "irkgl_get_tile", "irkgl_probe_fp64_fma",
+           "irkgl_integrate_noalloc")
+NOALLOC_MAX_PARAMS = 63
 
 _P = ctypes.c_void_p
 
@@ -83,9 +85,12 @@ def load(path: str | None = None, build_if_missing: bool = False):
     L.irkgl_last_cuda_error.restype = ctypes.c_char_p
     L.irkgl_get_tile.argtypes = [_P]
     L.irkgl_probe_fp64_fma.argtypes = [_P, ctypes.POINTER(ctypes.c_longlong), _P]
+    L.irkgl_integrate_noalloc.argtypes = [irkgl_rhs, ctypes.c_int, ctypes.c_double, _P, _P,
+                                          ctypes.c_int, _P, ctypes.c_longlong, _P, _P,
+                                          ctypes.POINTER(irkgl_outputs), _P]
     for name in ("irkgl_default_coeffs", "irkgl_create", "irkgl_set_option", "irkgl_step",
                  "irkgl_integrate", "irkgl_integrate_host", "irkgl_get_tile",
-                 "irkgl_probe_fp64_fma"):
+                 "irkgl_probe_fp64_fma", "irkgl_integrate_noalloc"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -259,6 +264,28 @@ def irkgl_integrate_host(ctx: int, dim: int, q0, v0, out: Outputs, nsteps=None,
         _ptr(nsteps, torch.int64, (B,), "nsteps", False), int(nsteps_all),
         _ptr(h, f64, (B,), "h", False), _ptr(order, torch.int32, (B,), "order", False),
         ctypes.byref(st), _stream(stream)))
+
+
+def irkgl_integrate_noalloc(kind: int, params, dim: int, h: float, q0, v0, out: Outputs,
+                            nsteps=None, nsteps_all: int = 0, h_per_traj=None, order=None,
+                            stream=None) -> int:
+    """Context-free integration that allocates nothing on the device (see
+    irkgl.h).  Device tensors as for irkgl_integrate; returns the C code
+    (raises on errors other than IRKGL_ERR_INVALID, which is returned so
+    callers can see the capacity check)."""
+    B = q0.shape[0]
+    f64 = torch.float64
+    arr = (ctypes.c_double * len(params))(*[float(x) for x in params])
+    f = irkgl_rhs(kind, ctypes.cast(arr, ctypes.POINTER(ctypes.c_double)), len(params))
+    st = out._struct(B, dim)
+    rc = load().irkgl_integrate_noalloc(
+        f, dim, float(h), _ptr(q0, f64, (B, dim), "q0"), _ptr(v0, f64, (B, dim), "v0"), B,
+        _ptr(nsteps, torch.int64, (B,), "nsteps"), int(nsteps_all),
+        _ptr(h_per_traj, f64, (B,), "h_per_traj"), _ptr(order, torch.int32, (B,), "order"),
+        ctypes.byref(st), _stream(stream))
+    if rc != ERR_INVALID:
+        _check(rc)
+    return rc
 
 
 class Integrator:
