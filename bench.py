@@ -42,6 +42,10 @@ TOL = 1e-13
 #   per fixed-point sweep (8 stages): g and R 120 + mixing 288 + Delta 16
 FLOPS_PER_STEP = 413
 FLOPS_PER_SWEEP = 424
+# Same count for the 6-body ensemble (d = 18, 15 pairs, energy split over the
+# lane group): per step init 2736 + update 810 + energy 336; per sweep
+# pairwise g and R 3720 + mixing 2592 + Delta 144.
+FLOPS_NBODY6 = (3882, 6456)
 
 # DRAM traffic of the batched kernel from the committed ncu capture, valid only
 # for the kernel source it was taken on (sha256 prefix of irkgl_device.cuh).
@@ -60,6 +64,10 @@ def parse():
     ap.add_argument("--lanes", type=int, default=0, help="lanes per trajectory (0 = library default)")
     ap.add_argument("--no-order", action="store_true", help="natural order instead of similarity order")
     ap.add_argument("--skip-extras", action="store_true", help="skip e2e, plain form and CPU baseline")
+    ap.add_argument("--workload", default="kepler", choices=["kepler", "nbody6"],
+                    help="kepler: the 65,536-orbit ensemble (default); nbody6: 16,384 perturbed "
+                         "copies of a 6-body system")
+    ap.add_argument("--traj-steps", type=int, default=100000, help="steps per copy for nbody6")
     return ap.parse_args()
 
 
@@ -227,16 +235,28 @@ def main():
         return float(t.item())
 
     # ---- workload (rank r draws its own ensemble; rank 0 is the standard one)
-    w = workloads.kepler_ensemble(batch=args.batch, periods=args.periods, seed_id=2 + 1000 * rank)
-    order = (np.arange(args.batch, dtype=np.int32) if args.no_order
-             else workloads.similarity_order(w["e"]))
+    if args.workload == "kepler":
+        w = workloads.kepler_ensemble(batch=args.batch, periods=args.periods, seed_id=2 + 1000 * rank)
+        order = (np.arange(args.batch, dtype=np.int32) if args.no_order
+                 else workloads.similarity_order(w["e"]))
+        kind, fps, fpw = irkgl.RHS_KEPLER, FLOPS_PER_STEP, FLOPS_PER_SWEEP
+        desc = (f"kepler_ensemble B={args.batch} per GPU, e~U[0,0.9), {args.periods} periods, "
+                "h=2pi/round(200+100e), one persistent launch")
+    else:
+        args.batch = min(args.batch, 16384)
+        w = workloads.nbody_ensemble(copies=args.batch, steps=args.traj_steps, seed_id=3 + 1000 * rank)
+        order = np.arange(args.batch, dtype=np.int32)
+        kind, (fps, fpw) = irkgl.RHS_NBODY, FLOPS_NBODY6
+        desc = (f"nbody6_ensemble: {args.batch} copies (1e-8 perturbations) of a 6-body system, "
+                f"h=0.5% of the innermost period, {args.traj_steps} steps, one persistent launch")
+    dim = w["dim"]
     q0 = torch.tensor(w["q0"], device=dev)
     v0 = torch.tensor(w["v0"], device=dev)
     ns = torch.tensor(w["nsteps"], device=dev)
     hh = torch.tensor(w["h"], device=dev)
     od = torch.tensor(order, device=dev)
-    integ = irkgl.Integrator(irkgl.RHS_KEPLER, [1.0], 2, float(w["h"][0]), lanes_per_traj=args.lanes)
-    out = irkgl.Outputs.allocate(args.batch, 2, device=dev)
+    integ = irkgl.Integrator(kind, w["params"], dim, float(w["h"][0]), lanes_per_traj=args.lanes)
+    out = irkgl.Outputs.allocate(args.batch, dim, device=dev)
 
     # ---- FP64 roof: the library's FMA-chain probe, timed on this stream
     scratch = torch.zeros(1, dtype=torch.float64, device=dev)
@@ -290,7 +310,7 @@ def main():
     value = args.steps * steps_ok / t_max
     value_all = args.steps * steps_all / t_max
 
-    flops_launch = FLOPS_PER_STEP * float(steps.sum()) + FLOPS_PER_SWEEP * float(iters.sum())
+    flops_launch = fps * float(steps.sum()) + fpw * float(iters.sum())
     achieved = flops_launch / statistics.mean(times) / 1e12
     traffic = NCU_TRAFFIC_BYTES_PER_LAUNCH if NCU_KERNEL_SHA == kernel_sha() else None
 
@@ -299,9 +319,8 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": f"kepler_ensemble B={args.batch} per GPU, e~U[0,0.9), "
-                               f"{args.periods} periods, h=2pi/round(200+100e), one persistent launch",
-                   "batch_per_gpu": args.batch, "periods": args.periods,
+        "config": {"workload": desc, "batch_per_gpu": args.batch,
+                   "periods": args.periods if args.workload == "kepler" else None,
                    "lanes_per_traj": integ.tile,
                    "order": "natural" if args.no_order else "similarity (e descending)",
                    "l2": "state ~12.6 MB < L2; L2 flushed with a 256 MiB write before every timed step",
@@ -316,19 +335,19 @@ def main():
                      "frac": achieved / peak_tflops, "traffic": traffic,
                      "peak_source": "FP64 FMA-chain probe (irkgl_probe_fp64_fma) measured live, "
                                     "2 flops per FMA",
-                     "kernel": "irkgl_kernel<Kepler>", "flops_per_launch": flops_launch},
+                     "kernel": f"irkgl_kernel<{args.workload}>", "flops_per_launch": flops_launch},
         "clocks": clk,
     }
 
-    if not args.skip_extras:
+    if not args.skip_extras and args.workload == "kepler":
         # ---- e2e: the host-buffer C-ABI call, copies inside the timed region
         hq0 = torch.tensor(w["q0"]).pin_memory()
         hv0 = torch.tensor(w["v0"]).pin_memory()
         hns = torch.tensor(w["nsteps"]).pin_memory()
         hh_ = torch.tensor(w["h"]).pin_memory()
         hod = torch.tensor(order).pin_memory()
-        hout = irkgl.Outputs(q=torch.empty((args.batch, 2), dtype=torch.float64).pin_memory(),
-                             v=torch.empty((args.batch, 2), dtype=torch.float64).pin_memory(),
+        hout = irkgl.Outputs(q=torch.empty((args.batch, dim), dtype=torch.float64).pin_memory(),
+                             v=torch.empty((args.batch, dim), dtype=torch.float64).pin_memory(),
                              dH_max=torch.empty(args.batch, dtype=torch.float64).pin_memory(),
                              iters=torch.empty(args.batch, dtype=torch.int64).pin_memory(),
                              steps=torch.empty(args.batch, dtype=torch.int64).pin_memory(),

@@ -14,7 +14,7 @@
 #include <mutex>
 
 #include "irkgl.h"
-#include "irkgl_device.cuh"
+#include "irkgl_kernels.h"
 #include "irkgl_tables.h"
 
 using irkgl::Coef;
@@ -35,64 +35,16 @@ int cuda_fail(cudaError_t e) {
     if (e_ != cudaSuccess) return cuda_fail(e_); \
   } while (0)
 
-typedef void (*kernel_fn)(KArgs, Coef);
-
-struct KernelEntry {
-  int kind;
-  int dim;
-  int lpt;
-  int block;
-  const void* fn;
-  void (*launch)(dim3, dim3, cudaStream_t, const KArgs&, const Coef&);
-};
-
-template <class Rhs, int LPT, int BLOCK>
-void launch_impl(dim3 grid, dim3 block, cudaStream_t st, const KArgs& a, const Coef& c) {
-  irkgl::irkgl_kernel<Rhs, LPT, BLOCK><<<grid, block, 0, st>>>(a, c);
-}
-
-#define IRKGL_ENTRY(KIND, DIM, RHS, LPT, BLOCK)                                        \
-  KernelEntry {                                                                        \
-    KIND, DIM, LPT, BLOCK, (const void*)irkgl::irkgl_kernel<RHS, LPT, BLOCK>,         \
-        launch_impl<RHS, LPT, BLOCK>                                                   \
-  }
-
-#define IRKGL_ENTRIES_LPT(KIND, DIM, RHS_T, LPT) \
-  IRKGL_ENTRY(KIND, DIM, RHS_T, LPT, 128), IRKGL_ENTRY(KIND, DIM, RHS_T, LPT, 256), \
-      IRKGL_ENTRY(KIND, DIM, RHS_T, LPT, 64)
-
-using K1 = irkgl::Kepler<8>;
-using K2 = irkgl::Kepler<4>;
-using K4 = irkgl::Kepler<2>;
-using K8 = irkgl::Kepler<1>;
-using HH1 = irkgl::HenonHeiles<8>;
-using HH2 = irkgl::HenonHeiles<4>;
-using HH4 = irkgl::HenonHeiles<2>;
-using HH8 = irkgl::HenonHeiles<1>;
-template <int D> using Ha1 = irkgl::Harmonic<8, D>;
-template <int D> using Ha2 = irkgl::Harmonic<4, D>;
-template <int D> using Ha8 = irkgl::Harmonic<1, D>;
-
-const KernelEntry kTable[] = {
-    IRKGL_ENTRIES_LPT(IRKGL_RHS_KEPLER, 2, K1, 1),
-    IRKGL_ENTRIES_LPT(IRKGL_RHS_KEPLER, 2, K2, 2),
-    IRKGL_ENTRIES_LPT(IRKGL_RHS_KEPLER, 2, K4, 4),
-    IRKGL_ENTRIES_LPT(IRKGL_RHS_KEPLER, 2, K8, 8),
-    IRKGL_ENTRIES_LPT(IRKGL_RHS_HENON_HEILES, 2, HH1, 1),
-    IRKGL_ENTRIES_LPT(IRKGL_RHS_HENON_HEILES, 2, HH2, 2),
-    IRKGL_ENTRIES_LPT(IRKGL_RHS_HENON_HEILES, 2, HH4, 4),
-    IRKGL_ENTRIES_LPT(IRKGL_RHS_HENON_HEILES, 2, HH8, 8),
-    IRKGL_ENTRIES_LPT(IRKGL_RHS_HARMONIC, 1, Ha1<1>, 1),
-    IRKGL_ENTRIES_LPT(IRKGL_RHS_HARMONIC, 1, Ha8<1>, 8),
-    IRKGL_ENTRIES_LPT(IRKGL_RHS_HARMONIC, 2, Ha2<2>, 2),
-    IRKGL_ENTRIES_LPT(IRKGL_RHS_HARMONIC, 2, Ha8<2>, 8),
-    IRKGL_ENTRIES_LPT(IRKGL_RHS_HARMONIC, 3, Ha2<3>, 2),
-    IRKGL_ENTRIES_LPT(IRKGL_RHS_HARMONIC, 3, Ha8<3>, 8),
-};
+using irkgl::KernelEntry;
 
 const KernelEntry* find_kernel(int kind, int dim, int lpt, int block) {
-  for (const KernelEntry& e : kTable)
-    if (e.kind == kind && e.dim == dim && e.lpt == lpt && e.block == block) return &e;
+  const irkgl::KernelTable tables[] = {irkgl::kernels_kepler(), irkgl::kernels_henon_heiles(),
+                                       irkgl::kernels_harmonic(), irkgl::kernels_nbody()};
+  for (const irkgl::KernelTable& t : tables)
+    for (int i = 0; i < t.count; i++) {
+      const KernelEntry& e = t.entries[i];
+      if (e.kind == kind && e.dim == dim && e.lpt == lpt && e.block == block) return &e;
+    }
   return nullptr;
 }
 

@@ -22,6 +22,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace irkgl {
 
 constexpr int S = 8;
@@ -224,9 +226,142 @@ struct Harmonic {
   }
 };
 
+// Newtonian N-body in 3-D (Eq. Ham2): g_a = G sum_{b != a} m_b (q_b - q_a)/|q_b - q_a|^3.
+// Pairs are visited once (a < b) and both bodies are updated, 20 FP64
+// operations per pair; (h b_i) G m_b is folded into one weight per body.
+template <int SPL, int NB>
+struct NBody {
+  static constexpr int D = 3 * NB;
+  double G, m[NB];
+  double w[SPL][NB];  // (h b_i) G m_b
+  __device__ void load_params(const double* p) {
+    G = p[0];
+#pragma unroll
+    for (int b = 0; b < NB; b++) m[b] = p[1 + b];
+  }
+  __device__ void set_step(const double (&hb)[SPL]) {
+#pragma unroll
+    for (int t = 0; t < SPL; t++)
+#pragma unroll
+      for (int b = 0; b < NB; b++) w[t][b] = (hb[t] * G) * m[b];
+  }
+  __device__ __forceinline__ void stage_R(int t, const double (&x)[D], double (&R)[D]) const {
+#pragma unroll
+    for (int l = 0; l < D; l++) R[l] = 0.0;
+#pragma unroll
+    for (int a = 0; a < NB; a++)
+#pragma unroll
+      for (int b = a + 1; b < NB; b++) {
+        const double dx = x[3 * b] - x[3 * a];
+        const double dy = x[3 * b + 1] - x[3 * a + 1];
+        const double dz = x[3 * b + 2] - x[3 * a + 2];
+        const double z = rinv3(fma(dx, dx, fma(dy, dy, dz * dz)));
+        const double wb = w[t][b] * z, wa = w[t][a] * z;
+        R[3 * a] = fma(wb, dx, R[3 * a]);
+        R[3 * a + 1] = fma(wb, dy, R[3 * a + 1]);
+        R[3 * a + 2] = fma(wb, dz, R[3 * a + 2]);
+        R[3 * b] = fma(-wa, dx, R[3 * b]);
+        R[3 * b + 1] = fma(-wa, dy, R[3 * b + 1]);
+        R[3 * b + 2] = fma(-wa, dz, R[3 * b + 2]);
+      }
+  }
+  // The share of H computed by lane r of a group of L lanes: pairs
+  // p = r, r + L, ... (of the NB (NB-1)/2) and the kinetic energy of bodies
+  // a = r, r + L, ...; the group sums the shares.
+  static constexpr bool kSplitH = true;
+  __device__ double H_part(int r, int L, const double* q, const double* v) const {
+    double acc = 0.0;
+    for (int a = r; a < NB; a += L)
+      acc = fma(0.5 * m[a], fma(v[3 * a], v[3 * a], fma(v[3 * a + 1], v[3 * a + 1], v[3 * a + 2] * v[3 * a + 2])), acc);
+    constexpr int NP = NB * (NB - 1) / 2;
+    double pot = 0.0;
+    for (int p = r; p < NP; p += L) {
+      int a = 0, b = p;
+      while (b >= NB - 1 - a) {
+        b -= NB - 1 - a;
+        a++;
+      }
+      b += a + 1;
+      const double dx = q[3 * b] - q[3 * a];
+      const double dy = q[3 * b + 1] - q[3 * a + 1];
+      const double dz = q[3 * b + 2] - q[3 * a + 2];
+      pot = fma(m[a] * m[b], rinv1(fma(dx, dx, fma(dy, dy, dz * dz))), pot);
+    }
+    return fma(-G, pot, acc);
+  }
+  __device__ double H(const double (&q)[D], const double (&v)[D]) const {
+    double kin = 0.0, pot = 0.0;
+#pragma unroll
+    for (int a = 0; a < NB; a++)
+      kin = fma(0.5 * m[a], fma(v[3 * a], v[3 * a], fma(v[3 * a + 1], v[3 * a + 1], v[3 * a + 2] * v[3 * a + 2])), kin);
+#pragma unroll
+    for (int a = 0; a < NB; a++)
+#pragma unroll
+      for (int b = a + 1; b < NB; b++) {
+        const double dx = q[3 * b] - q[3 * a];
+        const double dy = q[3 * b + 1] - q[3 * a + 1];
+        const double dz = q[3 * b + 2] - q[3 * a + 2];
+        pot = fma(m[a] * m[b], rinv1(fma(dx, dx, fma(dy, dy, dz * dz))), pot);
+      }
+    return fma(-G, pot, kin);
+  }
+};
+
 // ------------------------------------------------------------------------
 // the kernel
 // ------------------------------------------------------------------------
+template <class T, class = void>
+struct split_energy : std::false_type {};
+template <class T>
+struct split_energy<T, std::void_t<decltype(T::kSplitH)>> : std::integral_constant<bool, T::kSplitH> {};
+
+// H(q, v) of the group's trajectory, from the owned components.  Right-hand
+// sides with a split energy (N-body) compute shares on every lane and sum
+// them with a butterfly; the others evaluate H on every lane redundantly.
+template <class Rhs, int LPT, int NS>
+__device__ __forceinline__ double group_energy(const Rhs& rhs, const double (&qh)[NS],
+                                               const double (&vh)[NS], unsigned mask, int gbase,
+                                               int r);
+
+// Value of component l (compile-time) of a per-component quantity owned by
+// lane (l % LPT) of the group, slot l / LPT.
+template <int LPT, int NS>
+__device__ __forceinline__ double owned_get(const double (&own)[NS], int l, unsigned mask, int gbase) {
+  if constexpr (LPT == 1) return own[l];
+  else return __shfl_sync(mask, own[l / LPT], gbase + l % LPT);
+}
+
+template <class Rhs, int LPT, int NS>
+__device__ __forceinline__ double group_energy(const Rhs& rhs, const double (&qh)[NS],
+                                               const double (&vh)[NS], unsigned mask, int gbase,
+                                               int r) {
+  constexpr int D = Rhs::D;
+  double qf[D], vf[D];
+#pragma unroll
+  for (int l = 0; l < D; l++) {
+    qf[l] = owned_get<LPT, NS>(qh, l, mask, gbase);
+    vf[l] = owned_get<LPT, NS>(vh, l, mask, gbase);
+  }
+  if constexpr (split_energy<Rhs>::value && LPT > 1) {
+    double e = rhs.H_part(r, LPT, qf, vf);
+#pragma unroll
+    for (int off = 1; off < LPT; off <<= 1) e = e + __shfl_xor_sync(mask, e, off);
+    return e;
+  } else {
+    return rhs.H(qf, vf);
+  }
+}
+
+// Select component (s*LPT + r) of a replicated per-component array, r runtime.
+template <int LPT, int D>
+__device__ __forceinline__ double select_own(const double (&arr)[D], int s, int r) {
+  double x = arr[s * LPT];
+#pragma unroll
+  for (int rr = 1; rr < LPT; rr++)
+    if (s * LPT + rr < D && r == rr) x = arr[s * LPT + rr];
+  return x;
+}
+
 template <class Rhs, int LPT, int BLOCK>
 __global__ void __launch_bounds__(BLOCK)
     irkgl_kernel(const __grid_constant__ KArgs a, const __grid_constant__ Coef cf) {
@@ -261,11 +396,13 @@ __global__ void __launch_bounds__(BLOCK)
 #pragma unroll
   for (int t = 0; t < SPL; t++) cc[t] = cf.c[i0 + t];
 
-  // per-trajectory state (uniform across the group's lanes unless noted)
+  // Per-trajectory state.  Component l of q and v (hi and lo parts) and its
+  // stopping-rule history live only on lane l % LPT of the group (slot
+  // l / LPT); stage quantities live on the lane that holds the stage.
   Rhs rhs;
   rhs.load_params(a.params);
-  double q[D], v[D];          // hi parts, replicated
-  double qlo[NS], vlo[NS];    // lo parts of the owned components l = s*LPT + r
+  double qh[NS], ql[NS], vh[NS], vl[NS];   // owned components: compensated pairs
+  unsigned long long dmin[NS], dprev[NS];  // owned components: Eq. stopping history
   double R[SPL][D];           // own stages' R (Rprev between steps)
   double Q[SPL][D];           // own stages' values
   double cv[SPL][D];          // c_i v
@@ -308,15 +445,13 @@ __global__ void __launch_bounds__(BLOCK)
             h = a.h ? a.h[t] : a.h_all;
             const size_t off = static_cast<size_t>(t) * D;
 #pragma unroll
-            for (int l = 0; l < D; l++) {
-              q[l] = a.q_in[off + l];
-              v[l] = a.v_in[off + l];
-            }
-#pragma unroll
             for (int s = 0; s < NS; s++) {
               const int l = s * LPT + r;
-              qlo[s] = (a.qlo_in && l < D) ? a.qlo_in[off + l] : 0.0;
-              vlo[s] = (a.vlo_in && l < D) ? a.vlo_in[off + l] : 0.0;
+              const bool in = l < D;
+              qh[s] = in ? a.q_in[off + l] : 0.0;
+              vh[s] = in ? a.v_in[off + l] : 0.0;
+              ql[s] = (a.qlo_in && in) ? a.qlo_in[off + l] : 0.0;
+              vl[s] = (a.vlo_in && in) ? a.vlo_in[off + l] : 0.0;
             }
             const size_t roff = static_cast<size_t>(t) * S * D;
 #pragma unroll
@@ -328,10 +463,6 @@ __global__ void __launch_bounds__(BLOCK)
 #pragma unroll
             for (int tt = 0; tt < SPL; tt++) hb[tt] = h * cf.b[i0 + tt];
             rhs.set_step(hb);
-            if (a.monitor > 0) {
-              H0 = rhs.H(q, v);
-              invH0 = 1.0 / H0;
-            }
           }
         }
       }
@@ -342,16 +473,21 @@ __global__ void __launch_bounds__(BLOCK)
     const bool stepping = active && (n < N);
     const unsigned stepmask = __ballot_sync(FULL, stepping);
     if (stepping) {
+      if (a.monitor > 0 && n == 0) {
+        H0 = group_energy<Rhs, LPT, NS>(rhs, qh, vh, stepmask, gbase, r);
+        invH0 = 1.0 / H0;
+      }
       // init (Eq. IRK_init2 in fused form): Q_i = q + h (c_i v + sum_k W_ik Rprev_k)
 #pragma unroll
-      for (int t = 0; t < SPL; t++)
-#pragma unroll
-        for (int l = 0; l < D; l++) cv[t][l] = cc[t] * v[l];
-#pragma unroll
       for (int l = 0; l < D; l++) {
+        const double vlv = owned_get<LPT, NS>(vh, l, stepmask, gbase);
+        const double qlv = owned_get<LPT, NS>(qh, l, stepmask, gbase);
         double acc[SPL];
 #pragma unroll
-        for (int t = 0; t < SPL; t++) acc[t] = cv[t][l];
+        for (int t = 0; t < SPL; t++) {
+          cv[t][l] = cc[t] * vlv;
+          acc[t] = cv[t][l];
+        }
 #pragma unroll
         for (int j = 0; j < S; j++) {
           double Rj;
@@ -361,14 +497,13 @@ __global__ void __launch_bounds__(BLOCK)
           for (int t = 0; t < SPL; t++) acc[t] = fma(IRKGL_W(t, j), Rj, acc[t]);
         }
 #pragma unroll
-        for (int t = 0; t < SPL; t++) Q[t][l] = fma(h, acc[t], q[l]);
+        for (int t = 0; t < SPL; t++) Q[t][l] = fma(h, acc[t], qlv);
       }
 
-      unsigned long long dmin[D], dprev[D];
 #pragma unroll
-      for (int l = 0; l < D; l++) {
-        dmin[l] = INF_BITS;
-        dprev[l] = INF_BITS;
+      for (int s = 0; s < NS; s++) {
+        dmin[s] = INF_BITS;
+        dprev[s] = INF_BITS;
       }
       int k = 0;
       bool conv = false;
@@ -381,9 +516,10 @@ __global__ void __launch_bounds__(BLOCK)
 #pragma unroll
           for (int t = 0; t < SPL; t++) rhs.stage_R(t, Q[t], R[t]);
           // Qn_i = q + h (c_i v + sum_j eta_ij R_j) (Eq. Qi2), Delta (Eq. Delta_n)
-          bool stop = true, bad = false;
+          bool cond_own = true, bad = false;
 #pragma unroll
           for (int l = 0; l < D; l++) {
+            const double qlv = owned_get<LPT, NS>(qh, l, sweepmask, gbase);
             double acc[SPL];
 #pragma unroll
             for (int t = 0; t < SPL; t++) acc[t] = cv[t][l];
@@ -398,21 +534,31 @@ __global__ void __launch_bounds__(BLOCK)
             unsigned long long dl = 0;
 #pragma unroll
             for (int t = 0; t < SPL; t++) {
-              const double qn = fma(h, acc[t], q[l]);
+              const double qn = fma(h, acc[t], qlv);
               dl = umax64(dl, abs_bits(qn - Q[t][l]));
               Q[t][l] = qn;
             }
 #pragma unroll
             for (int off = 1; off < LPT; off <<= 1)
               dl = umax64(dl, __shfl_xor_sync(sweepmask, dl, off));
-            // Eq. stopping on this component (non-negative doubles order like
-            // their bit patterns; NaN/Inf patterns are >= INF_BITS)
-            bad = bad || (dl >= INF_BITS);
-            const bool cond = (dl == 0) || (dmin[l] <= umin64(dprev[l], dl));
-            stop = stop && cond;
-            dmin[l] = umin64(dmin[l], dprev[l]);
-            dprev[l] = dl;
+            bad = bad || (dl >= INF_BITS);  // NaN/Inf patterns are >= INF_BITS
+            // Eq. stopping on this component, by its owner (non-negative
+            // doubles order like their bit patterns)
+#pragma unroll
+            for (int s = 0; s < NS; s++) {
+              if (s * LPT + r == l) {
+                const bool cond = (dl == 0) || (dmin[s] <= umin64(dprev[s], dl));
+                cond_own = cond_own && cond;
+                dmin[s] = umin64(dmin[s], dprev[s]);
+                dprev[s] = dl;
+              }
+            }
           }
+          // the group stops when every component's condition holds
+          bool stop = cond_own;
+#pragma unroll
+          for (int off = 1; off < LPT; off <<= 1)
+            stop = stop && __shfl_xor_sync(sweepmask, static_cast<int>(stop), off);
           if (bad) {
             st = ST_NONFINITE;
             conv = true;
@@ -450,41 +596,18 @@ __global__ void __launch_bounds__(BLOCK)
           scR[l] = y;
         }
         // compensated update of the owned components l = s*LPT + r
-        double nq[NS], nv[NS];
 #pragma unroll
         for (int s = 0; s < NS; s++) {
-          double a_sR = sR[s * LPT], a_scR = scR[s * LPT], qh = q[s * LPT], vh = v[s * LPT];
-#pragma unroll
-          for (int rr = 1; rr < LPT; rr++) {
-            if (s * LPT + rr < D && r == rr) {
-              a_sR = sR[s * LPT + rr];
-              a_scR = scR[s * LPT + rr];
-              qh = q[s * LPT + rr];
-              vh = v[s * LPT + rr];
-            }
-          }
           if (s * LPT + r < D) {
-            two_sum_add(vh, vlo[s], a_sR);
+            two_sum_add(vh[s], vl[s], select_own<LPT, D>(sR, s, r));
             // dq = h v_hi + (h v_lo - h sum c_i R_i)
-            const double dq = fma(h, vh, fma(h, vlo[s], -(h * a_scR)));
-            two_sum_add(qh, qlo[s], dq);
-          }
-          nq[s] = qh;
-          nv[s] = vh;
-        }
-#pragma unroll
-        for (int l = 0; l < D; l++) {
-          if constexpr (LPT == 1) {
-            q[l] = nq[l];
-            v[l] = nv[l];
-          } else {
-            q[l] = __shfl_sync(okmask, nq[l / LPT], gbase + l % LPT);
-            v[l] = __shfl_sync(okmask, nv[l / LPT], gbase + l % LPT);
+            const double dq = fma(h, vh[s], fma(h, vl[s], -(h * select_own<LPT, D>(scR, s, r))));
+            two_sum_add(qh[s], ql[s], dq);
           }
         }
         n++;
         if (a.monitor > 0 && (n % a.monitor) == 0) {
-          const double Hn = rhs.H(q, v);
+          const double Hn = group_energy<Rhs, LPT, NS>(rhs, qh, vh, okmask, gbase, r);
           const double dH = fabs((Hn - H0) * invH0);
           if (dH > dHmax) dHmax = dH;
         }
@@ -499,18 +622,10 @@ __global__ void __launch_bounds__(BLOCK)
       for (int s = 0; s < NS; s++) {
         const int l = s * LPT + r;
         if (l < D) {
-          // owned components: hi parts from the replicated arrays
-          double qh = q[s * LPT], vh = v[s * LPT];
-#pragma unroll
-          for (int rr = 1; rr < LPT; rr++)
-            if (s * LPT + rr < D && r == rr) {
-              qh = q[s * LPT + rr];
-              vh = v[s * LPT + rr];
-            }
-          a.q_out[off + l] = qh;
-          a.v_out[off + l] = vh;
-          if (a.qlo_out) a.qlo_out[off + l] = qlo[s];
-          if (a.vlo_out) a.vlo_out[off + l] = vlo[s];
+          a.q_out[off + l] = qh[s];
+          a.v_out[off + l] = vh[s];
+          if (a.qlo_out) a.qlo_out[off + l] = ql[s];
+          if (a.vlo_out) a.vlo_out[off + l] = vl[s];
         }
       }
       if (a.rp_out && st == ST_OK) {

@@ -1,0 +1,44 @@
+// irkgl_kernels.h -- internal: the table of compiled kernel instantiations.
+//
+// Each right-hand side's instantiations live in their own translation unit
+// (k_*.cu) so that they compile in parallel; irkgl_api.cu looks kernels up
+// by (kind, dimension, lanes per trajectory, block size).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "irkgl_device.cuh"
+
+namespace irkgl {
+
+struct KernelEntry {
+  int kind;
+  int dim;
+  int lpt;
+  int block;
+  const void* fn;
+  void (*launch)(dim3, dim3, cudaStream_t, const KArgs&, const Coef&);
+};
+
+template <class Rhs, int LPT, int BLOCK>
+void launch_impl(dim3 grid, dim3 block, cudaStream_t st, const KArgs& a, const Coef& c) {
+  irkgl_kernel<Rhs, LPT, BLOCK><<<grid, block, 0, st>>>(a, c);
+}
+
+struct KernelTable {
+  const KernelEntry* entries;
+  int count;
+};
+
+KernelTable kernels_kepler();
+KernelTable kernels_henon_heiles();
+KernelTable kernels_harmonic();
+KernelTable kernels_nbody();
+
+}  // namespace irkgl
+
+#define IRKGL_ENTRY(KIND, DIM, RHS, LPT, BLOCK)                                        \
+  ::irkgl::KernelEntry {                                                               \
+    KIND, DIM, LPT, BLOCK, (const void*)::irkgl::irkgl_kernel<RHS, LPT, BLOCK>,       \
+        ::irkgl::launch_impl<RHS, LPT, BLOCK>                                          \
+  }

@@ -1,0 +1,19 @@
+// k_kepler.cu -- compiled instantiations of the batched IRKGL16 kernel.
+#include "irkgl.h"
+#include "irkgl_kernels.h"
+
+namespace {
+
+const ::irkgl::KernelEntry kEntries[] = {
+    IRKGL_ENTRY(IRKGL_RHS_KEPLER, 2, ::irkgl::Kepler<8>, 1, 128),
+    IRKGL_ENTRY(IRKGL_RHS_KEPLER, 2, ::irkgl::Kepler<4>, 2, 128),
+    IRKGL_ENTRY(IRKGL_RHS_KEPLER, 2, ::irkgl::Kepler<4>, 2, 64),
+    IRKGL_ENTRY(IRKGL_RHS_KEPLER, 2, ::irkgl::Kepler<4>, 2, 256),
+    IRKGL_ENTRY(IRKGL_RHS_KEPLER, 2, ::irkgl::Kepler<2>, 4, 128),
+    IRKGL_ENTRY(IRKGL_RHS_KEPLER, 2, ::irkgl::Kepler<1>, 8, 128),
+};
+}  // namespace
+
+namespace irkgl {
+KernelTable kernels_kepler() { return KernelTable{kEntries, static_cast<int>(sizeof(kEntries) / sizeof(kEntries[0]))}; }
+}  // namespace irkgl

@@ -1,0 +1,115 @@
+"""GPU parity for the N-body ensemble (6 bodies, d = 18) against the oracle.
+
+  * states over steps 1..10 within 1e-13 relative, sweep counts within +-1
+    over the first 1,000 steps (perturbed copies of the system);
+  * chaotic-run criterion: over 64 copies x 10,000 steps the median, p90 and
+    max of max_n |dH/H| agree with the oracle's within a factor of 2, and are
+    <= 1e-13 where the oracle's are;
+  * chunked stepping == one persistent launch, bitwise; N = 3..5 variants.
+"""
+import numpy as np
+import pytest
+
+from oracle import cbind
+from paper_2511_03655_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    from paper_2511_03655_gb300 import build, irkgl
+    build.build()
+    irkgl.load()
+    return torch
+
+
+def dev(torch, a):
+    return torch.tensor(np.ascontiguousarray(a), device="cuda")
+
+
+def rel(qg, vg, qo, vo):
+    g = np.concatenate([np.asarray(qg), np.asarray(vg)], axis=-1)
+    o = np.concatenate([np.asarray(qo), np.asarray(vo)], axis=-1)
+    return np.abs(g - o).max(axis=-1) / np.abs(o).max(axis=-1)
+
+
+def test_nbody_first_steps_and_iterations(torch_cuda):
+    from paper_2511_03655_gb300 import irkgl
+    torch = torch_cuda
+    w = workloads.nbody_ensemble(copies=8, steps=1000)
+    d, h = w["dim"], float(w["h"][0])
+    integ = irkgl.Integrator(irkgl.RHS_NBODY, w["params"], d, h)
+    assert integ.tile == 8
+    q, v = dev(torch, w["q0"]), dev(torch, w["v0"])
+    ql, vl = torch.zeros_like(q), torch.zeros_like(v)
+    rp = torch.zeros((8, 8, d), dtype=torch.float64, device="cuda")
+    st = dict(q=w["q0"], v=w["v0"], q_lo=None, v_lo=None, r_prev=None)
+    for s in range(10):
+        integ.step(q, v, ql, vl, rp, nsteps=1)
+        r = cbind.run(cbind.NBODY, w["params"], st["q"], st["v"], h, 1, q_lo=st["q_lo"],
+                      v_lo=st["v_lo"], r_prev=st["r_prev"])
+        st = dict(q=r["q"], v=r["v"], q_lo=r["q_lo"], v_lo=r["v_lo"], r_prev=r["r_prev"])
+        assert rel(q.cpu(), v.cpu(), r["q"], r["v"]).max() <= 1e-13, s
+    it = torch.zeros((8, 1000), dtype=torch.int32, device="cuda")
+    q, v = dev(torch, w["q0"]), dev(torch, w["v0"])
+    integ.step(q, v, torch.zeros_like(q), torch.zeros_like(v), torch.zeros_like(rp), nsteps=1000,
+               iters=it)
+    r = cbind.run(cbind.NBODY, w["params"], w["q0"], w["v0"], h, 1000, iters_len=1000, nthreads=8)
+    diff = it.cpu().numpy() - r["iters"]
+    assert np.abs(diff).max() <= 1
+    assert (diff == 0).mean() > 0.8
+    integ.close()
+
+
+def test_nbody_energy_statistics_chaotic_criterion(torch_cuda):
+    from paper_2511_03655_gb300 import irkgl
+    torch = torch_cuda
+    w = workloads.nbody_ensemble(copies=64, steps=10000)
+    d, h = w["dim"], float(w["h"][0])
+    integ = irkgl.Integrator(irkgl.RHS_NBODY, w["params"], d, h)
+    out = integ.integrate(dev(torch, w["q0"]), dev(torch, w["v0"]), nsteps_all=10000)
+    torch.cuda.synchronize()
+    r = cbind.run(cbind.NBODY, w["params"], w["q0"], w["v0"], h, 10000, nthreads=8)
+    g, o = out.dH_max.cpu().numpy(), r["dH_max"]
+    assert (out.status.cpu().numpy() == 0).all() and (r["status"] == 0).all()
+    for stat in (np.median, lambda x: np.percentile(x, 90), np.max):
+        sg, so = stat(g), stat(o)
+        assert sg <= 2 * so and so <= 2 * sg, (sg, so)
+        if so <= 1e-13:
+            assert sg <= 1e-13
+    integ.close()
+
+
+def test_nbody_chunked_equals_single_launch(torch_cuda):
+    from paper_2511_03655_gb300 import irkgl
+    torch = torch_cuda
+    w = workloads.nbody_ensemble(copies=40, steps=300)
+    d, h = w["dim"], float(w["h"][0])
+    integ = irkgl.Integrator(irkgl.RHS_NBODY, w["params"], d, h)
+    a = integ.integrate(dev(torch, w["q0"]), dev(torch, w["v0"]), nsteps_all=300)
+    q, v = dev(torch, w["q0"]), dev(torch, w["v0"])
+    ql, vl = torch.zeros_like(q), torch.zeros_like(v)
+    rp = torch.zeros((40, 8, d), dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        integ.step(q, v, ql, vl, rp, nsteps=100)
+    torch.cuda.synchronize()
+    assert torch.equal(a.q, q) and torch.equal(a.v, v) and torch.equal(a.r_prev, rp)
+    assert torch.equal(a.q_lo, ql) and torch.equal(a.v_lo, vl)
+    integ.close()
+
+
+@pytest.mark.parametrize("nb", [3, 4, 5])
+def test_nbody_smaller_systems(torch_cuda, nb):
+    from paper_2511_03655_gb300 import irkgl
+    torch = torch_cuda
+    w = workloads.nbody_ensemble(copies=16, nbodies=nb, steps=500, seed_id=10 + nb)
+    d, h = w["dim"], float(w["h"][0])
+    integ = irkgl.Integrator(irkgl.RHS_NBODY, w["params"], d, h)
+    out = integ.integrate(dev(torch, w["q0"]), dev(torch, w["v0"]), nsteps_all=500)
+    torch.cuda.synchronize()
+    r = cbind.run(cbind.NBODY, w["params"], w["q0"], w["v0"], h, 500, nthreads=8)
+    assert rel(out.q.cpu(), out.v.cpu(), r["q"], r["v"]).max() <= 1e-10
+    assert (out.dH_max.cpu().numpy() <= 1e-13).all()
+    integ.close()
