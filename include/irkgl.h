@@ -55,7 +55,9 @@ enum {
   IRKGL_STATUS_OK = 0,        /* all requested steps completed */
   IRKGL_STATUS_MAXITER = 1,   /* a step reached the sweep cap without meeting Eq. stopping;
                                  the trajectory stops at the start of that step */
-  IRKGL_STATUS_NONFINITE = 2  /* a stage value became Inf/NaN; stops as above */
+  IRKGL_STATUS_NONFINITE = 2, /* a stage value became Inf/NaN; stops as above */
+  IRKGL_STATUS_BAD_INSTANCE = 3 /* ragged batches: the instance descriptor is invalid (kind,
+                                   dim > dmax, parameter count); nothing of it was touched */
 };
 
 /* Built-in right-hand sides g(q) (device functions; the paper's user
@@ -94,6 +96,21 @@ typedef struct {
   int* status;        /* [batch] IRKGL_STATUS_* */
 } irkgl_outputs;
 
+/* One instance of a ragged batch (irkgl_integrate_ragged): its own right-hand
+ * side, dimension, step and horizon.  States of all instances are packed
+ * one after another: instance k occupies elements [offset, offset + dim) of
+ * the packed position/velocity arrays and [8*offset, 8*(offset + dim)) of a
+ * packed R array; its parameters are params[param_offset .. + nparams). */
+typedef struct {
+  int kind;           /* irkgl_rhs_kind: IRKGL_RHS_NBODY, IRKGL_RHS_FPUT or IRKGL_RHS_HARMONIC */
+  int dim;            /* position dimension d (N-body: 3 x bodies) */
+  long long offset;   /* first packed element of this instance */
+  int param_offset;   /* first parameter in the packed parameter array */
+  int nparams;        /* N-body: 1 + bodies (G, masses); FPUT: 1 (alpha); harmonic: 1 (omega) */
+  double h;           /* step size (finite, nonzero) */
+  long long nsteps;   /* steps to take (>= 0) */
+} irkgl_instance;
+
 /* Options for irkgl_set_option. */
 enum {
   IRKGL_OPT_LANES_PER_TRAJ = 1, /* tile: 1, 2, 4 or 8 lanes share one trajectory's 8 stages
@@ -101,7 +118,16 @@ enum {
   IRKGL_OPT_KMAX = 2,           /* sweep cap per step (default 100); 1..1000 */
   IRKGL_OPT_MONITOR_EVERY = 3,  /* evaluate H every m steps for dH_max (default 1; 0 = off) */
   IRKGL_OPT_BLOCK_THREADS = 4,  /* threads per block: 64, 128 or 256 (default 128) */
-  IRKGL_OPT_GRID_BLOCKS = 5     /* persistent grid size (0 = one full wave, the default) */
+  IRKGL_OPT_GRID_BLOCKS = 5,    /* persistent grid size (0 = one full wave, the default) */
+  IRKGL_OPT_WIDE_TEAM = 6,      /* ragged batches: threads per instance, 32, 64, 128 or 256
+                                   (0 = chosen from the largest dimension, the default) */
+  IRKGL_OPT_MONITOR_LOCAL = 7,  /* 1: dH_max reports the local error max_n |(H_n - H_{n-1})/H_{n-1}|
+                                   (Eq. DHlocmax) instead of the global one (default 0; not
+                                   carried across irkgl_advance calls) */
+  IRKGL_OPT_MIX = 8             /* stage mixing of Eq. Qi2 and the initial guess: 0 = FP64 FMA
+                                   chain (default); 1 = exact fixed-point sums on the integer
+                                   pipes, rounded once (one lane per trajectory, default tables
+                                   only; IRKGL_ERR_UNSUPPORTED otherwise) */
 };
 
 /* Fill *out with the default IRKGL16 tables of Sec. 2.4 (nodes c and weights
@@ -139,6 +165,26 @@ int irkgl_step(struct irkgl_ctx* ctx, double* q, double* v, double* q_lo, double
                double* r_prev, const double* h, int batch, int nsteps, int* iters,
                int* status, void* cuda_stream);
 
+/* Advance device-resident trajectories by a per-trajectory number of steps,
+ * continuing everything a long run carries (the compensated state, R_prev
+ * for the extrapolated guess of Eq. IRK_init2, the reference energy H_0 and
+ * the running max |dH/H|), so a run split into chunks of any sizes gives the
+ * bits of one uninterrupted run.  Used by the serving loop, which advances
+ * many requests in interleaved chunks.  Device arrays, [batch] unless noted:
+ *   q, v, q_lo, v_lo [batch][dim], r_prev [batch][8][dim]   in/out (required)
+ *   h        per-trajectory step, or NULL for the context's h
+ *   nsteps   steps to take in this call (0 = leave the trajectory alone)
+ *   H0       in/out reference energy (required when dH_max is given)
+ *   h0_init  1 on the first call of a run: H0 is computed at the first step
+ *            and written; 0 afterwards: H0 is read
+ *   dH_max, iters   in/out running maxima / totals (NULL = not tracked)
+ *   status   out: IRKGL_STATUS_* of this call (NULL = not wanted)
+ * Errors: IRKGL_ERR_INVALID, IRKGL_ERR_UNSUPPORTED, IRKGL_ERR_CUDA. */
+int irkgl_advance(struct irkgl_ctx* ctx, double* q, double* v, double* q_lo, double* v_lo,
+                  double* r_prev, const double* h, const long long* nsteps, double* H0,
+                  int h0_init, double* dH_max, long long* iters, int* status, int batch,
+                  void* cuda_stream);
+
 /* Integrate `batch` independent initial states (device arrays q0, v0
  * [batch][dim], R_prev = 0, lo = 0) in one persistent launch.
  *   nsteps  [batch] steps per trajectory (device), or NULL to use nsteps_all
@@ -161,6 +207,37 @@ int irkgl_integrate_host(struct irkgl_ctx* ctx, const double* q0, const double* 
                          const long long* nsteps, long long nsteps_all, const double* h,
                          const int* order, const irkgl_outputs* out, void* cuda_stream);
 
+/* Integrate a ragged batch: `ninst` independent instances of different right-hand
+ * sides and dimensions (irkgl_instance, device array) in one persistent launch
+ * of the wide kernel: a team of threads (a warp, or a whole block, see
+ * IRKGL_OPT_WIDE_TEAM) owns one instance at a time, with its 8 stage values
+ * in shared memory.  The step is the same as irkgl_integrate's (Eqs.
+ * IRK_init2, IRK_FP2, stopping, qnvn2 with compensated sums), starting from
+ * R_prev = 0 and lo = 0.
+ *   dmax     the largest inst[k].dim (host value; sizes shared memory), 1..1024
+ *   params   packed parameters (device)
+ *   q0, v0   packed initial states (device)
+ *   order    processing order (device permutation of 0..ninst-1) or NULL;
+ *            costliest first keeps the persistent teams balanced
+ *   out      q, v, q_lo, v_lo packed like q0; r_prev packed [.][8][dim];
+ *            dH_max, iters, steps, status per instance
+ * The context supplies the tables, options and work counter; its own right-
+ * hand side and dimension are not used.  Errors: IRKGL_ERR_INVALID,
+ * IRKGL_ERR_UNSUPPORTED (dmax beyond the compiled shapes), IRKGL_ERR_CUDA. */
+int irkgl_integrate_ragged(struct irkgl_ctx* ctx, const irkgl_instance* inst, int ninst, int dmax,
+                           const double* params, const double* q0, const double* v0,
+                           const int* order, const irkgl_outputs* out, void* cuda_stream);
+
+/* Continue a ragged batch in place (the wide-kernel counterpart of
+ * irkgl_advance): instance k takes nsteps[k] steps (device int64 [ninst];
+ * inst[k].nsteps is ignored) from the packed state q, v, q_lo, v_lo, r_prev
+ * (all required, in/out), with H0 / h0_init / dH_max / iters as in
+ * irkgl_advance (per instance).  Errors as irkgl_integrate_ragged. */
+int irkgl_advance_ragged(struct irkgl_ctx* ctx, const irkgl_instance* inst, int ninst, int dmax,
+                         const double* params, double* q, double* v, double* q_lo, double* v_lo,
+                         double* r_prev, const long long* nsteps, double* H0, int h0_init,
+                         double* dH_max, long long* iters, int* status, void* cuda_stream);
+
 /* Release the context and its device workspace (NULL is ignored). */
 void irkgl_destroy(struct irkgl_ctx* ctx);
 
@@ -180,6 +257,13 @@ int irkgl_get_tile(struct irkgl_ctx* ctx);
  * launch with events on the same stream; FMAs / seconds is the FP64 roof
  * used for the roofline fraction.  Errors: IRKGL_ERR_INVALID, IRKGL_ERR_CUDA. */
 int irkgl_probe_fp64_fma(double* scratch, long long* fma_count, void* cuda_stream);
+
+/* Diagnostic, not part of the method: the fixed-point stage mixing of
+ * IRKGL_OPT_MIX = 1 applied to n columns R[n][8] (device): out[n][8][2]
+ * receives sum_j eta_ij R_j and sum_j W_ij R_j for each row i, as the kernel
+ * computes them (exact sums rounded once).  Errors: IRKGL_ERR_INVALID,
+ * IRKGL_ERR_CUDA. */
+int irkgl_diag_fixed_mix(const double* R, double* out, int n, void* cuda_stream);
 
 /* Integration for callers that cannot allocate device memory.  (The paper
  * has no counterpart: this is a deployment entry point.)

@@ -15,6 +15,7 @@
 
 #include "irkgl.h"
 #include "irkgl_kernels.h"
+#include "irkgl_wide.cuh"
 #include "irkgl_tables.h"
 
 using irkgl::Coef;
@@ -37,13 +38,14 @@ int cuda_fail(cudaError_t e) {
 
 using irkgl::KernelEntry;
 
-const KernelEntry* find_kernel(int kind, int dim, int lpt, int block) {
+const KernelEntry* find_kernel(int kind, int dim, int lpt, int block, int mix = 0) {
   const irkgl::KernelTable tables[] = {irkgl::kernels_kepler(), irkgl::kernels_henon_heiles(),
                                        irkgl::kernels_harmonic(), irkgl::kernels_nbody()};
   for (const irkgl::KernelTable& t : tables)
     for (int i = 0; i < t.count; i++) {
       const KernelEntry& e = t.entries[i];
-      if (e.kind == kind && e.dim == dim && e.lpt == lpt && e.block == block) return &e;
+      if (e.kind == kind && e.dim == dim && e.lpt == lpt && e.block == block && e.mix == mix)
+        return &e;
     }
   return nullptr;
 }
@@ -81,6 +83,15 @@ __global__ void __launch_bounds__(256) fp64_fma_probe(double* out, double a, dou
 
 }  // namespace
 
+namespace irkgl {
+struct WideShape {
+  int team, block, slots;
+  const void* fn;
+  void (*launch)(dim3, dim3, size_t, cudaStream_t, const WideArgs&, const Coef&);
+};
+int wide_shapes(const WideShape** out);
+}  // namespace irkgl
+
 struct irkgl_ctx {
   int kind;
   int dim;
@@ -96,6 +107,10 @@ struct irkgl_ctx {
   int monitor;
   int block;
   int grid_blocks;
+  int wide_team;
+  int monitor_local;
+  int mix;             // IRKGL_OPT_MIX
+  int default_tables;  // the context uses irkgl_default_coeffs (needed by mix = 1)
   // staging for irkgl_integrate_host
   void* d_stage;
   size_t stage_bytes;
@@ -126,6 +141,7 @@ const char* irkgl_strerror(int code) {
     case IRKGL_ERR_UNSUPPORTED: return "no compiled kernel for this right-hand side, dimension and tile";
     case IRKGL_STATUS_MAXITER: return "status: fixed-point sweep cap reached";
     case IRKGL_STATUS_NONFINITE: return "status: non-finite stage value";
+    case IRKGL_STATUS_BAD_INSTANCE: return "status: invalid instance descriptor";
     default: return "unknown code";
   }
 }
@@ -199,7 +215,8 @@ int irkgl_create(irkgl_ctx** out, irkgl_rhs f, int dim, double h, const irkgl_co
     c->coef.b[i] = tab.b[i];
   }
   for (int x = 0; x < 64; x++) c->coef.eta[x] = tab.eta[x];
-  if (is_default_table(&tab)) {
+  c->default_tables = is_default_table(&tab) ? 1 : 0;
+  if (c->default_tables) {
     for (int x = 0; x < 64; x++) c->coef.W[x] = IRKGL_TAB_W[x];
   } else {
     // W = mu diag(b) nu in FP64, fixed summation order (host code is built
@@ -256,6 +273,19 @@ int irkgl_set_option(irkgl_ctx* c, int option, long long value) {
       if (value < 0 || value > (1 << 20)) return IRKGL_ERR_INVALID;
       c->grid_blocks = static_cast<int>(value);
       return IRKGL_OK;
+    case IRKGL_OPT_MIX:
+      if (value != 0 && value != 1) return IRKGL_ERR_INVALID;
+      c->mix = static_cast<int>(value);
+      return IRKGL_OK;
+    case IRKGL_OPT_MONITOR_LOCAL:
+      if (value != 0 && value != 1) return IRKGL_ERR_INVALID;
+      c->monitor_local = static_cast<int>(value);
+      return IRKGL_OK;
+    case IRKGL_OPT_WIDE_TEAM:
+      if (!(value == 0 || value == 32 || value == 64 || value == 128 || value == 256))
+        return IRKGL_ERR_INVALID;
+      c->wide_team = static_cast<int>(value);
+      return IRKGL_OK;
     default:
       return IRKGL_ERR_INVALID;
   }
@@ -263,17 +293,20 @@ int irkgl_set_option(irkgl_ctx* c, int option, long long value) {
 
 int irkgl_get_tile(irkgl_ctx* c) {
   if (!c) return IRKGL_ERR_INVALID;
+  if (c->mix) return find_kernel(c->kind, c->dim, 1, c->block, 1) ? 1 : 0;
   return c->lpt ? c->lpt : default_lpt(c->kind, c->dim);
 }
 
 static int run(irkgl_ctx* c, KArgs& a, cudaStream_t st) {
-  const int lpt = c->lpt ? c->lpt : default_lpt(c->kind, c->dim);
-  const KernelEntry* ke = lpt ? find_kernel(c->kind, c->dim, lpt, c->block) : nullptr;
+  if (c->mix && !c->default_tables) return IRKGL_ERR_UNSUPPORTED;
+  const int lpt = c->mix ? 1 : (c->lpt ? c->lpt : default_lpt(c->kind, c->dim));
+  const KernelEntry* ke = lpt ? find_kernel(c->kind, c->dim, lpt, c->block, c->mix) : nullptr;
   if (!ke) return IRKGL_ERR_UNSUPPORTED;
   a.counter = c->d_counter;
   a.params = c->d_params;
   a.kmax = c->kmax;
   a.monitor = c->monitor;
+  a.monitor_local = c->monitor_local;
   const int traj_per_block = c->block / lpt;
   long long need = (static_cast<long long>(a.batch) + traj_per_block - 1) / traj_per_block;
   int grid = c->grid_blocks;
@@ -324,6 +357,42 @@ int irkgl_step(irkgl_ctx* c, double* q, double* v, double* q_lo, double* v_lo, d
   return rc;
 }
 
+int irkgl_advance(irkgl_ctx* c, double* q, double* v, double* q_lo, double* v_lo, double* r_prev,
+                  const double* h, const long long* nsteps, double* H0, int h0_init,
+                  double* dH_max, long long* iters, int* status, int batch, void* stream) {
+  if (!c || batch < 0) return IRKGL_ERR_INVALID;
+  if (batch == 0) return IRKGL_OK;
+  if (!q || !v || !q_lo || !v_lo || !r_prev || !nsteps) return IRKGL_ERR_INVALID;
+  if (dH_max && !H0) return IRKGL_ERR_INVALID;
+  KArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.batch = batch;
+  a.q_in = q;
+  a.v_in = v;
+  a.qlo_in = q_lo;
+  a.vlo_in = v_lo;
+  a.rp_in = r_prev;
+  a.q_out = q;
+  a.v_out = v;
+  a.qlo_out = q_lo;
+  a.vlo_out = v_lo;
+  a.rp_out = r_prev;
+  a.nsteps = nsteps;
+  a.h = h;
+  a.h_all = c->h;
+  a.iters_total = iters;
+  a.dH_max = dH_max;
+  a.status = status;
+  a.H0_io = H0;
+  a.h0_init = h0_init ? 1 : 0;
+  a.accumulate = 1;
+  const int saved_monitor = c->monitor;
+  if (!dH_max) c->monitor = 0;
+  const int rc = run(c, a, static_cast<cudaStream_t>(stream));
+  c->monitor = saved_monitor;
+  return rc;
+}
+
 int irkgl_integrate(irkgl_ctx* c, const double* q0, const double* v0, int batch,
                     const long long* nsteps, long long nsteps_all, const double* h,
                     const int* order, const irkgl_outputs* out, void* stream) {
@@ -351,6 +420,102 @@ int irkgl_integrate(irkgl_ctx* c, const double* q0, const double* v0, int batch,
   a.status = out->status;
   a.steps_done = out->steps;
   return run(c, a, static_cast<cudaStream_t>(stream));
+}
+
+static int run_wide(irkgl_ctx* c, irkgl::WideArgs& a, int ninst, int dmax, cudaStream_t st) {
+  static_assert(sizeof(irkgl_instance) == sizeof(irkgl::WideInstance), "instance layout");
+  if (dmax < 1) return IRKGL_ERR_INVALID;
+  if (dmax > 1024) return IRKGL_ERR_UNSUPPORTED;
+  // team shape: requested size, else a warp for small instances, else the
+  // smallest block whose threads x slots cover dmax
+  const irkgl::WideShape* shapes = nullptr;
+  const int ns = irkgl::wide_shapes(&shapes);
+  const irkgl::WideShape* ws = nullptr;
+  for (int i = 0; i < ns && !ws; i++) {
+    const irkgl::WideShape& x = shapes[i];
+    if (x.team * x.slots < dmax) continue;
+    if (c->wide_team ? x.team == c->wide_team : true) ws = &x;
+  }
+  if (!ws) return IRKGL_ERR_UNSUPPORTED;
+  const int teams = ws->block / ws->team;
+  const size_t smem = irkgl::wide_smem_bytes(teams, dmax);
+  if (smem > 227 * 1024) return IRKGL_ERR_UNSUPPORTED;
+  IRKGL_CUDA(cudaFuncSetAttribute(ws->fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(smem)));
+  int per_sm = 0;
+  IRKGL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ws->fn, ws->block, smem));
+  if (per_sm < 1) return IRKGL_ERR_UNSUPPORTED;
+  int grid = c->grid_blocks > 0 ? c->grid_blocks : per_sm * c->sm_count;
+  const int need = (ninst + teams - 1) / teams;
+  if (grid > need) grid = need;
+  a.ninst = ninst;
+  a.kmax = c->kmax;
+  a.dmax = dmax;
+  a.counter = c->d_counter;
+  a.monitor_local = c->monitor_local;
+  IRKGL_CUDA(cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned), st));
+  ws->launch(dim3(grid), dim3(ws->block), smem, st, a, c->coef);
+  IRKGL_CUDA(cudaGetLastError());
+  return IRKGL_OK;
+}
+
+int irkgl_integrate_ragged(irkgl_ctx* c, const irkgl_instance* inst, int ninst, int dmax,
+                           const double* params, const double* q0, const double* v0,
+                           const int* order, const irkgl_outputs* out, void* stream) {
+  if (!c || ninst < 0 || !out) return IRKGL_ERR_INVALID;
+  if (ninst == 0) return IRKGL_OK;
+  if (!inst || !params || !q0 || !v0 || !out->q || !out->v) return IRKGL_ERR_INVALID;
+  irkgl::WideArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.monitor = c->monitor;
+  a.inst = reinterpret_cast<const irkgl::WideInstance*>(inst);
+  a.params = params;
+  a.q_in = q0;
+  a.v_in = v0;
+  a.q_out = out->q;
+  a.v_out = out->v;
+  a.qlo_out = out->q_lo;
+  a.vlo_out = out->v_lo;
+  a.rp_out = out->r_prev;
+  a.dH_max = out->dH_max;
+  a.iters_total = out->iters;
+  a.steps_done = out->steps;
+  a.status = out->status;
+  a.order = order;
+  return run_wide(c, a, ninst, dmax, static_cast<cudaStream_t>(stream));
+}
+
+int irkgl_advance_ragged(irkgl_ctx* c, const irkgl_instance* inst, int ninst, int dmax,
+                         const double* params, double* q, double* v, double* q_lo, double* v_lo,
+                         double* r_prev, const long long* nsteps, double* H0, int h0_init,
+                         double* dH_max, long long* iters, int* status, void* stream) {
+  if (!c || ninst < 0) return IRKGL_ERR_INVALID;
+  if (ninst == 0) return IRKGL_OK;
+  if (!inst || !params || !q || !v || !q_lo || !v_lo || !r_prev || !nsteps) return IRKGL_ERR_INVALID;
+  if (dH_max && !H0) return IRKGL_ERR_INVALID;
+  irkgl::WideArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.monitor = dH_max ? c->monitor : 0;
+  a.inst = reinterpret_cast<const irkgl::WideInstance*>(inst);
+  a.params = params;
+  a.q_in = q;
+  a.v_in = v;
+  a.q_out = q;
+  a.v_out = v;
+  a.qlo_in = q_lo;
+  a.vlo_in = v_lo;
+  a.qlo_out = q_lo;
+  a.vlo_out = v_lo;
+  a.rp_in = r_prev;
+  a.rp_out = r_prev;
+  a.nsteps_call = nsteps;
+  a.H0_io = H0;
+  a.h0_init = h0_init ? 1 : 0;
+  a.accumulate = 1;
+  a.dH_max = dH_max;
+  a.iters_total = iters;
+  a.status = status;
+  return run_wide(c, a, ninst, dmax, static_cast<cudaStream_t>(stream));
 }
 
 int irkgl_integrate_host(irkgl_ctx* c, const double* q0, const double* v0, int batch,

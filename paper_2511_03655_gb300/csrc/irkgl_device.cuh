@@ -24,13 +24,15 @@
 
 #include <type_traits>
 
+#include "irkgl_tables.h"
+
 namespace irkgl {
 
 constexpr int S = 8;
 constexpr unsigned FULL = 0xffffffffu;
 constexpr unsigned long long INF_BITS = 0x7ff0000000000000ULL;
 
-enum { ST_OK = 0, ST_MAXITER = 1, ST_NONFINITE = 2 };
+enum { ST_OK = 0, ST_MAXITER = 1, ST_NONFINITE = 2, ST_BADDESC = 3 };
 
 // Coefficients passed by value (kernel parameter space = constant bank).
 struct Coef {
@@ -67,6 +69,10 @@ struct KArgs {
   long long* steps_done;    // [batch] or null
   unsigned int* counter;    // work counter, zero at launch
   const double* params;     // right-hand-side parameters (device)
+  double* H0_io;            // [batch] reference energy: read, or written when h0_init
+  int h0_init;              // 1: compute H0 at the first step and store it in H0_io
+  int accumulate;           // 1: dH_max / iters_total start from the values in the arrays
+  int monitor_local;        // 1: dH_max = max_n |(H_n - H_{n-1}) / H_{n-1}| (Eq. DHlocmax)
 };
 
 // ------------------------------------------------------------------------
@@ -149,6 +155,141 @@ __device__ __forceinline__ void two_sum_add(double& hi, double& lo, double x) {
   const double hi2 = __dadd_rn(s, lo2);
   lo = __dsub_rn(lo2, __dsub_rn(hi2, s));
   hi = hi2;
+}
+
+// ------------------------------------------------------------------------
+// Fixed-point mixing on the integer pipes (kernel variant MIX = 1)
+//
+// The sums sum_j eta_ij R_j (and sum_k W_ik R_k) are accumulated exactly in
+// 128-bit integers and rounded once to FP64, instead of eight FP64 FMAs:
+//   * the eight R_j of one component share a scale: with emax the largest
+//     biased exponent among them, R_j is truncated to the integer
+//     r_j = R_j 2^(1083 - emax) (|r_j| < 2^61; exact unless R_j is more than
+//     2^8 smaller than the largest, where the dropped bits lie below 2^-61 of
+//     it), then offset to r'_j = r_j + 2^61 >= 0;
+//   * eta_ij = +-n_ij 2^-63 with n_ij an exact integer (every eta is on that
+//     grid); W_ik = +-w_ik 2^-50 rounded (W only seeds the initial guess);
+//   * products n r' (64 x 64 -> 128 bits, eight 32-bit multiply-adds with
+//     carry) go to a positive or a negative accumulator by the coefficient's
+//     sign, known at compile time; the difference minus the row constant
+//     sum_j (+-n_ij) 2^61 is the exact sum, rounded to nearest-even FP64.
+// The result is the correctly rounded value of the (exact) sum, one rounding
+// instead of the FMA chain's eight.
+// ------------------------------------------------------------------------
+struct U128 {
+  unsigned x0, x1, x2, x3;
+};
+
+// a += p * q (unsigned 64 x 64 -> 128)
+__device__ __forceinline__ void mac64(U128& a, unsigned long long p, unsigned long long q) {
+  const unsigned p0 = static_cast<unsigned>(p), p1 = static_cast<unsigned>(p >> 32);
+  const unsigned q0 = static_cast<unsigned>(q), q1 = static_cast<unsigned>(q >> 32);
+  asm("mad.lo.cc.u32 %0, %4, %6, %0;\n\t"
+      "madc.hi.cc.u32 %1, %4, %6, %1;\n\t"
+      "addc.cc.u32 %2, %2, 0;\n\t"
+      "addc.u32 %3, %3, 0;\n\t"
+      "mad.lo.cc.u32 %1, %4, %7, %1;\n\t"
+      "madc.hi.cc.u32 %2, %4, %7, %2;\n\t"
+      "addc.u32 %3, %3, 0;\n\t"
+      "mad.lo.cc.u32 %1, %5, %6, %1;\n\t"
+      "madc.hi.cc.u32 %2, %5, %6, %2;\n\t"
+      "addc.u32 %3, %3, 0;\n\t"
+      "mad.lo.cc.u32 %2, %5, %7, %2;\n\t"
+      "madc.hi.u32 %3, %5, %7, %3;"
+      : "+r"(a.x0), "+r"(a.x1), "+r"(a.x2), "+r"(a.x3)
+      : "r"(p0), "r"(p1), "r"(q0), "r"(q1));
+}
+
+// a -= b (mod 2^128)
+__device__ __forceinline__ void sub128(U128& a, unsigned b0, unsigned b1, unsigned b2, unsigned b3) {
+  asm("sub.cc.u32 %0, %0, %4;\n\t"
+      "subc.cc.u32 %1, %1, %5;\n\t"
+      "subc.cc.u32 %2, %2, %6;\n\t"
+      "subc.u32 %3, %3, %7;"
+      : "+r"(a.x0), "+r"(a.x1), "+r"(a.x2), "+r"(a.x3)
+      : "r"(b0), "r"(b1), "r"(b2), "r"(b3));
+}
+
+// Round-to-nearest-even FP64 of v * 2^e2, v a 128-bit two's complement
+// integer.  The result must be a normal number (|value| well inside range).
+__device__ __forceinline__ double s128_to_double(const U128& v, int e2) {
+  const unsigned s = v.x3 >> 31;
+  unsigned long long hi = (static_cast<unsigned long long>(v.x3) << 32) | v.x2;
+  unsigned long long lo = (static_cast<unsigned long long>(v.x1) << 32) | v.x0;
+  if (s) {
+    lo = ~lo + 1ull;
+    hi = ~hi + (lo == 0ull ? 1ull : 0ull);
+  }
+  if ((hi | lo) == 0ull) return 0.0;
+  int lz = 0;
+  if (hi == 0ull) {
+    hi = lo;
+    lo = 0ull;
+    lz = 64;
+  }
+  const int z = __clzll(static_cast<long long>(hi));
+  if (z) {
+    hi = (hi << z) | (lo >> (64 - z));
+    lo <<= z;
+  }
+  lz += z;
+  const int E = (127 - lz + e2) + 1023;  // biased exponent of the leading bit
+  const unsigned long long mant = hi >> 11;  // 53 bits, leading bit 2^52
+  const unsigned long long rbit = (hi >> 10) & 1ull;
+  const unsigned long long sticky = ((hi & 0x3ffull) | lo) != 0ull ? 1ull : 0ull;
+  unsigned long long bits = (static_cast<unsigned long long>(E - 1) << 52) + mant;
+  bits += rbit & (sticky | (mant & 1ull));
+  bits |= static_cast<unsigned long long>(s) << 63;
+  return __longlong_as_double(static_cast<long long>(bits));
+}
+
+__device__ __forceinline__ int biased_exp(double x) {
+  return static_cast<int>((static_cast<unsigned long long>(__double_as_longlong(x)) >> 52) & 0x7ff);
+}
+
+// r' = trunc(x 2^(1083 - emax)) + 2^61 for x with biased exponent <= emax
+// (zero and subnormal x give the offset alone).
+__device__ __forceinline__ unsigned long long to_fixed_offset(double x, int emax) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+  const int e = static_cast<int>((b >> 52) & 0x7ff);
+  const unsigned long long m = e ? ((b & 0x000fffffffffffffull) | 0x0010000000000000ull) : 0ull;
+  const int sh = 8 - (emax - e);
+  const unsigned long long mag = sh >= 0 ? (m << sh) : (sh > -64 ? (m >> (-sh)) : 0ull);
+  constexpr unsigned long long OFF = 1ull << IRKGL_R_BIAS;
+  return (b >> 63) ? OFF - mag : OFF + mag;
+}
+
+// sum_j coef_ij R_j for row i (compile-time after unrolling), R_j given as
+// offset fixed point rb[j] with shared exponent emax.  IS_W selects W.
+template <bool IS_W>
+__device__ __forceinline__ double fixed_row(int i, const unsigned long long (&rb)[S], int emax) {
+  U128 P{0u, 0u, 0u, 0u}, N{0u, 0u, 0u, 0u};
+#pragma unroll
+  for (int j = 0; j < S; j++) {
+    const int k = i * S + j;
+    const unsigned long long m = IS_W ? irkgl_w_mag(k) : irkgl_eta_mag(k);
+    const bool neg = IS_W ? irkgl_w_neg(k) : irkgl_eta_neg(k);
+    if (neg) mac64(N, m, rb[j]);
+    else mac64(P, m, rb[j]);
+  }
+  sub128(P, N.x0, N.x1, N.x2, N.x3);
+  if (IS_W) sub128(P, irkgl_w_bias(i, 0), irkgl_w_bias(i, 1), irkgl_w_bias(i, 2), irkgl_w_bias(i, 3));
+  else sub128(P, irkgl_eta_bias(i, 0), irkgl_eta_bias(i, 1), irkgl_eta_bias(i, 2), irkgl_eta_bias(i, 3));
+  constexpr int shift = IS_W ? IRKGL_W_SHIFT : IRKGL_ETA_SHIFT;
+  return s128_to_double(P, emax - 1083 - shift);
+}
+
+// Offset fixed-point form of the eight R_j of one component; returns emax and
+// flags a non-finite R (whose sums must come out non-finite).
+__device__ __forceinline__ int fixed_column(const double (&Rc)[S], unsigned long long (&rb)[S],
+                                            bool& nonfinite) {
+  int emax = 0;
+#pragma unroll
+  for (int j = 0; j < S; j++) emax = max(emax, biased_exp(Rc[j]));
+  nonfinite = emax == 0x7ff;
+#pragma unroll
+  for (int j = 0; j < S; j++) rb[j] = to_fixed_offset(Rc[j], emax);
+  return emax;
 }
 
 // ------------------------------------------------------------------------
@@ -362,9 +503,10 @@ __device__ __forceinline__ double select_own(const double (&arr)[D], int s, int 
   return x;
 }
 
-template <class Rhs, int LPT, int BLOCK>
+template <class Rhs, int LPT, int BLOCK, int MIX = 0>
 __global__ void __launch_bounds__(BLOCK)
     irkgl_kernel(const __grid_constant__ KArgs a, const __grid_constant__ Coef cf) {
+  static_assert(MIX == 0 || LPT == 1, "fixed-point mixing needs all stages in one lane");
   constexpr int D = Rhs::D;
   constexpr int SPL = S / LPT;
   constexpr int NS = (D + LPT - 1) / LPT;  // owned component slots per lane
@@ -407,6 +549,7 @@ __global__ void __launch_bounds__(BLOCK)
   double Q[SPL][D];           // own stages' values
   double cv[SPL][D];          // c_i v
   double h = 0.0, H0 = 0.0, invH0 = 0.0, dHmax = 0.0;
+  double Hprev = 0.0, invHprev = 0.0;  // local-error monitor
   long long n = 0, N = 0, itot = 0;
   int traj = -1, st = ST_OK;
   bool active = false, exhausted = false;
@@ -443,6 +586,16 @@ __global__ void __launch_bounds__(BLOCK)
             dHmax = 0.0;
             N = a.nsteps ? a.nsteps[t] : a.nsteps_all;
             h = a.h ? a.h[t] : a.h_all;
+            if (a.accumulate) {
+              if (a.dH_max) dHmax = a.dH_max[t];
+              if (a.iters_total) itot = a.iters_total[t];
+            }
+            if (a.H0_io && !a.h0_init) {
+              H0 = a.H0_io[t];
+              invH0 = 1.0 / H0;
+              Hprev = H0;
+              invHprev = invH0;
+            }
             const size_t off = static_cast<size_t>(t) * D;
 #pragma unroll
             for (int s = 0; s < NS; s++) {
@@ -469,35 +622,62 @@ __global__ void __launch_bounds__(BLOCK)
     }
     if (__all_sync(FULL, exhausted && !active)) break;
 
+    // ---------------- reference energy H_0 of trajectories before their first
+    // step.  The groups that need it differ from warp iteration to iteration,
+    // so the shuffles inside run under the ballot of exactly those lanes.
+    {
+      const bool want = active && n == 0 && a.monitor > 0 && (!a.H0_io || a.h0_init);
+      const unsigned h0mask = __ballot_sync(FULL, want);
+      if (want) {
+        H0 = group_energy<Rhs, LPT, NS>(rhs, qh, vh, h0mask, gbase, r);
+        invH0 = 1.0 / H0;
+        Hprev = H0;
+        invHprev = invH0;
+        if (a.H0_io && leader) a.H0_io[traj] = H0;
+      }
+    }
+
     // ---------------- one step for every group that still has steps to take
     const bool stepping = active && (n < N);
     const unsigned stepmask = __ballot_sync(FULL, stepping);
     if (stepping) {
-      if (a.monitor > 0 && n == 0) {
-        H0 = group_energy<Rhs, LPT, NS>(rhs, qh, vh, stepmask, gbase, r);
-        invH0 = 1.0 / H0;
-      }
       // init (Eq. IRK_init2 in fused form): Q_i = q + h (c_i v + sum_k W_ik Rprev_k)
 #pragma unroll
       for (int l = 0; l < D; l++) {
         const double vlv = owned_get<LPT, NS>(vh, l, stepmask, gbase);
         const double qlv = owned_get<LPT, NS>(qh, l, stepmask, gbase);
-        double acc[SPL];
+        if constexpr (MIX == 1) {
+          double Rc[S];
 #pragma unroll
-        for (int t = 0; t < SPL; t++) {
-          cv[t][l] = cc[t] * vlv;
-          acc[t] = cv[t][l];
+          for (int j = 0; j < S; j++) Rc[j] = R[j][l];
+          unsigned long long rb[S];
+          bool nf;
+          const int emax = fixed_column(Rc, rb, nf);
+#pragma unroll
+          for (int t = 0; t < SPL; t++) {
+            cv[t][l] = cc[t] * vlv;
+            double T = fixed_row<true>(t, rb, emax);
+            if (nf) T = __longlong_as_double(0x7ff8000000000000LL);
+            Q[t][l] = fma(h, cv[t][l] + T, qlv);
+          }
+        } else {
+          double acc[SPL];
+#pragma unroll
+          for (int t = 0; t < SPL; t++) {
+            cv[t][l] = cc[t] * vlv;
+            acc[t] = cv[t][l];
+          }
+#pragma unroll
+          for (int j = 0; j < S; j++) {
+            double Rj;
+            if constexpr (LPT == 1) Rj = R[j][l];
+            else Rj = __shfl_sync(stepmask, R[j % SPL][l], gbase + j / SPL);
+#pragma unroll
+            for (int t = 0; t < SPL; t++) acc[t] = fma(IRKGL_W(t, j), Rj, acc[t]);
+          }
+#pragma unroll
+          for (int t = 0; t < SPL; t++) Q[t][l] = fma(h, acc[t], qlv);
         }
-#pragma unroll
-        for (int j = 0; j < S; j++) {
-          double Rj;
-          if constexpr (LPT == 1) Rj = R[j][l];
-          else Rj = __shfl_sync(stepmask, R[j % SPL][l], gbase + j / SPL);
-#pragma unroll
-          for (int t = 0; t < SPL; t++) acc[t] = fma(IRKGL_W(t, j), Rj, acc[t]);
-        }
-#pragma unroll
-        for (int t = 0; t < SPL; t++) Q[t][l] = fma(h, acc[t], qlv);
       }
 
 #pragma unroll
@@ -521,15 +701,30 @@ __global__ void __launch_bounds__(BLOCK)
           for (int l = 0; l < D; l++) {
             const double qlv = owned_get<LPT, NS>(qh, l, sweepmask, gbase);
             double acc[SPL];
+            if constexpr (MIX == 1) {
+              double Rc[S];
 #pragma unroll
-            for (int t = 0; t < SPL; t++) acc[t] = cv[t][l];
+              for (int j = 0; j < S; j++) Rc[j] = R[j][l];
+              unsigned long long rb[S];
+              bool nf;
+              const int emax = fixed_column(Rc, rb, nf);
 #pragma unroll
-            for (int j = 0; j < S; j++) {
-              double Rj;
-              if constexpr (LPT == 1) Rj = R[j][l];
-              else Rj = __shfl_sync(sweepmask, R[j % SPL][l], gbase + j / SPL);
+              for (int t = 0; t < SPL; t++) {
+                double T = fixed_row<false>(t, rb, emax);
+                if (nf) T = __longlong_as_double(0x7ff8000000000000LL);
+                acc[t] = cv[t][l] + T;
+              }
+            } else {
 #pragma unroll
-              for (int t = 0; t < SPL; t++) acc[t] = fma(IRKGL_ETA(t, j), Rj, acc[t]);
+              for (int t = 0; t < SPL; t++) acc[t] = cv[t][l];
+#pragma unroll
+              for (int j = 0; j < S; j++) {
+                double Rj;
+                if constexpr (LPT == 1) Rj = R[j][l];
+                else Rj = __shfl_sync(sweepmask, R[j % SPL][l], gbase + j / SPL);
+#pragma unroll
+                for (int t = 0; t < SPL; t++) acc[t] = fma(IRKGL_ETA(t, j), Rj, acc[t]);
+              }
             }
             unsigned long long dl = 0;
 #pragma unroll
@@ -606,10 +801,21 @@ __global__ void __launch_bounds__(BLOCK)
           }
         }
         n++;
-        if (a.monitor > 0 && (n % a.monitor) == 0) {
-          const double Hn = group_energy<Rhs, LPT, NS>(rhs, qh, vh, okmask, gbase, r);
-          const double dH = fabs((Hn - H0) * invH0);
-          if (dH > dHmax) dHmax = dH;
+        if (a.monitor > 0) {
+          const bool mon = (n % a.monitor) == 0;  // differs between groups when monitor > 1
+          const unsigned monmask = __ballot_sync(okmask, mon);
+          if (mon) {
+            const double Hn = group_energy<Rhs, LPT, NS>(rhs, qh, vh, monmask, gbase, r);
+            double dH;
+            if (a.monitor_local) {
+              dH = fabs((Hn - Hprev) * invHprev);
+              Hprev = Hn;
+              invHprev = 1.0 / Hn;
+            } else {
+              dH = fabs((Hn - H0) * invH0);
+            }
+            if (dH > dHmax) dHmax = dH;
+          }
         }
       }
     }

@@ -16,13 +16,14 @@ struct KernelEntry {
   int dim;
   int lpt;
   int block;
+  int mix;  // 0: FP64 FMA mixing, 1: fixed-point mixing on the integer pipes
   const void* fn;
   void (*launch)(dim3, dim3, cudaStream_t, const KArgs&, const Coef&);
 };
 
-template <class Rhs, int LPT, int BLOCK>
+template <class Rhs, int LPT, int BLOCK, int MIX>
 void launch_impl(dim3 grid, dim3 block, cudaStream_t st, const KArgs& a, const Coef& c) {
-  irkgl_kernel<Rhs, LPT, BLOCK><<<grid, block, 0, st>>>(a, c);
+  irkgl_kernel<Rhs, LPT, BLOCK, MIX><<<grid, block, 0, st>>>(a, c);
 }
 
 struct KernelTable {
@@ -37,8 +38,9 @@ KernelTable kernels_nbody();
 
 }  // namespace irkgl
 
-#define IRKGL_ENTRY(KIND, DIM, RHS, LPT, BLOCK)                                        \
-  ::irkgl::KernelEntry {                                                               \
-    KIND, DIM, LPT, BLOCK, (const void*)::irkgl::irkgl_kernel<RHS, LPT, BLOCK>,       \
-        ::irkgl::launch_impl<RHS, LPT, BLOCK>                                          \
+#define IRKGL_ENTRY_MIX(KIND, DIM, RHS, LPT, BLOCK, MIX)                                  \
+  ::irkgl::KernelEntry {                                                                 \
+    KIND, DIM, LPT, BLOCK, MIX, (const void*)::irkgl::irkgl_kernel<RHS, LPT, BLOCK, MIX>, \
+        ::irkgl::launch_impl<RHS, LPT, BLOCK, MIX>                                       \
   }
+#define IRKGL_ENTRY(KIND, DIM, RHS, LPT, BLOCK) IRKGL_ENTRY_MIX(KIND, DIM, RHS, LPT, BLOCK, 0)

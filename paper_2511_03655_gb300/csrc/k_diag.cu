@@ -1,0 +1,32 @@
+// k_diag.cu -- diagnostic kernel for the fixed-point mixing (tests only).
+#include <cuda_runtime.h>
+
+#include "irkgl.h"
+#include "irkgl_device.cuh"
+
+namespace {
+__global__ void fixed_mix_kernel(const double* R, double* out, int n) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= n) return;
+  double Rc[irkgl::S];
+#pragma unroll
+  for (int j = 0; j < irkgl::S; j++) Rc[j] = R[x * irkgl::S + j];
+  unsigned long long rb[irkgl::S];
+  bool nf;
+  const int emax = irkgl::fixed_column(Rc, rb, nf);
+#pragma unroll
+  for (int i = 0; i < irkgl::S; i++) {
+    out[(x * irkgl::S + i) * 2] = nf ? __longlong_as_double(0x7ff8000000000000LL)
+                                     : irkgl::fixed_row<false>(i, rb, emax);
+    out[(x * irkgl::S + i) * 2 + 1] = nf ? __longlong_as_double(0x7ff8000000000000LL)
+                                         : irkgl::fixed_row<true>(i, rb, emax);
+  }
+}
+}  // namespace
+
+extern "C" int irkgl_diag_fixed_mix(const double* R, double* out, int n, void* stream) {
+  if (n < 0 || (n > 0 && (!R || !out))) return IRKGL_ERR_INVALID;
+  if (n == 0) return IRKGL_OK;
+  fixed_mix_kernel<<<(n + 127) / 128, 128, 0, static_cast<cudaStream_t>(stream)>>>(R, out, n);
+  return cudaGetLastError() == cudaSuccess ? IRKGL_OK : IRKGL_ERR_CUDA;
+}

@@ -6,6 +6,8 @@ namespace {
 
 const ::irkgl::KernelEntry kEntries[] = {
     IRKGL_ENTRY(IRKGL_RHS_KEPLER, 2, ::irkgl::Kepler<8>, 1, 128),
+    IRKGL_ENTRY_MIX(IRKGL_RHS_KEPLER, 2, ::irkgl::Kepler<8>, 1, 128, 1),
+    IRKGL_ENTRY_MIX(IRKGL_RHS_KEPLER, 2, ::irkgl::Kepler<8>, 1, 64, 1),
     IRKGL_ENTRY(IRKGL_RHS_KEPLER, 2, ::irkgl::Kepler<4>, 2, 128),
     IRKGL_ENTRY(IRKGL_RHS_KEPLER, 2, ::irkgl::Kepler<4>, 2, 64),
     IRKGL_ENTRY(IRKGL_RHS_KEPLER, 2, ::irkgl::Kepler<4>, 2, 256),

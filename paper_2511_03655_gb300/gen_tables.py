@@ -136,6 +136,62 @@ def tables():
     return {"c": cf, "b": bf, "mu": mu, "eta": eta, "nu": nu, "W": Wf}
 
 
+ETA_SHIFT = 63   # eta_ij = +-n_ij * 2^-63, n_ij exact (|eta| in [2^-11, 1))
+W_SHIFT = 50     # W_ij ~ +-w_ij * 2^-50, w_ij = round(|W_ij| 2^50) (only seeds the guess)
+R_BIAS = 61      # fixed-point R values are offset by 2^61 to make them non-negative
+
+
+def int_tables(t):
+    """Integer forms for the fixed-point mixing: magnitudes, signs and the
+    per-row correction sum_j (+-n_ij) 2^R_BIAS that removes the offset."""
+    out = {}
+    for name, shift, exact in (("ETA", ETA_SHIFT, True), ("W", W_SHIFT, False)):
+        mags, negs, bias = [], [], []
+        for i in range(S):
+            row_sum = 0
+            for j in range(S):
+                x = Fraction(t["eta" if name == "ETA" else "W"][i][j]) * (1 << shift)
+                if exact:
+                    assert x.denominator == 1, "eta is not on the 2^-63 grid"
+                    m = abs(x.numerator)
+                else:
+                    m = abs(round(x))
+                assert m < (1 << 63)
+                neg = x < 0
+                mags.append(m)
+                negs.append(1 if neg else 0)
+                row_sum += -m if neg else m
+            bias.append(row_sum * (1 << R_BIAS))
+        out[name] = (mags, negs, bias)
+    return out
+
+
+def _render_int(t) -> str:
+    it = int_tables(t)
+    lines = ["", "// Integer forms for the fixed-point mixing (see gen_tables.int_tables):",
+             f"// |ETA_ij| * 2^{ETA_SHIFT} (exact), round(|W_ij| * 2^{W_SHIFT}); signs; per-row",
+             f"// corrections sum_j (+-m_ij) 2^{R_BIAS} as 128-bit two's complement words.",
+             f"#define IRKGL_ETA_SHIFT {ETA_SHIFT}", f"#define IRKGL_W_SHIFT {W_SHIFT}",
+             f"#define IRKGL_R_BIAS {R_BIAS}"]
+    for name in ("ETA", "W"):
+        mags, negs, bias = it[name]
+        lines.append(f"__host__ __device__ constexpr unsigned long long irkgl_{name.lower()}_mag(int k) {{")
+        lines.append("  constexpr unsigned long long t[64] = {")
+        lines.append("    " + ",\n    ".join(", ".join(f"0x{m:016x}ull" for m in mags[r * 8:(r + 1) * 8]) for r in range(8)).replace("\\n", "\n") + "};")
+        lines.append("  return t[k];\n}")
+        negmask = sum(1 << k for k, v in enumerate(negs) if v)
+        lines.append(f"__host__ __device__ constexpr bool irkgl_{name.lower()}_neg(int k) {{ return (0x{negmask:016x}ull >> k) & 1ull; }}")
+        words = []
+        for b in bias:
+            v = b % (1 << 128)
+            words.append([(v >> (32 * w)) & 0xffffffff for w in range(4)])
+        lines.append(f"__host__ __device__ constexpr unsigned irkgl_{name.lower()}_bias(int i, int w) {{")
+        lines.append("  constexpr unsigned t[32] = {")
+        lines.append("    " + ",\n    ".join(", ".join(f"0x{x:08x}u" for x in ws) for ws in words).replace("\\n", "\n") + "};")
+        lines.append("  return t[i * 4 + w];\n}")
+    return "\n".join(lines) + "\n"
+
+
 def render(t) -> str:
     def arr1(name, v):
         return f"static const double {name}[8] = {{\n  " + ",\n  ".join(float.hex(x) for x in v) + "};\n"
@@ -155,7 +211,7 @@ def render(t) -> str:
     out.append(arr2("IRKGL_TAB_ETA", t["eta"]))
     out.append(arr2("IRKGL_TAB_NU", t["nu"]))
     out.append(arr2("IRKGL_TAB_W", t["W"]))
-    return "\n".join(out)
+    return "\n".join(out) + _render_int(t)
 
 
 def main(argv=None):

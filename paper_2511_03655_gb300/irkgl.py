@@ -23,11 +23,15 @@ ERR_INVALID, ERR_NOMEM, ERR_CUDA, ERR_UNSUPPORTED = -1, -2, -3, -4
 STATUS_OK, STATUS_MAXITER, STATUS_NONFINITE = 0, 1, 2
 RHS_KEPLER, RHS_NBODY, RHS_FPUT, RHS_HENON_HEILES, RHS_HARMONIC = 1, 2, 3, 4, 5
 OPT_LANES_PER_TRAJ, OPT_KMAX, OPT_MONITOR_EVERY, OPT_BLOCK_THREADS, OPT_GRID_BLOCKS = 1, 2, 3, 4, 5
+OPT_WIDE_TEAM = 6
+OPT_MONITOR_LOCAL = 7
+OPT_MIX = 8
 
 EXPORTS = ("irkgl_default_coeffs", "irkgl_create", "irkgl_set_option", "irkgl_step",
            "irkgl_integrate", "irkgl_integrate_host", "irkgl_destroy", "irkgl_strerror",
            "irkgl_last_cuda_error", "irkgl_get_tile", "irkgl_probe_fp64_fma",
-           "irkgl_integrate_noalloc")
+           "irkgl_integrate_noalloc", "irkgl_integrate_ragged", "irkgl_advance",
+           "irkgl_advance_ragged", "irkgl_diag_fixed_mix")
 NOALLOC_MAX_PARAMS = 63
 
 _P = ctypes.c_void_p
@@ -46,6 +50,12 @@ class irkgl_coeffs(ctypes.Structure):
     _fields_ = [("c", ctypes.c_double * 8), ("b", ctypes.c_double * 8),
                 ("mu", ctypes.c_double * 64), ("eta", ctypes.c_double * 64),
                 ("nu", ctypes.c_double * 64)]
+
+
+class irkgl_instance(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("dim", ctypes.c_int), ("offset", ctypes.c_longlong),
+                ("param_offset", ctypes.c_int), ("nparams", ctypes.c_int), ("h", ctypes.c_double),
+                ("nsteps", ctypes.c_longlong)]
 
 
 class irkgl_outputs(ctypes.Structure):
@@ -85,12 +95,20 @@ def load(path: str | None = None, build_if_missing: bool = False):
     L.irkgl_last_cuda_error.restype = ctypes.c_char_p
     L.irkgl_get_tile.argtypes = [_P]
     L.irkgl_probe_fp64_fma.argtypes = [_P, ctypes.POINTER(ctypes.c_longlong), _P]
+    L.irkgl_advance.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int, _P, _P, _P,
+                                ctypes.c_int, _P]
+    L.irkgl_diag_fixed_mix.argtypes = [_P, _P, ctypes.c_int, _P]
+    L.irkgl_advance_ragged.argtypes = [_P, _P, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P, _P,
+                                       _P, _P, ctypes.c_int, _P, _P, _P, _P]
+    L.irkgl_integrate_ragged.argtypes = [_P, _P, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P,
+                                         ctypes.POINTER(irkgl_outputs), _P]
     L.irkgl_integrate_noalloc.argtypes = [irkgl_rhs, ctypes.c_int, ctypes.c_double, _P, _P,
                                           ctypes.c_int, _P, ctypes.c_longlong, _P, _P,
                                           ctypes.POINTER(irkgl_outputs), _P]
     for name in ("irkgl_default_coeffs", "irkgl_create", "irkgl_set_option", "irkgl_step",
                  "irkgl_integrate", "irkgl_integrate_host", "irkgl_get_tile",
-                 "irkgl_probe_fp64_fma", "irkgl_integrate_noalloc"):
+                 "irkgl_probe_fp64_fma", "irkgl_integrate_noalloc", "irkgl_integrate_ragged",
+                 "irkgl_advance", "irkgl_advance_ragged", "irkgl_diag_fixed_mix"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -176,6 +194,15 @@ def irkgl_probe_fp64_fma(scratch: torch.Tensor, stream=None) -> int:
     return n.value
 
 
+def irkgl_diag_fixed_mix(R: torch.Tensor, stream=None) -> torch.Tensor:
+    """Fixed-point mixing of columns R [n, 8] -> [n, 8, 2] (eta rows, W rows)."""
+    n = R.shape[0]
+    out = torch.empty((n, 8, 2), dtype=torch.float64, device=R.device)
+    _check(load().irkgl_diag_fixed_mix(_ptr(R, torch.float64, (n, 8), "R"),
+                                       _ptr(out, torch.float64, (n, 8, 2), "out"), n, _stream(stream)))
+    return out
+
+
 def irkgl_destroy(ctx: int):
     load().irkgl_destroy(_P(ctx))
 
@@ -196,6 +223,20 @@ def irkgl_step(ctx: int, dim: int, q, v, q_lo=None, v_lo=None, r_prev=None, h=No
         _ptr(r_prev, f64, (B, 8, dim), "r_prev"), _ptr(h, f64, (B,), "h"),
         B, int(nsteps), _ptr(iters, i32, (B, nsteps), "iters"), _ptr(status, i32, (B,), "status"),
         _stream(stream)))
+
+
+def irkgl_advance(ctx: int, dim: int, q, v, q_lo, v_lo, r_prev, nsteps, h=None, H0=None,
+                  h0_init: bool = False, dH_max=None, iters=None, status=None, stream=None):
+    """Continue device-resident trajectories by nsteps[b] steps each (int64 [B])."""
+    B = q.shape[0]
+    f64 = torch.float64
+    _check(load().irkgl_advance(
+        _P(ctx), _ptr(q, f64, (B, dim), "q"), _ptr(v, f64, (B, dim), "v"),
+        _ptr(q_lo, f64, (B, dim), "q_lo"), _ptr(v_lo, f64, (B, dim), "v_lo"),
+        _ptr(r_prev, f64, (B, 8, dim), "r_prev"), _ptr(h, f64, (B,), "h"),
+        _ptr(nsteps, torch.int64, (B,), "nsteps"), _ptr(H0, f64, (B,), "H0"), int(bool(h0_init)),
+        _ptr(dH_max, f64, (B,), "dH_max"), _ptr(iters, torch.int64, (B,), "iters"),
+        _ptr(status, torch.int32, (B,), "status"), B, _stream(stream)))
 
 
 @dataclass
@@ -266,6 +307,79 @@ def irkgl_integrate_host(ctx: int, dim: int, q0, v0, out: Outputs, nsteps=None,
         ctypes.byref(st), _stream(stream)))
 
 
+def instances_tensor(w: dict, device) -> torch.Tensor:
+    """Pack a ragged batch description (arrays kind, dim, offset, param_offset,
+    nparams, h, nsteps) into a device byte tensor of irkgl_instance records."""
+    n = len(w["kind"])
+    arr = (irkgl_instance * n)()
+    for k in range(n):
+        arr[k] = irkgl_instance(int(w["kind"][k]), int(w["dim"][k]), int(w["offset"][k]),
+                                int(w["param_offset"][k]), int(w["nparams"][k]), float(w["h"][k]),
+                                int(w["nsteps"][k]))
+    raw = torch.frombuffer(bytearray(bytes(arr)), dtype=torch.uint8)
+    return raw.to(device)
+
+
+@dataclass
+class RaggedOutputs:
+    q: torch.Tensor
+    v: torch.Tensor
+    q_lo: torch.Tensor | None = None
+    v_lo: torch.Tensor | None = None
+    r_prev: torch.Tensor | None = None
+    dH_max: torch.Tensor | None = None
+    iters: torch.Tensor | None = None
+    steps: torch.Tensor | None = None
+    status: torch.Tensor | None = None
+
+    @staticmethod
+    def allocate(total_dim: int, ninst: int, device="cuda"):
+        f = dict(dtype=torch.float64, device=device)
+        return RaggedOutputs(q=torch.empty(total_dim, **f), v=torch.empty(total_dim, **f),
+                             q_lo=torch.empty(total_dim, **f), v_lo=torch.empty(total_dim, **f),
+                             r_prev=torch.empty(8 * total_dim, **f),
+                             dH_max=torch.empty(ninst, **f),
+                             iters=torch.empty(ninst, dtype=torch.int64, device=device),
+                             steps=torch.empty(ninst, dtype=torch.int64, device=device),
+                             status=torch.empty(ninst, dtype=torch.int32, device=device))
+
+    def _struct(self):
+        f64, i64, i32 = torch.float64, torch.int64, torch.int32
+        return irkgl_outputs(_ptr(self.q, f64, None, "out.q"), _ptr(self.v, f64, None, "out.v"),
+                             _ptr(self.q_lo, f64, None, "out.q_lo"), _ptr(self.v_lo, f64, None, "out.v_lo"),
+                             _ptr(self.r_prev, f64, None, "out.r_prev"),
+                             _ptr(self.dH_max, f64, None, "out.dH_max"),
+                             _ptr(self.iters, i64, None, "out.iters"), _ptr(self.steps, i64, None, "out.steps"),
+                             _ptr(self.status, i32, None, "out.status"))
+
+
+def irkgl_integrate_ragged(ctx: int, inst: torch.Tensor, ninst: int, dmax: int, params, q0, v0,
+                           out: RaggedOutputs, order=None, stream=None):
+    """Ragged batch (device tensors): inst from instances_tensor(); packed
+    params, q0, v0; order int32 [ninst] or None."""
+    f64 = torch.float64
+    st = out._struct()
+    _check(load().irkgl_integrate_ragged(
+        _P(ctx), _ptr(inst, torch.uint8, None, "inst"), int(ninst), int(dmax),
+        _ptr(params, f64, None, "params"), _ptr(q0, f64, None, "q0"), _ptr(v0, f64, None, "v0"),
+        _ptr(order, torch.int32, (ninst,), "order"), ctypes.byref(st), _stream(stream)))
+
+
+def irkgl_advance_ragged(ctx: int, inst: torch.Tensor, ninst: int, dmax: int, params, q, v, q_lo,
+                         v_lo, r_prev, nsteps, H0=None, h0_init: bool = False, dH_max=None,
+                         iters=None, status=None, stream=None):
+    """Continue a ragged batch in place (packed device tensors); nsteps int64 [ninst]."""
+    f64 = torch.float64
+    _check(load().irkgl_advance_ragged(
+        _P(ctx), _ptr(inst, torch.uint8, None, "inst"), int(ninst), int(dmax),
+        _ptr(params, f64, None, "params"), _ptr(q, f64, None, "q"), _ptr(v, f64, None, "v"),
+        _ptr(q_lo, f64, None, "q_lo"), _ptr(v_lo, f64, None, "v_lo"),
+        _ptr(r_prev, f64, None, "r_prev"), _ptr(nsteps, torch.int64, (ninst,), "nsteps"),
+        _ptr(H0, f64, (ninst,), "H0"), int(bool(h0_init)), _ptr(dH_max, f64, (ninst,), "dH_max"),
+        _ptr(iters, torch.int64, (ninst,), "iters"), _ptr(status, torch.int32, (ninst,), "status"),
+        _stream(stream)))
+
+
 def irkgl_integrate_noalloc(kind: int, params, dim: int, h: float, q0, v0, out: Outputs,
                             nsteps=None, nsteps_all: int = 0, h_per_traj=None, order=None,
                             stream=None) -> int:
@@ -293,9 +407,10 @@ class Integrator:
 
     def __init__(self, kind: int, params, dim: int, h: float, coeffs: dict | None = None,
                  lanes_per_traj: int = 0, kmax: int = 100, monitor_every: int = 1,
-                 block_threads: int = 128):
+                 block_threads: int = 128, mix: int = 0):
         self.dim = dim
         self.ctx = irkgl_create(kind, params, dim, h, coeffs)
+        self.set(OPT_MIX, mix)
         self.set(OPT_LANES_PER_TRAJ, lanes_per_traj)
         self.set(OPT_KMAX, kmax)
         self.set(OPT_MONITOR_EVERY, monitor_every)
@@ -310,6 +425,9 @@ class Integrator:
 
     def step(self, *args, **kw):
         return irkgl_step(self.ctx, self.dim, *args, **kw)
+
+    def advance(self, *args, **kw):
+        return irkgl_advance(self.ctx, self.dim, *args, **kw)
 
     def integrate(self, q0, v0, out=None, **kw) -> Outputs:
         out = out or Outputs.allocate(q0.shape[0], self.dim, device=q0.device)

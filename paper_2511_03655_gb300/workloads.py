@@ -22,6 +22,16 @@ Workloads (sizes as in the benchmark configurations):
                    h = 0.5 % of the innermost period, 1e5 steps.  (A synthetic
                    stand-in for the paper's 6-body outer Solar System, whose DE430
                    initial conditions are not available here.)
+  fput_chain       FPUT alpha chain, n interior particles, fixed ends, alpha = 0.25,
+                   unit harmonic energy in mode 1: q_j = A sin(j pi/(n+1)),
+                   A = 2/(omega_1 sqrt(n+1)), omega_1 = 2 sin(pi/(2(n+1))), v = 0.
+  uneven_batch     4,096 instances, half N-body (N ~ U{3..64}: central mass + N-1
+                   bodies as in nbody_ensemble, one system per instance) and half
+                   FPUT (n ~ U{8..512}); per-instance h from a step table.
+  serving_requests Poisson arrivals (rate lambda); each request takes one family of
+                   the workloads above (Kepler orbits, 6-body copies, N-body with
+                   N ~ U{7..nb_max}, FPUT with n ~ U{8..n_max}), a batch ~ logU[1, B_max]
+                   and a horizon ~ logU[1e2, T_max] steps.
 """
 from __future__ import annotations
 
@@ -147,3 +157,110 @@ def nbody_ensemble(copies: int = 16384, nbodies: int = 6, steps: int = 100000, s
             "params": [1.0] + list(sysd["masses"]), "dim": d, "q0": q0, "v0": v0,
             "h": np.full(copies, h), "nsteps": np.full(copies, steps, dtype=np.int64),
             "masses": sysd["masses"]}
+
+
+def fput_chain(n: int, alpha: float = 0.25):
+    """Mode-1 initial condition of the FPUT alpha chain with unit harmonic energy."""
+    j = np.arange(1, n + 1, dtype=np.float64)
+    w1 = 2.0 * math.sin(math.pi / (2.0 * (n + 1)))
+    A = 2.0 / (w1 * math.sqrt(n + 1.0))
+    return {"q": A * np.sin(j * math.pi / (n + 1)), "v": np.zeros(n), "params": [alpha],
+            "omega_max": 2.0 * math.sin(n * math.pi / (2.0 * (n + 1)))}
+
+
+# Default step table (kind, size bucket) -> h rule.  N-body: a fraction of the
+# innermost period; FPUT: an absolute step.  The autotuner
+# (paper_2511_03655_gb300.autotune) refines these by pilot runs.
+DEFAULT_STEP_TABLE = {
+    "nbody": {"fraction_of_inner_period": 0.005},
+    "fput": {"h": 0.25},
+}
+
+
+def uneven_batch(ninst: int = 4096, steps: int = 10000, seed_id: int = 4, nmax_body: int = 64,
+                 nmax_chain: int = 512, step_table: dict | None = None):
+    """Ragged batch: instance list (kind, dim, offset, param_offset, nparams, h, nsteps)
+    plus packed q0, v0 and parameters."""
+    table = step_table or DEFAULT_STEP_TABLE
+    u = uniform(SEED_BASE + seed_id, 2 * ninst).reshape(2, ninst)
+    kinds, dims, hs, params, qs, vs = [], [], [], [], [], []
+    for k in range(ninst):
+        if k % 2 == 0:
+            nb = 3 + int(u[0, k] * (nmax_body - 2))
+            sysd = nbody_system(nb, seed_id=10000 + k)
+            h = table["nbody"]["fraction_of_inner_period"] * sysd["period_inner"]
+            kinds.append(2)
+            dims.append(3 * nb)
+            params.append([1.0] + list(sysd["masses"]))
+            qs.append(sysd["q"])
+            vs.append(sysd["v"])
+        else:
+            n = 8 + int(u[1, k] * (nmax_chain - 7))
+            c = fput_chain(n)
+            fput_h = table["fput"]
+            h = fput_h["h"] if "h" in fput_h else fput_h["by_bucket"][_bucket(n)]
+            kinds.append(3)
+            dims.append(n)
+            params.append(c["params"])
+            qs.append(c["q"])
+            vs.append(c["v"])
+        hs.append(h)
+    offsets = np.concatenate([[0], np.cumsum(dims)[:-1]]).astype(np.int64)
+    pcount = np.array([len(p) for p in params])
+    poffsets = np.concatenate([[0], np.cumsum(pcount)[:-1]]).astype(np.int64)
+    return {"name": f"uneven_batch_{ninst}", "kind": np.array(kinds, dtype=np.int32),
+            "dim": np.array(dims, dtype=np.int32), "offset": offsets,
+            "param_offset": poffsets.astype(np.int32), "nparams": pcount.astype(np.int32),
+            "h": np.array(hs), "nsteps": np.full(ninst, steps, dtype=np.int64),
+            "params": np.concatenate([np.asarray(p, dtype=np.float64) for p in params]),
+            "q0": np.concatenate(qs), "v0": np.concatenate(vs)}
+
+
+def _bucket(n: int) -> str:
+    for lim in (16, 32, 64, 128, 256, 512, 1024, 1536):
+        if n <= lim:
+            return str(lim)
+    return "inf"
+
+
+def _logu(u, lo, hi):
+    return math.exp(math.log(lo) + (math.log(hi) - math.log(lo)) * u)
+
+
+def serving_requests(n: int = 200, rate: float = 2000.0, seed_id: int = 5, batch_max: int = 4096,
+                     horizon_max: int = 100000, nb_max: int = 64, n_max: int = 1024,
+                     families=("kepler", "nbody6", "nbody", "fput")):
+    """Request descriptions for the serving loop (dicts; see serve.Request)."""
+    u = uniform(SEED_BASE + seed_id, 8 * n).reshape(n, 8)
+    t = np.cumsum(-np.log(1.0 - u[:, 0]) / rate)  # exponential inter-arrival times
+    out = []
+    for k in range(n):
+        fam = families[int(u[k, 1] * len(families)) % len(families)]
+        B = max(1, int(round(_logu(u[k, 2], 1, batch_max))))
+        T = int(round(_logu(u[k, 3], 100, horizon_max)))
+        sid = 20000 + k
+        if fam == "kepler":
+            e = 0.9 * uniform(SEED_BASE + sid, B)
+            q, v = kepler_ic(e)
+            m = np.rint(200.0 + 100.0 * e)
+            h = 2 * math.pi / m
+            req = dict(kind="kepler", params=[1.0], dim=2, q0=q, v0=v, h=h, nsteps=T)
+        elif fam == "nbody6":
+            w = nbody_ensemble(copies=B, steps=T, seed_id=sid)
+            req = dict(kind="nbody", params=w["params"], dim=18, q0=w["q0"], v0=w["v0"],
+                       h=float(w["h"][0]), nsteps=T)
+        elif fam == "nbody":
+            nb = 7 + int(u[k, 4] * (nb_max - 6))
+            w = nbody_ensemble(copies=B, nbodies=nb, steps=T, seed_id=sid)
+            req = dict(kind="nbody", params=w["params"], dim=3 * nb, q0=w["q0"], v0=w["v0"],
+                       h=float(w["h"][0]), nsteps=T)
+        else:
+            nn = 8 + int(u[k, 5] * (n_max - 7))
+            c = fput_chain(nn)
+            q = np.repeat(c["q"][None, :], B, axis=0) * (1.0 + 1e-8 * (2 * uniform(SEED_BASE + sid, B * nn).reshape(B, nn) - 1))
+            req = dict(kind="fput", params=c["params"], dim=nn, q0=q, v0=np.zeros((B, nn)),
+                       h=DEFAULT_STEP_TABLE["fput"]["h"], nsteps=T)
+        req["arrival"] = float(t[k])
+        req["rid"] = k
+        out.append(req)
+    return out

@@ -1,0 +1,107 @@
+"""The fixed-point stage mixing (IRKGL_OPT_MIX = 1) against exact rational
+arithmetic, and the mixed kernel against the oracle.
+
+sum_j eta_ij R_j is formed exactly in 128-bit integers and rounded once, so
+for columns whose R_j lie within a factor 2^8 of the largest the result must
+equal the correctly rounded value of the exact sum bit for bit."""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from oracle import cbind, coeffs
+from paper_2511_03655_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import torch
+    from paper_2511_03655_gb300 import build, irkgl
+    build.build()
+    irkgl.load()
+    return torch, irkgl
+
+
+def test_fixed_mix_is_correctly_rounded(lib):
+    torch, irkgl = lib
+    eta = coeffs.fp64_tables()["eta"]
+    rng = np.random.default_rng(11)
+    n = 400
+    scale = 10.0 ** rng.uniform(-12, 2, size=(n, 1))
+    sign = np.where(rng.uniform(size=(n, 8)) < 0.5, -1.0, 1.0)
+    # magnitudes within a factor 2^8 of each other (the exact regime)
+    R = sign * scale * (1.0 + rng.uniform(size=(n, 8))) * 2.0 ** rng.integers(0, 7, size=(n, 8))
+    R[0] = 0.0                       # all zero
+    R[1, :4] = 0.0                   # some zero
+    R[2] = -R[3]                     # signs flipped
+    out = irkgl.irkgl_diag_fixed_mix(torch.tensor(R, device="cuda")).cpu().numpy()
+    for x in range(n):
+        for i in range(8):
+            exact = sum(Fraction(eta[i][j]) * Fraction(float(R[x, j])) for j in range(8))
+            assert out[x, i, 0] == float(exact), (x, i)
+
+
+def test_fixed_mix_nonfinite_propagates(lib):
+    torch, irkgl = lib
+    R = np.ones((2, 8))
+    R[0, 3] = np.inf
+    R[1, 5] = np.nan
+    out = irkgl.irkgl_diag_fixed_mix(torch.tensor(R, device="cuda")).cpu().numpy()
+    assert np.isnan(out).all()
+
+
+@pytest.mark.parametrize("block", [128, 64])
+def test_mixed_kernel_kepler_parity(lib, block):
+    torch, irkgl = lib
+    w = workloads.kepler_single()
+    h = float(w["h"][0])
+    integ = irkgl.Integrator(irkgl.RHS_KEPLER, [1.0], 2, h, mix=1, block_threads=block)
+    assert integ.tile == 1
+    q, v = torch.tensor(w["q0"], device="cuda"), torch.tensor(w["v0"], device="cuda")
+    ql, vl = torch.zeros_like(q), torch.zeros_like(v)
+    rp = torch.zeros((1, 8, 2), dtype=torch.float64, device="cuda")
+    st = dict(q=w["q0"], v=w["v0"], q_lo=None, v_lo=None, r_prev=None)
+    for s in range(10):
+        integ.step(q, v, ql, vl, rp, nsteps=1)
+        r = cbind.run(cbind.KEPLER, [1.0], st["q"], st["v"], h, 1, q_lo=st["q_lo"],
+                      v_lo=st["v_lo"], r_prev=st["r_prev"])
+        st = dict(q=r["q"], v=r["v"], q_lo=r["q_lo"], v_lo=r["v_lo"], r_prev=r["r_prev"])
+        g = np.concatenate([q.cpu().numpy(), v.cpu().numpy()], axis=1)
+        e = np.concatenate([r["q"], r["v"]], axis=1)
+        assert (np.abs(g - e).max() / np.abs(e).max()) <= 1e-13, s
+    it = torch.zeros((1, 1000), dtype=torch.int32, device="cuda")
+    q, v = torch.tensor(w["q0"], device="cuda"), torch.tensor(w["v0"], device="cuda")
+    integ.step(q, v, torch.zeros_like(q), torch.zeros_like(v), torch.zeros_like(rp), nsteps=1000,
+               iters=it)
+    r = cbind.run(cbind.KEPLER, [1.0], w["q0"], w["v0"], w["h"], 1000, iters_len=1000)
+    diff = it.cpu().numpy()[0] - r["iters"][0]
+    assert np.abs(diff).max() <= 1 and (diff == 0).mean() > 0.8
+    out = integ.integrate(torch.tensor(w["q0"], device="cuda"), torch.tensor(w["v0"], device="cuda"),
+                          nsteps_all=20000)
+    torch.cuda.synchronize()
+    r = cbind.run(cbind.KEPLER, [1.0], w["q0"], w["v0"], w["h"], 20000)
+    g = np.concatenate([out.q.cpu().numpy(), out.v.cpu().numpy()], axis=1)
+    e = np.concatenate([r["q"], r["v"]], axis=1)
+    assert np.abs(g - e).max() / np.abs(e).max() <= 1e-9
+    assert out.dH_max.item() <= 1e-13
+    integ.close()
+
+
+def test_mixed_kernel_ensemble(lib):
+    torch, irkgl = lib
+    w = workloads.kepler_ensemble(batch=2048, periods=2)
+    integ = irkgl.Integrator(irkgl.RHS_KEPLER, [1.0], 2, 0.01, mix=1)
+    out = integ.integrate(torch.tensor(w["q0"], device="cuda"), torch.tensor(w["v0"], device="cuda"),
+                          nsteps=torch.tensor(w["nsteps"], device="cuda"),
+                          h=torch.tensor(w["h"], device="cuda"))
+    torch.cuda.synchronize()
+    r = cbind.run(cbind.KEPLER, [1.0], w["q0"], w["v0"], w["h"], w["nsteps"], nthreads=8)
+    g = np.concatenate([out.q.cpu().numpy(), out.v.cpu().numpy()], axis=1)
+    e = np.concatenate([r["q"], r["v"]], axis=1)
+    assert (np.abs(g - e).max(axis=1) / np.abs(e).max(axis=1)).max() <= 1e-11
+    assert (out.status.cpu().numpy() == 0).all()
+    ig = out.iters.cpu().numpy()
+    assert (np.abs(ig - r["iters_total"]) <= 0.1 * r["iters_total"] + 2).all()
+    integ.close()

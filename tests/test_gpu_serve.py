@@ -1,0 +1,79 @@
+"""The continuous-batching server: every request's result is the same alone and
+in the mix (bitwise: a chunked run continues exactly), admission respects the
+memory budget, and results agree with the oracle."""
+import copy
+
+import numpy as np
+import pytest
+
+from oracle import cbind
+from paper_2511_03655_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def server_mod():
+    import torch
+    from paper_2511_03655_gb300 import build, irkgl, serve
+    build.build()
+    irkgl.load()
+    torch.cuda.init()
+    return serve
+
+
+def small_requests(n=14):
+    return workloads.serving_requests(n=n, rate=4000.0, batch_max=64, horizon_max=400, nb_max=12,
+                                      n_max=96)
+
+
+def test_result_same_alone_and_in_mix(server_mod):
+    serve = server_mod
+    descs = small_requests()
+    mix = serve.make_requests(copy.deepcopy(descs))
+    st = serve.Server(nstreams=8, chunk_traj_steps=2e3).run(mix)
+    assert st.summary()["requests"] == len(descs)
+    assert st.max_concurrent > 1  # requests really overlapped
+    for d, r in zip(descs, mix):
+        alone = serve.make_requests([copy.deepcopy(d)])
+        serve.Server(nstreams=1, chunk_traj_steps=7e2).run(alone)  # different chunking too
+        a = alone[0]
+        assert (r.status == 0).all() and (a.status == 0).all()
+        assert np.array_equal(r.q, a.q) and np.array_equal(r.v, a.v), d["kind"]
+        assert np.array_equal(r.iters, a.iters) and np.array_equal(r.dH_max, a.dH_max)
+
+
+def test_mix_matches_single_launch(server_mod):
+    serve = server_mod
+    descs = small_requests(8)
+    mix = serve.make_requests(copy.deepcopy(descs))
+    serve.Server(nstreams=4, chunk_traj_steps=1e3).run(mix)
+    plain = serve.make_requests(copy.deepcopy(descs))
+    serve.run_plain(plain)
+    for r, p in zip(mix, plain):
+        assert np.array_equal(r.q, p.q) and np.array_equal(r.v, p.v), r.kind
+        assert np.array_equal(r.iters, p.iters)
+
+
+def test_admission_by_memory_budget(server_mod):
+    serve = server_mod
+    descs = small_requests(6)
+    reqs = serve.make_requests(copy.deepcopy(descs))
+    budget = max(r.device_bytes() for r in reqs)  # one request at a time fits
+    st = serve.Server(mem_budget_bytes=budget, nstreams=4).run(reqs)
+    s = st.summary()
+    assert s["requests"] == 6 and st.max_concurrent == 1 and st.peak_bytes <= budget
+    assert all(r.q is not None for r in reqs)
+
+
+def test_served_results_match_oracle(server_mod):
+    serve = server_mod
+    descs = [d for d in small_requests(20) if d["kind"] in ("kepler", "fput")][:4]
+    reqs = serve.make_requests(copy.deepcopy(descs))
+    serve.Server(nstreams=4, chunk_traj_steps=1e3).run(reqs)
+    for r in reqs:
+        kind = cbind.KEPLER if r.kind == "kepler" else cbind.FPUT
+        o = cbind.run(kind, r.params, r.q0, r.v0, r.h, r.nsteps, nthreads=8)
+        g = np.concatenate([r.q, r.v], axis=1)
+        e = np.concatenate([o["q"], o["v"]], axis=1)
+        assert (np.abs(g - e).max(axis=1) / np.abs(e).max(axis=1)).max() <= 1e-11, r.kind
