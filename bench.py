@@ -216,27 +216,13 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
 
-    def barrier():
-        if world > 1:
-            dist.barrier()
-
-    def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    def sum_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
+    from paper_2511_03655_gb300 import dist as pdist
+    barrier, max_over_ranks, sum_over_ranks = pdist.barrier, pdist.reduce_max, pdist.reduce_sum
 
     # ---- workload (rank r draws its own ensemble; rank 0 is the standard one)
     if args.workload == "kepler":
-        w = workloads.kepler_ensemble(batch=args.batch, periods=args.periods, seed_id=2 + 1000 * rank)
+        w = workloads.kepler_ensemble(batch=args.batch, periods=args.periods,
+                                      seed_id=pdist.shard_seed(2, rank))
         order = (np.arange(args.batch, dtype=np.int32) if args.no_order
                  else workloads.similarity_order(w["e"]))
         kind, fps, fpw = irkgl.RHS_KEPLER, FLOPS_PER_STEP, FLOPS_PER_SWEEP
@@ -244,7 +230,8 @@ def main():
                 "h=2pi/round(200+100e), one persistent launch")
     else:
         args.batch = min(args.batch, 16384)
-        w = workloads.nbody_ensemble(copies=args.batch, steps=args.traj_steps, seed_id=3 + 1000 * rank)
+        w = workloads.nbody_ensemble(copies=args.batch, steps=args.traj_steps,
+                                     seed_id=pdist.shard_seed(3, rank))
         order = np.arange(args.batch, dtype=np.int32)
         kind, (fps, fpw) = irkgl.RHS_NBODY, FLOPS_NBODY6
         desc = (f"nbody6_ensemble: {args.batch} copies (1e-8 perturbations) of a 6-body system, "

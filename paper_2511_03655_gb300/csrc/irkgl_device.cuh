@@ -749,11 +749,12 @@ __global__ void __launch_bounds__(BLOCK)
               }
             }
           }
-          // the group stops when every component's condition holds
-          bool stop = cond_own;
+          // the group stops when every component's condition holds (the
+          // shuffle must run on every lane: no short-circuit around it)
+          int stop_i = cond_own ? 1 : 0;
 #pragma unroll
-          for (int off = 1; off < LPT; off <<= 1)
-            stop = stop && __shfl_xor_sync(sweepmask, static_cast<int>(stop), off);
+          for (int off = 1; off < LPT; off <<= 1) stop_i &= __shfl_xor_sync(sweepmask, stop_i, off);
+          const bool stop = stop_i != 0;
           if (bad) {
             st = ST_NONFINITE;
             conv = true;
