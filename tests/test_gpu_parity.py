@@ -194,15 +194,27 @@ def test_other_rhs_parity(torch_cuda, name):
         qo, vo, _ = oracle_steps(kind_o, params, q0, v0, h, 10)
         for s in range(10):
             assert rel_state_diff(qg[:, s], vg[:, s], qo[:, s], vo[:, s]).max() <= 1e-13
+        # sweep counts compared from the identical state at every step: the
+        # GPU state (hi, lo, R_prev) after each step is handed to the oracle,
+        # so only the arithmetic of the step differs.  At h ~ 1 (about five
+        # sweeps per step) the last sweeps sit at the roundoff floor, where
+        # FMA vs separate rounding moves the stop by 1 on many steps and by
+        # 2 on a few (the +-1 bound is checked on the Kepler workloads).
+        diffs = []
+        _, _, _, _, (q, v, ql, vl, rp) = gpu_steps(torch_cuda, kind_g, params, q0, v0, h, 1, lpt=lpt)
+        from paper_2511_03655_gb300 import irkgl as _irkgl
+        integ = _irkgl.Integrator(kind_g, params, q.shape[1], h, lanes_per_traj=lpt)
+        it = torch_cuda.zeros((q.shape[0], 1), dtype=torch_cuda.int32, device="cuda")
+        for _ in range(200):
+            r = cbind.run(kind_o, params, q.cpu().numpy(), v.cpu().numpy(), h, 1, q_lo=ql.cpu().numpy(),
+                          v_lo=vl.cpu().numpy(), r_prev=rp.cpu().numpy(), iters_len=1)
+            integ.step(q, v, ql, vl, rp, nsteps=1, iters=it)
+            diffs.append(it.cpu().numpy()[:, 0] - r["iters"][:, 0])
+        integ.close()
+        diff = np.abs(np.array(diffs))
+        assert diff.max() <= 2 and (diff <= 1).mean() >= 0.95, (diff.max(), (diff <= 1).mean())
         qg, vg, itg, st, _ = gpu_steps(torch_cuda, kind_g, params, q0, v0, h, 300, lpt=lpt, chunk=300)
         r = cbind.run(kind_o, params, q0, v0, h, 300, iters_len=300)
-        # at h ~ 1 these take ~5 sweeps per step; the last sweeps sit at the
-        # roundoff floor, where FMA vs separate rounding moves the stopping
-        # sweep by 1 on about half the steps and by 2 on a few percent (the
-        # +-1 bound is checked on the Kepler workloads); measured on GB300:
-        # max 2, |diff| <= 1 on 95.7 % of Henon-Heiles steps
-        diff = np.abs(itg - r["iters"])
-        assert diff.max() <= 2 and (diff <= 1).mean() >= 0.9, (diff.max(), (diff <= 1).mean())
         assert rel_state_diff(qg[:, -1], vg[:, -1], r["q"], r["v"]).max() <= 1e-11
 
 
