@@ -68,7 +68,12 @@ typedef enum {
                                   params = {G, m_0, ..., m_{N-1}} */
   IRKGL_RHS_FPUT = 3,          /* d = n: FPUT alpha chain, fixed ends; params = {alpha} */
   IRKGL_RHS_HENON_HEILES = 4,  /* d = 2: Henon-Heiles (Sec. 5.1);    params = {lambda} */
-  IRKGL_RHS_HARMONIC = 5       /* any d: g = -omega^2 q;             params = {omega} */
+  IRKGL_RHS_HARMONIC = 5,      /* any d: g = -omega^2 q;             params = {omega} */
+  IRKGL_RHS_HENON_HEILES_FORCED = 6 /* d = 2: the non-autonomous example of Sec. 3,
+                                  g(t, q) with lambda + xi sin t in place of lambda;
+                                  params = {lambda, xi}.  Evaluated at the stage times
+                                  t_n + c_i h.  Time starts at 0 except through
+                                  irkgl_advance_t; the energy monitor is off (dH_max = 0) */
 } irkgl_rhs_kind;
 
 typedef struct {
@@ -184,6 +189,28 @@ int irkgl_advance(struct irkgl_ctx* ctx, double* q, double* v, double* q_lo, dou
                   double* r_prev, const double* h, const long long* nsteps, double* H0,
                   int h0_init, double* dH_max, long long* iters, int* status, int batch,
                   void* cuda_stream);
+
+/* irkgl_advance for a right-hand side that depends on t (IRKGL_RHS_HENON_HEILES_FORCED),
+ * with the time carried alongside the state.  Each trajectory starts at
+ * t_n = t[b] + t_lo[b]; g is evaluated at the stage times fl(t[b] + fl(h c_i))
+ * (Eq. IRK_FP, first line, with the time split off by the paper's
+ * compensated-sum device of Sec. 5), and after every step (t, t_lo) gains h
+ * by the same TwoSum + Fast2Sum update as q and v, so chunked runs give the
+ * bits of one run.  Device arrays, [batch] unless noted:
+ *   q, v, q_lo, v_lo [batch][dim], r_prev [batch][8][dim]   in/out (required)
+ *   t        in/out time, hi part (required)
+ *   t_lo     in/out time, compensation part; NULL = 0, not written back
+ *   h        per-trajectory step, or NULL for the context's h
+ *   nsteps   steps to take in this call (required)
+ *   iters    in/out running total of sweeps (NULL = not tracked)
+ *   status   out: IRKGL_STATUS_* of this call (NULL = not wanted)
+ * No energy monitor (H(t) is not conserved).  Errors: IRKGL_ERR_INVALID (also
+ * for a context whose right-hand side does not read t), IRKGL_ERR_UNSUPPORTED,
+ * IRKGL_ERR_CUDA. */
+int irkgl_advance_t(struct irkgl_ctx* ctx, double* q, double* v, double* q_lo, double* v_lo,
+                    double* r_prev, double* t, double* t_lo, const double* h,
+                    const long long* nsteps, long long* iters, int* status, int batch,
+                    void* cuda_stream);
 
 /* Integrate `batch` independent initial states (device arrays q0, v0
  * [batch][dim], R_prev = 0, lo = 0) in one persistent launch.

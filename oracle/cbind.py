@@ -21,7 +21,7 @@ SRC = os.path.join(HERE, "irkgl_oracle.c")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD_DIR, "liborc.so")
 
-KEPLER, NBODY, FPUT, HENON_HEILES, HARMONIC = 1, 2, 3, 4, 5
+KEPLER, NBODY, FPUT, HENON_HEILES, HARMONIC, HH_FORCED = 1, 2, 3, 4, 5, 6
 _lock = threading.Lock()
 _lib = None
 
@@ -61,6 +61,9 @@ def lib():
                 P(ctypes.c_longlong), ctypes.c_int, P(ctypes.c_int), ctypes.c_int,
                 P(ctypes.c_longlong), P(ctypes.c_double), P(ctypes.c_int),
                 P(ctypes.c_longlong), ctypes.c_int]
+            L.orc_run_t.restype = ctypes.c_int
+            L.orc_run_t.argtypes = (L.orc_run.argtypes[:11] + [P(ctypes.c_double), P(ctypes.c_double)]
+                                    + L.orc_run.argtypes[11:])
             L.orc_hamiltonian.restype = ctypes.c_double
             L.orc_hamiltonian.argtypes = [ctypes.c_int, P(ctypes.c_double), ctypes.c_int,
                                           P(ctypes.c_double), P(ctypes.c_double)]
@@ -88,13 +91,16 @@ def _ptr(a, ctype):
 
 
 def run(kind: int, params, q, v, h, nsteps, *, q_lo=None, v_lo=None, r_prev=None,
-        iters_len: int = 0, kmax: int = 100, nthreads: int = 1, tab: dict | None = None):
+        t0=None, t_lo=None, iters_len: int = 0, kmax: int = 100, nthreads: int = 1,
+        tab: dict | None = None):
     """Advance a batch with the C oracle.
 
     q, v: (batch, d) float64.  params: (P,) shared or (batch, P) per
-    trajectory.  h: scalar or (batch,).  nsteps: int or (batch,).
-    Returns a dict of numpy arrays: q, v, q_lo, v_lo, r_prev (batch, 8, d),
-    iters (batch, iters_len), iters_total, dH_max, status, steps.
+    trajectory.  h: scalar or (batch,).  nsteps: int or (batch,).  t0, t_lo:
+    scalar or (batch,) start time as a compensated pair (default 0; read
+    only by a time-dependent g).  Returns a dict of numpy arrays: q, v, q_lo,
+    v_lo, r_prev (batch, 8, d), t, t_lo, iters (batch, iters_len),
+    iters_total, dH_max, status, steps.
     """
     q = np.array(q, dtype=np.float64, order="C", copy=True)
     v = np.array(v, dtype=np.float64, order="C", copy=True)
@@ -116,18 +122,21 @@ def run(kind: int, params, q, v, h, nsteps, *, q_lo=None, v_lo=None, r_prev=None
     dH = np.zeros(batch, dtype=np.float64)
     st = np.zeros(batch, dtype=np.int32)
     steps = np.zeros(batch, dtype=np.int64)
+    th = np.array(np.broadcast_to(np.asarray(0.0 if t0 is None else t0, dtype=np.float64), (batch,)))
+    tl = np.array(np.broadcast_to(np.asarray(0.0 if t_lo is None else t_lo, dtype=np.float64), (batch,)))
     t = table(tab)
-    rc = lib().orc_run(ctypes.byref(t), kind, _ptr(params, ctypes.c_double), pstride, d, batch,
+    rc = lib().orc_run_t(ctypes.byref(t), kind, _ptr(params, ctypes.c_double), pstride, d, batch,
                        _ptr(q, ctypes.c_double), _ptr(v, ctypes.c_double),
                        _ptr(q_lo, ctypes.c_double), _ptr(v_lo, ctypes.c_double),
-                       _ptr(r_prev, ctypes.c_double), _ptr(hh, ctypes.c_double),
+                       _ptr(r_prev, ctypes.c_double), _ptr(th, ctypes.c_double),
+                       _ptr(tl, ctypes.c_double), _ptr(hh, ctypes.c_double),
                        _ptr(ns, ctypes.c_longlong), kmax,
                        _ptr(iters, ctypes.c_int) if iters_len > 0 else None, iters_len,
                        _ptr(tot, ctypes.c_longlong), _ptr(dH, ctypes.c_double),
                        _ptr(st, ctypes.c_int), _ptr(steps, ctypes.c_longlong), nthreads)
     if rc != 0:
         raise MemoryError("oracle allocation failed")
-    return {"q": q, "v": v, "q_lo": q_lo, "v_lo": v_lo, "r_prev": r_prev,
+    return {"q": q, "v": v, "q_lo": q_lo, "v_lo": v_lo, "r_prev": r_prev, "t": th, "t_lo": tl,
             "iters": iters[:, :iters_len], "iters_total": tot, "dH_max": dH,
             "status": st, "steps": steps}
 

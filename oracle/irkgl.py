@@ -118,6 +118,50 @@ def sqrt(x):
     return x.sqrt()
 
 
+def sin(x):
+    """sin of a float (the C library's) or of a Decimal (Taylor series at the
+    current context precision, argument reduced by multiples of 2 pi)."""
+    if isinstance(x, float):
+        return math.sin(x)
+    if isinstance(x, Decimal):
+        from decimal import getcontext, localcontext
+        prec = getcontext().prec
+        with localcontext() as ctx:
+            ctx.prec = prec + 10
+            two_pi = 2 * _dec_pi()
+            y = x - two_pi * (x / two_pi).to_integral_value()
+            term, acc, k = y, y, 1
+            eps = Decimal(10) ** (-(prec + 5))
+            while abs(term) > eps:
+                term = -term * y * y / ((2 * k) * (2 * k + 1))
+                acc += term
+                k += 1
+        return +acc
+    raise TypeError("sin: unsupported scalar type %r" % type(x))
+
+
+def _dec_pi():
+    """pi at the current Decimal precision (Machin's formula)."""
+    from decimal import getcontext, localcontext
+    prec = getcontext().prec
+    with localcontext() as ctx:
+        ctx.prec = prec + 10
+
+        def arctan_inv(n):
+            x = Decimal(1) / n
+            x2 = x * x
+            term, acc, k = x, x, 1
+            eps = Decimal(10) ** (-(prec + 8))
+            while abs(term) > eps:
+                term = -term * x2
+                acc += term / (2 * k + 1)
+                k += 1
+            return acc
+
+        pi = 16 * arctan_inv(5) - 4 * arctan_inv(239)
+    return +pi
+
+
 def zero_like(x):
     """An exact zero of the same scalar type as x."""
     if isinstance(x, Dual):
@@ -171,6 +215,32 @@ class HenonHeiles:
     def H(self, q, v):
         return ((v[0] * v[0] + v[1] * v[1]) / 2 + (q[0] * q[0] + q[1] * q[1]) / 2
                 + self.lam * (q[0] * q[0] * q[1] - q[1] * q[1] * q[1] / 3))
+
+
+class HenonHeilesForced:
+    """The non-autonomous Henon-Heiles system printed in Sec. 3 (the user
+    function example): q1'' = -q1 - 2 (lam + xi sin t) q1 q2,
+    q2'' = -q2 - (lam + xi sin t) (q1^2 - q2^2).  xi = 0 gives HenonHeiles.
+    g depends on t, so the step evaluates it at the stage times t_n + c_i h
+    (Eq. IRK_FP, first line).  H is the Hamiltonian at time t; it is not
+    conserved when xi != 0."""
+
+    d = 2
+    time_dependent = True
+
+    def __init__(self, lam=1.0, xi=0.0):
+        self.lam = lam
+        self.xi = xi
+
+    def g(self, q, t):
+        aux = self.lam + self.xi * sin(t)
+        return [-q[0] - 2 * aux * q[0] * q[1],
+                -q[1] - aux * (q[0] * q[0] - q[1] * q[1])]
+
+    def H(self, q, v, t=0.0):
+        aux = self.lam + self.xi * sin(t)
+        return ((v[0] * v[0] + v[1] * v[1]) / 2 + (q[0] * q[0] + q[1] * q[1]) / 2
+                + aux * (q[0] * q[0] * q[1] - q[1] * q[1] * q[1] / 3))
 
 
 class Harmonic:
@@ -303,11 +373,16 @@ def stop_test(delta, dmin, dprev):
 # --------------------------------------------------------------------------
 # the step
 # --------------------------------------------------------------------------
+def stage_times(t, h, c):
+    """t_n + c_i h for i = 1..s (Eq. IRK_FP, first line), h c_i rounded first."""
+    return [t + h * c[i] for i in range(S)]
+
+
 class State:
     """Trajectory state: compensated positions/velocities and the previous
     step's increments R (used by the extrapolated initial guess)."""
 
-    def __init__(self, q, v, q_lo=None, v_lo=None, r_prev=None):
+    def __init__(self, q, v, q_lo=None, v_lo=None, r_prev=None, t=None, t_lo=None):
         d = len(q)
         zero = zero_like(q[0])
         self.q = list(q)
@@ -316,9 +391,13 @@ class State:
         self.v_lo = list(v_lo) if v_lo is not None else [zero] * d
         self.r_prev = ([list(r) for r in r_prev] if r_prev is not None
                        else [[zero] * d for _ in range(S)])
+        # time t_n as a compensated pair (only read by time-dependent g)
+        zt = Decimal(0) if isinstance(value(q[0]), Decimal) else 0.0
+        self.t = t if t is not None else zt
+        self.t_lo = t_lo if t_lo is not None else zero_like(self.t)
 
     def copy(self):
-        return State(self.q, self.v, self.q_lo, self.v_lo, self.r_prev)
+        return State(self.q, self.v, self.q_lo, self.v_lo, self.r_prev, self.t, self.t_lo)
 
 
 def step(state: State, h, tab: dict, rhs, kmax: int = KMAX, diag: dict | None = None):
@@ -356,6 +435,11 @@ def step(state: State, h, tab: dict, rhs, kmax: int = KMAX, diag: dict | None = 
     if diag is not None:
         diag["Q0"] = [list(r) for r in Q]
 
+    # stage times t_n + c_i h of a time-dependent g (Eq. IRK_FP, first
+    # line): h c_i rounded, then added to the hi part of t_n
+    timed = getattr(rhs, "time_dependent", False)
+    tau = stage_times(state.t, h, c) if timed else None
+
     # --- fixed-point sweeps, Eq. IRK_FP2 + stopping rule ------------------
     inf = float("inf")
     dmin = [inf] * d    # min(Delta^[1..k-2])
@@ -363,7 +447,10 @@ def step(state: State, h, tab: dict, rhs, kmax: int = KMAX, diag: dict | None = 
     k = 0
     while True:
         k += 1
-        G = [rhs.g(Q[i]) for i in range(S)]
+        if timed:
+            G = [rhs.g(Q[i], tau[i]) for i in range(S)]
+        else:
+            G = [rhs.g(Q[i]) for i in range(S)]
         R = [[h * (b[i] * G[i][l]) for l in range(d)] for i in range(S)]
         Qn = []
         for i in range(S):
@@ -395,7 +482,7 @@ def step(state: State, h, tab: dict, rhs, kmax: int = KMAX, diag: dict | None = 
             return state.copy(), k, MAXITER
 
     # --- update, Eq. qnvn2 with compensated sums --------------------------
-    new = State(state.q, state.v, state.q_lo, state.v_lo, R)
+    new = State(state.q, state.v, state.q_lo, state.v_lo, R, state.t, state.t_lo)
     for l in range(d):
         sR = R[0][l]
         for i in range(1, S):
@@ -407,19 +494,23 @@ def step(state: State, h, tab: dict, rhs, kmax: int = KMAX, diag: dict | None = 
         dq = h * vh + (h * vl - h * scR)
         qh, ql = two_sum_add(state.q[l], state.q_lo[l], dq)
         new.q[l], new.q_lo[l], new.v[l], new.v_lo[l] = qh, ql, vh, vl
+    # t_{n+1} = t_n + h, compensated like the state
+    new.t, new.t_lo = two_sum_add(state.t, state.t_lo, h)
     return new, k, OK
 
 
-def integrate(q0, v0, h, nsteps, tab, rhs, kmax=KMAX, record=None):
-    """Run ``nsteps`` steps from (q0, v0) with Rprev = 0.
+def integrate(q0, v0, h, nsteps, tab, rhs, kmax=KMAX, record=None, t0=None):
+    """Run ``nsteps`` steps from (q0, v0) at time t0 (default 0) with Rprev = 0.
 
     Returns a dict with the final state, per-step iteration counts, the
     status, steps completed and max_n |(H_n - H_0)/H_0| (Eq. DHglobmax,
-    evaluated on the hi parts).  ``record`` (a list) receives (q, v) after
-    every step when given.
+    evaluated on the hi parts; 0 for a time-dependent g, whose H is not
+    conserved).  ``record`` (a list) receives (q, v) after every step when
+    given.
     """
-    st = State(q0, v0)
-    H0 = rhs.H(st.q, st.v)
+    st = State(q0, v0, t=t0)
+    timed = getattr(rhs, "time_dependent", False)
+    H0 = None if timed else rhs.H(st.q, st.v)
     dmax = 0.0
     iters = []
     status = OK
@@ -431,10 +522,11 @@ def integrate(q0, v0, h, nsteps, tab, rhs, kmax=KMAX, record=None):
             n -= 1
             break
         st = st2
-        Hn = rhs.H(st.q, st.v)
-        dH = abs(value((Hn - H0) / H0))
-        if dH > dmax:
-            dmax = dH
+        if not timed:
+            Hn = rhs.H(st.q, st.v)
+            dH = abs(value((Hn - H0) / H0))
+            if dH > dmax:
+                dmax = dH
         if record is not None:
             record.append((list(st.q), list(st.v)))
     return {"state": st, "iters": iters, "status": status, "steps": n, "dH_max": dmax}

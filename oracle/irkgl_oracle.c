@@ -26,7 +26,16 @@ typedef struct {
   double c[S], b[S], mu[S * S], eta[S * S], nu[S * S]; /* row-major [i*8+j] */
 } orc_tab;
 
-enum { ORC_KEPLER = 1, ORC_NBODY = 2, ORC_FPUT = 3, ORC_HENON_HEILES = 4, ORC_HARMONIC = 5 };
+enum {
+  ORC_KEPLER = 1,
+  ORC_NBODY = 2,
+  ORC_FPUT = 3,
+  ORC_HENON_HEILES = 4,
+  ORC_HARMONIC = 5,
+  ORC_HH_FORCED = 6 /* the non-autonomous example of Sec. 3: lam + xi sin t */
+};
+
+static int time_dependent(int kind) { return kind == ORC_HH_FORCED; }
 enum { ORC_OK = 0, ORC_MAXITER = 1, ORC_NONFINITE = 2 };
 
 /* ---------------- right-hand sides g(q) and Hamiltonians ---------------- */
@@ -38,7 +47,8 @@ static double bond(const double* q, int d, int j) {
   return right - left;
 }
 
-static void rhs_g(int kind, const double* p, int d, const double* q, double* g) {
+/* g(t, q); only ORC_HH_FORCED reads t. */
+static void rhs_g(int kind, const double* p, int d, const double* q, double* g, double t) {
   switch (kind) {
     case ORC_KEPLER: {
       double mu = p[0];
@@ -52,6 +62,12 @@ static void rhs_g(int kind, const double* p, int d, const double* q, double* g) 
       double lam = p[0];
       g[0] = -q[0] - 2.0 * lam * q[0] * q[1];
       g[1] = -q[1] - lam * (q[0] * q[0] - q[1] * q[1]);
+      break;
+    }
+    case ORC_HH_FORCED: {
+      double aux = p[0] + p[1] * sin(t);
+      g[0] = -q[0] - 2.0 * aux * q[0] * q[1];
+      g[1] = -q[1] - aux * (q[0] * q[0] - q[1] * q[1]);
       break;
     }
     case ORC_HARMONIC: {
@@ -158,10 +174,14 @@ static void two_sum_add(double* hi, double* lo, double x) {
 }
 
 /* One step for one trajectory; work arrays sized 5*S*d + 3*d doubles.
- * Returns the status; *k receives the number of sweeps. */
+ * (*th, *tl) is the time t_n as a compensated pair; a time-dependent g is
+ * evaluated at the stage times *th + h c_i.  Returns the status; *k
+ * receives the number of sweeps. */
 static int one_step(const orc_tab* t, int kind, const double* p, int d, double h, int kmax,
-                    double* q, double* v, double* qlo, double* vlo, double* rp, int* kout,
-                    double* work) {
+                    double* q, double* v, double* qlo, double* vlo, double* rp, double* th,
+                    double* tl, int* kout, double* work) {
+  double tau[S];
+  for (int i = 0; i < S; i++) tau[i] = *th + h * t->c[i];
   double* V = work;             /* S*d, reused as Lq */
   double* Q = V + S * d;        /* S*d */
   double* Qn = Q + S * d;       /* S*d */
@@ -194,7 +214,7 @@ static int one_step(const orc_tab* t, int kind, const double* p, int d, double h
   int k = 0;
   for (;;) {
     k++;
-    for (int i = 0; i < S; i++) rhs_g(kind, p, d, Q + i * d, G + i * d);
+    for (int i = 0; i < S; i++) rhs_g(kind, p, d, Q + i * d, G + i * d, tau[i]);
     for (int i = 0; i < S; i++)
       for (int l = 0; l < d; l++) R[i * d + l] = h * (t->b[i] * G[i * d + l]);
     int finite = 1;
@@ -249,6 +269,7 @@ static int one_step(const orc_tab* t, int kind, const double* p, int d, double h
     vlo[l] = vl;
   }
   memcpy(rp, R, sizeof(double) * S * d);
+  two_sum_add(th, tl, h); /* t_{n+1} = t_n + h */
   return ORC_OK;
 }
 
@@ -258,6 +279,7 @@ typedef struct {
   const double* params;
   int pstride, d, batch;
   double *q, *v, *qlo, *vlo, *rp;
+  double *t_hi, *t_lo; /* may be NULL: time starts at 0 and is not returned */
   const double* h;
   const long long* nsteps;
   int kmax;
@@ -286,16 +308,21 @@ static void* run_range(void* arg) {
     double* ql = J->qlo + (size_t)t * d;
     double* vl = J->vlo + (size_t)t * d;
     double* rp = J->rp + (size_t)t * S * d;
-    double H0 = rhs_H(J->kind, p, d, q, v);
+    double th0 = 0.0, tl0 = 0.0;
+    double* th = J->t_hi ? J->t_hi + t : &th0;
+    double* tl = J->t_lo ? J->t_lo + t : &tl0;
+    const int timed = time_dependent(J->kind);
+    double H0 = timed ? 0.0 : rhs_H(J->kind, p, d, q, v);
     double dmax = 0.0;
     long long tot = 0, n = 0;
     int st = ORC_OK;
     for (n = 0; n < J->nsteps[t]; n++) {
       int k = 0;
-      st = one_step(J->tab, J->kind, p, d, J->h[t], J->kmax, q, v, ql, vl, rp, &k, work);
+      st = one_step(J->tab, J->kind, p, d, J->h[t], J->kmax, q, v, ql, vl, rp, th, tl, &k, work);
       if (J->iters && n < J->iters_stride) J->iters[(size_t)t * J->iters_stride + n] = k;
       tot += k;
       if (st != ORC_OK) break;
+      if (timed) continue; /* H(t) is not conserved: no monitor */
       double Hn = rhs_H(J->kind, p, d, q, v);
       double dH = fabs((Hn - H0) / H0);
       if (dH > dmax) dmax = dH;
@@ -311,7 +338,8 @@ static void* run_range(void* arg) {
 
 /*
  * Advance `batch` independent trajectories of dimension d (positions) by
- * nsteps[t] steps of size h[t].  State arrays are trajectory-major and are
+ * nsteps[t] steps of size h[t].  t_hi, t_lo [batch] (may be NULL) hold each
+ * trajectory's time t_n as a compensated pair, read and updated in place.  State arrays are trajectory-major and are
  * updated in place: q, v, q_lo, v_lo [batch*d], r_prev [batch*8*d].
  * params points at the right-hand-side parameters of trajectory 0;
  * trajectory t uses params + t*pstride (pstride 0: shared).
@@ -320,11 +348,11 @@ static void* run_range(void* arg) {
  * H_0 at entry), status, steps_done.  nthreads >= 1 splits the batch into
  * contiguous ranges.  Returns 0, or -1 on allocation failure.
  */
-int orc_run(const orc_tab* tab, int kind, const double* params, int pstride, int d, int batch,
-            double* q, double* v, double* q_lo, double* v_lo, double* r_prev, const double* h,
-            const long long* nsteps, int kmax, int* iters, int iters_stride,
-            long long* iters_total, double* dH_max, int* status, long long* steps_done,
-            int nthreads) {
+int orc_run_t(const orc_tab* tab, int kind, const double* params, int pstride, int d, int batch,
+              double* q, double* v, double* q_lo, double* v_lo, double* r_prev, double* t_hi,
+              double* t_lo, const double* h, const long long* nsteps, int kmax, int* iters,
+              int iters_stride, long long* iters_total, double* dH_max, int* status,
+              long long* steps_done, int nthreads) {
   if (nthreads < 1) nthreads = 1;
   if (nthreads > batch) nthreads = batch > 0 ? batch : 1;
   job_t* jobs = (job_t*)calloc((size_t)nthreads, sizeof(job_t));
@@ -347,6 +375,8 @@ int orc_run(const orc_tab* tab, int kind, const double* params, int pstride, int
     J->qlo = q_lo;
     J->vlo = v_lo;
     J->rp = r_prev;
+    J->t_hi = t_hi;
+    J->t_lo = t_lo;
     J->h = h;
     J->nsteps = nsteps;
     J->kmax = kmax;
@@ -381,6 +411,17 @@ int orc_run(const orc_tab* tab, int kind, const double* params, int pstride, int
   free(jobs);
   free(th);
   return err;
+}
+
+/* orc_run_t without time arrays: every trajectory starts at t = 0. */
+int orc_run(const orc_tab* tab, int kind, const double* params, int pstride, int d, int batch,
+            double* q, double* v, double* q_lo, double* v_lo, double* r_prev, const double* h,
+            const long long* nsteps, int kmax, int* iters, int iters_stride,
+            long long* iters_total, double* dH_max, int* status, long long* steps_done,
+            int nthreads) {
+  return orc_run_t(tab, kind, params, pstride, d, batch, q, v, q_lo, v_lo, r_prev, NULL, NULL, h,
+                   nsteps, kmax, iters, iters_stride, iters_total, dH_max, status, steps_done,
+                   nthreads);
 }
 
 /* H of one state (for tests). */

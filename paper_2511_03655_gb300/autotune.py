@@ -100,7 +100,7 @@ def step_table(quick: bool = False) -> dict:
         table["nbody"]["fraction_of_inner_period"][str(nb)] = best
     # FPUT: absolute step per size bucket
     hs = [0.1, 0.15, 0.2, 0.3, 0.4, 0.5]
-    for n in ([16, 128] if quick else [16, 32, 64, 128, 256, 512, 1024]):
+    for n in ([16, 128] if quick else [16, 32, 64, 128, 256, 512]):
         best = hs[0]
         for h in hs:
             c = workloads.fput_chain(n)

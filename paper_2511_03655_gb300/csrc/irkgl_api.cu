@@ -169,6 +169,8 @@ static int check_rhs(const irkgl_rhs& f, int dim) {
     case IRKGL_RHS_KEPLER:
     case IRKGL_RHS_HENON_HEILES:
       return dim == 2 ? IRKGL_OK : IRKGL_ERR_INVALID;
+    case IRKGL_RHS_HENON_HEILES_FORCED:
+      return (dim == 2 && f.nparams == 2) ? IRKGL_OK : IRKGL_ERR_INVALID;
     case IRKGL_RHS_HARMONIC:
     case IRKGL_RHS_FPUT:
       return IRKGL_OK;
@@ -297,6 +299,9 @@ int irkgl_get_tile(irkgl_ctx* c) {
   return c->lpt ? c->lpt : default_lpt(c->kind, c->dim);
 }
 
+// Right-hand sides that read t: no energy monitor (H(t) is not conserved).
+static bool time_dependent_kind(int kind) { return kind == IRKGL_RHS_HENON_HEILES_FORCED; }
+
 static int run(irkgl_ctx* c, KArgs& a, cudaStream_t st) {
   if (c->mix && !c->default_tables) return IRKGL_ERR_UNSUPPORTED;
   const int lpt = c->mix ? 1 : (c->lpt ? c->lpt : default_lpt(c->kind, c->dim));
@@ -305,7 +310,7 @@ static int run(irkgl_ctx* c, KArgs& a, cudaStream_t st) {
   a.counter = c->d_counter;
   a.params = c->d_params;
   a.kmax = c->kmax;
-  a.monitor = c->monitor;
+  a.monitor = time_dependent_kind(c->kind) ? 0 : c->monitor;
   a.monitor_local = c->monitor_local;
   const int traj_per_block = c->block / lpt;
   long long need = (static_cast<long long>(a.batch) + traj_per_block - 1) / traj_per_block;
@@ -391,6 +396,39 @@ int irkgl_advance(irkgl_ctx* c, double* q, double* v, double* q_lo, double* v_lo
   const int rc = run(c, a, static_cast<cudaStream_t>(stream));
   c->monitor = saved_monitor;
   return rc;
+}
+
+int irkgl_advance_t(irkgl_ctx* c, double* q, double* v, double* q_lo, double* v_lo, double* r_prev,
+                    double* t, double* t_lo, const double* h, const long long* nsteps,
+                    long long* iters, int* status, int batch, void* stream) {
+  if (!c || batch < 0) return IRKGL_ERR_INVALID;
+  if (!time_dependent_kind(c->kind)) return IRKGL_ERR_INVALID;
+  if (batch == 0) return IRKGL_OK;
+  if (!q || !v || !q_lo || !v_lo || !r_prev || !t || !nsteps) return IRKGL_ERR_INVALID;
+  KArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.batch = batch;
+  a.q_in = q;
+  a.v_in = v;
+  a.qlo_in = q_lo;
+  a.vlo_in = v_lo;
+  a.rp_in = r_prev;
+  a.q_out = q;
+  a.v_out = v;
+  a.qlo_out = q_lo;
+  a.vlo_out = v_lo;
+  a.rp_out = r_prev;
+  a.t_in = t;
+  a.tlo_in = t_lo;
+  a.t_out = t;
+  a.tlo_out = t_lo;
+  a.nsteps = nsteps;
+  a.h = h;
+  a.h_all = c->h;
+  a.iters_total = iters;
+  a.status = status;
+  a.accumulate = 1;
+  return run(c, a, static_cast<cudaStream_t>(stream));
 }
 
 int irkgl_integrate(irkgl_ctx* c, const double* q0, const double* v0, int batch,

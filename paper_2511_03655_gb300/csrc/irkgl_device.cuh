@@ -73,6 +73,12 @@ struct KArgs {
   int h0_init;              // 1: compute H0 at the first step and store it in H0_io
   int accumulate;           // 1: dH_max / iters_total start from the values in the arrays
   int monitor_local;        // 1: dH_max = max_n |(H_n - H_{n-1}) / H_{n-1}| (Eq. DHlocmax)
+  // time t_n as a compensated pair, read only by time-dependent right-hand
+  // sides (null in: t = 0; null out: not written)
+  const double* t_in;       // [batch]
+  const double* tlo_in;     // [batch]
+  double* t_out;            // [batch]
+  double* tlo_out;          // [batch]
 };
 
 // ------------------------------------------------------------------------
@@ -345,6 +351,49 @@ struct HenonHeiles {
   }
 };
 
+// The non-autonomous Henon-Heiles system printed with the user-function
+// example of Sec. 3: g1 = -q1 (1 + 2 a(t) q2), g2 = -(q2 + a(t) (q1^2 - q2^2)),
+// a(t) = lam + xi sin t.  g is evaluated at the stage times t_n + c_i h
+// (Eq. IRK_FP, first line); a(t) is formed once per stage per step, since
+// the stage times do not change across the fixed-point sweeps.
+template <int SPL>
+struct HenonHeilesForced {
+  static constexpr int D = 2;
+  static constexpr bool kTime = true;
+  double lam, xi;
+  double s[SPL];             // -(h b_i)
+  double aux[SPL], aux2[SPL];  // a(t_n + c_i h) and twice it
+  __device__ void load_params(const double* p) {
+    lam = p[0];
+    xi = p[1];
+  }
+  __device__ void set_step(const double (&hb)[SPL]) {
+#pragma unroll
+    for (int t = 0; t < SPL; t++) s[t] = -hb[t];
+  }
+  __device__ void set_time(const double (&tau)[SPL]) {
+#pragma unroll
+    for (int t = 0; t < SPL; t++) {
+      aux[t] = fma(xi, sin(tau[t]), lam);
+      aux2[t] = 2.0 * aux[t];
+    }
+  }
+  __device__ __forceinline__ void stage_R(int t, const double (&x)[D], double (&R)[D]) const {
+    const double a = fma(aux2[t], x[1], 1.0);
+    R[0] = s[t] * (x[0] * a);
+    const double u = fma(x[0], x[0], -(x[1] * x[1]));
+    R[1] = s[t] * fma(aux[t], u, x[1]);
+  }
+  // H of the autonomous part; H(t) is not conserved, and the host turns the
+  // energy monitor off for this kind.
+  __device__ double H(const double (&q)[D], const double (&v)[D]) const {
+    const double ke = 0.5 * fma(v[0], v[0], v[1] * v[1]);
+    const double pe = 0.5 * fma(q[0], q[0], q[1] * q[1]);
+    const double cub = fma(q[0] * q[0], q[1], -(q[1] * q[1] * q[1]) * (1.0 / 3.0));
+    return fma(lam, cub, ke + pe);
+  }
+};
+
 template <int SPL, int DD>
 struct Harmonic {
   static constexpr int D = DD;
@@ -456,6 +505,13 @@ struct split_energy : std::false_type {};
 template <class T>
 struct split_energy<T, std::void_t<decltype(T::kSplitH)>> : std::integral_constant<bool, T::kSplitH> {};
 
+// Right-hand sides that read t (g(t, q)) declare kTime = true and provide
+// set_time(stage times of the lane's stages).
+template <class T, class = void>
+struct time_dependent : std::false_type {};
+template <class T>
+struct time_dependent<T, std::void_t<decltype(T::kTime)>> : std::integral_constant<bool, T::kTime> {};
+
 // H(q, v) of the group's trajectory, from the owned components.  Right-hand
 // sides with a split energy (N-body) compute shares on every lane and sum
 // them with a butterfly; the others evaluate H on every lane redundantly.
@@ -511,6 +567,7 @@ __global__ void __launch_bounds__(BLOCK)
   constexpr int SPL = S / LPT;
   constexpr int NS = (D + LPT - 1) / LPT;  // owned component slots per lane
   constexpr int PAD = S + 1;               // padded smem row (bank spread)
+  constexpr bool TIMED = time_dependent<Rhs>::value;
 
   __shared__ double s_eta[(LPT > 1) ? S * PAD : 1];
   __shared__ double s_W[(LPT > 1) ? S * PAD : 1];
@@ -551,6 +608,7 @@ __global__ void __launch_bounds__(BLOCK)
   double h = 0.0, H0 = 0.0, invH0 = 0.0, dHmax = 0.0;
   double Hprev = 0.0, invHprev = 0.0;  // local-error monitor
   long long n = 0, N = 0, itot = 0;
+  double th = 0.0, tl = 0.0;  // t_n (compensated), time-dependent g only
   int traj = -1, st = ST_OK;
   bool active = false, exhausted = false;
 
@@ -616,6 +674,10 @@ __global__ void __launch_bounds__(BLOCK)
 #pragma unroll
             for (int tt = 0; tt < SPL; tt++) hb[tt] = h * cf.b[i0 + tt];
             rhs.set_step(hb);
+            if constexpr (TIMED) {
+              th = a.t_in ? a.t_in[t] : 0.0;
+              tl = a.tlo_in ? a.tlo_in[t] : 0.0;
+            }
           }
         }
       }
@@ -641,6 +703,13 @@ __global__ void __launch_bounds__(BLOCK)
     const bool stepping = active && (n < N);
     const unsigned stepmask = __ballot_sync(FULL, stepping);
     if (stepping) {
+      if constexpr (TIMED) {
+        // stage times t_n + c_i h: h c_i rounded, then added to the hi part
+        double tau[SPL];
+#pragma unroll
+        for (int t = 0; t < SPL; t++) tau[t] = __dadd_rn(th, __dmul_rn(h, cc[t]));
+        rhs.set_time(tau);
+      }
       // init (Eq. IRK_init2 in fused form): Q_i = q + h (c_i v + sum_k W_ik Rprev_k)
 #pragma unroll
       for (int l = 0; l < D; l++) {
@@ -801,6 +870,7 @@ __global__ void __launch_bounds__(BLOCK)
             two_sum_add(qh[s], ql[s], dq);
           }
         }
+        if constexpr (TIMED) two_sum_add(th, tl, h);  // t_{n+1} = t_n + h
         n++;
         if (a.monitor > 0) {
           const bool mon = (n % a.monitor) == 0;  // differs between groups when monitor > 1
@@ -843,6 +913,10 @@ __global__ void __launch_bounds__(BLOCK)
           for (int l = 0; l < D; l++) a.rp_out[roff + (i0 + tt) * D + l] = R[tt][l];
       }
       if (leader) {
+        if constexpr (TIMED) {
+          if (a.t_out) a.t_out[traj] = th;
+          if (a.tlo_out) a.tlo_out[traj] = tl;
+        }
         if (a.dH_max) a.dH_max[traj] = dHmax;
         if (a.iters_total) a.iters_total[traj] = itot;
         if (a.status) a.status[traj] = st;

@@ -22,6 +22,7 @@ OK = 0
 ERR_INVALID, ERR_NOMEM, ERR_CUDA, ERR_UNSUPPORTED = -1, -2, -3, -4
 STATUS_OK, STATUS_MAXITER, STATUS_NONFINITE = 0, 1, 2
 RHS_KEPLER, RHS_NBODY, RHS_FPUT, RHS_HENON_HEILES, RHS_HARMONIC = 1, 2, 3, 4, 5
+RHS_HENON_HEILES_FORCED = 6  # g(t, q): lambda + xi sin t (params = [lambda, xi])
 OPT_LANES_PER_TRAJ, OPT_KMAX, OPT_MONITOR_EVERY, OPT_BLOCK_THREADS, OPT_GRID_BLOCKS = 1, 2, 3, 4, 5
 OPT_WIDE_TEAM = 6
 OPT_MONITOR_LOCAL = 7
@@ -97,6 +98,7 @@ def load(path: str | None = None, build_if_missing: bool = False):
     L.irkgl_probe_fp64_fma.argtypes = [_P, ctypes.POINTER(ctypes.c_longlong), _P]
     L.irkgl_advance.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int, _P, _P, _P,
                                 ctypes.c_int, _P]
+    L.irkgl_advance_t.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int, _P]
     L.irkgl_diag_fixed_mix.argtypes = [_P, _P, ctypes.c_int, _P]
     L.irkgl_advance_ragged.argtypes = [_P, _P, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P, _P,
                                        _P, _P, ctypes.c_int, _P, _P, _P, _P]
@@ -236,6 +238,22 @@ def irkgl_advance(ctx: int, dim: int, q, v, q_lo, v_lo, r_prev, nsteps, h=None, 
         _ptr(r_prev, f64, (B, 8, dim), "r_prev"), _ptr(h, f64, (B,), "h"),
         _ptr(nsteps, torch.int64, (B,), "nsteps"), _ptr(H0, f64, (B,), "H0"), int(bool(h0_init)),
         _ptr(dH_max, f64, (B,), "dH_max"), _ptr(iters, torch.int64, (B,), "iters"),
+        _ptr(status, torch.int32, (B,), "status"), B, _stream(stream)))
+
+
+def irkgl_advance_t(ctx: int, dim: int, q, v, q_lo, v_lo, r_prev, t, nsteps, t_lo=None, h=None,
+                    iters=None, status=None, stream=None):
+    """Continue trajectories of a time-dependent right-hand side by nsteps[b]
+    steps each, carrying the time t (float64 [B], and its compensation part
+    t_lo) in place."""
+    B = q.shape[0]
+    f64 = torch.float64
+    _check(load().irkgl_advance_t(
+        _P(ctx), _ptr(q, f64, (B, dim), "q"), _ptr(v, f64, (B, dim), "v"),
+        _ptr(q_lo, f64, (B, dim), "q_lo"), _ptr(v_lo, f64, (B, dim), "v_lo"),
+        _ptr(r_prev, f64, (B, 8, dim), "r_prev"), _ptr(t, f64, (B,), "t"),
+        _ptr(t_lo, f64, (B,), "t_lo"), _ptr(h, f64, (B,), "h"),
+        _ptr(nsteps, torch.int64, (B,), "nsteps"), _ptr(iters, torch.int64, (B,), "iters"),
         _ptr(status, torch.int32, (B,), "status"), B, _stream(stream)))
 
 
@@ -428,6 +446,9 @@ class Integrator:
 
     def advance(self, *args, **kw):
         return irkgl_advance(self.ctx, self.dim, *args, **kw)
+
+    def advance_t(self, *args, **kw):
+        return irkgl_advance_t(self.ctx, self.dim, *args, **kw)
 
     def integrate(self, q0, v0, out=None, **kw) -> Outputs:
         out = out or Outputs.allocate(q0.shape[0], self.dim, device=q0.device)

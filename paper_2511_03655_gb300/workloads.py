@@ -93,6 +93,31 @@ def henon_heiles_ic():
     return np.array([[q1, q2]]), np.array([[p1, p2]])
 
 
+def henon_heiles_ensemble(batch: int, energy: float = 1.0 / 12, seed_id: int = 7,
+                          t_max: float = 2 * math.pi):
+    """`batch` Henon-Heiles initial states on the energy surface H = energy
+    (the paper's H = 1/12 by default, Sec. 5.1): q1 = 0, (q2, p2) drawn
+    uniformly from the box [-0.35, 0.45] x [-0.3, 0.3] and kept where the
+    remaining energy leaves p1^2 > 0; p1 = +sqrt(2 (energy - rest)).  Also a
+    start time t0 ~ U[0, t_max) per state, for the non-autonomous system
+    of Sec. 3 (forcing lambda + xi sin t).  Returns (q0, v0, t0)."""
+    q, v = [], []
+    u = uniform(SEED_BASE + seed_id, 4 * batch + 64)
+    k = 0
+    while len(q) < batch:
+        if k + 2 > len(u):
+            u = np.concatenate([u, uniform(SEED_BASE + seed_id + 7919 * (k + 1), 4 * batch + 64)])
+        q2 = -0.35 + 0.8 * u[k]
+        p2 = -0.3 + 0.6 * u[k + 1]
+        k += 2
+        rest = p2 * p2 / 2 + q2 * q2 / 2 - q2 ** 3 / 3
+        if energy - rest > 1e-3:
+            q.append([0.0, q2])
+            v.append([math.sqrt(2 * (energy - rest)), p2])
+    t0 = t_max * uniform(SEED_BASE + seed_id + 1, batch)
+    return np.array(q), np.array(v), t0
+
+
 def similarity_order(key: np.ndarray, descending: bool = True) -> np.ndarray:
     """Processing order that puts trajectories with similar `key` (e.g. the
     eccentricity, or an estimated cost) next to each other, costliest first."""
