@@ -64,10 +64,13 @@ def parse():
     ap.add_argument("--lanes", type=int, default=0, help="lanes per trajectory (0 = library default)")
     ap.add_argument("--no-order", action="store_true", help="natural order instead of similarity order")
     ap.add_argument("--skip-extras", action="store_true", help="skip e2e, plain form and CPU baseline")
-    ap.add_argument("--workload", default="kepler", choices=["kepler", "nbody6"],
+    ap.add_argument("--workload", default="kepler", choices=["kepler", "nbody6", "uneven"],
                     help="kepler: the 65,536-orbit ensemble (default); nbody6: 16,384 perturbed "
-                         "copies of a 6-body system")
-    ap.add_argument("--traj-steps", type=int, default=100000, help="steps per copy for nbody6")
+                         "copies of a 6-body system; uneven: 4,096 ragged instances (N-body "
+                         "N~U{3..64} and FPUT n~U{8..512}), autotuned vs fixed tiling")
+    ap.add_argument("--traj-steps", type=int, default=None,
+                    help="steps per trajectory/instance (nbody6: 10000, uneven: 1000 by default)")
+    ap.add_argument("--ninst", type=int, default=4096, help="instances for the uneven workload")
     ap.add_argument("--mix", type=int, default=0, choices=[0, 1],
                     help="stage mixing: 0 FP64 FMA chain, 1 fixed-point sums on the integer pipes")
     ap.add_argument("--serve-requests", type=int, default=300,
@@ -196,6 +199,186 @@ def run_reference(args):
     return 0
 
 
+
+# --------------------------------------------------------------------------
+# config 4: the ragged batch, bucketed (autotuned tiling) vs one launch
+# --------------------------------------------------------------------------
+def fp64_peak_tflops(irkgl, torch, stream, dev):
+    """The library's FP64 FMA-chain probe, timed on `stream` (2 flops per FMA)."""
+    scratch = torch.zeros(1, dtype=torch.float64, device=dev)
+    for _ in range(3):
+        irkgl.irkgl_probe_fp64_fma(scratch)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    nfma = 0
+    for _ in range(5):
+        nfma += irkgl.irkgl_probe_fp64_fma(scratch)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return 2 * nfma / (e0.elapsed_time(e1) * 1e-3) / 1e12
+
+
+def run_uneven(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2511_03655_gb300 import autotune, build, irkgl, ragged, workloads
+    from paper_2511_03655_gb300 import dist as pdist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    irkgl.load()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    tuned = autotune.load_table()
+    w = workloads.uneven_batch(ninst=args.ninst, steps=args.traj_steps,
+                               seed_id=pdist.shard_seed(4, rank),
+                               step_table=tuned["step_table"] if tuned else None)
+    tiles = tuned["tiles"]["wide"] if tuned else None
+    plan = ragged.RaggedPlan(w, tiles=tiles)
+    params = torch.tensor(w["params"], device=dev)
+    q0, v0 = torch.tensor(w["q0"], device=dev), torch.tensor(w["v0"], device=dev)
+    runner = ragged.RaggedRunner(plan, params, q0, v0, device=dev)
+    out = irkgl.RaggedOutputs.allocate(len(w["q0"]), args.ninst, device=dev)
+    peak = fp64_peak_tflops(irkgl, torch, stream, dev)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn(out)
+        torch.cuda.synchronize()
+        flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+        ts = []
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            pdist.barrier()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn(out)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b) * 1e-3)
+        return ts
+
+    clocks = ClockSampler(local)
+    pdist.barrier()
+    clocks.start()
+    ts_auto = timed(runner.run)
+    clk = clocks.stop()
+    steps = out.steps.cpu().numpy()
+    iters = out.iters.cpu().numpy()
+    dH = out.dH_max.cpu().numpy()
+    st = out.status.cpu().numpy()
+    q_auto = out.q.clone()
+    ts_fixed = timed(runner.single)
+    same = bool(torch.equal(q_auto, out.q))
+    wp = plan.permuted()
+    ok = (dH <= TOL) & (st == 0)
+    t_auto = pdist.reduce_max(sum(ts_auto))
+    t_fixed = pdist.reduce_max(sum(ts_fixed))
+    steps_all = pdist.reduce_sum(float(steps.sum()))
+    steps_ok = pdist.reduce_sum(float(steps[ok].sum()))
+    flops = ragged.algorithmic_flops(wp["kind"], wp["dim"], steps, iters)
+    achieved = flops / statistics.mean(ts_auto) / 1e12
+    line = {
+        "metric": METRIC, "value": args.steps * steps_ok / t_auto, "unit": "traj-steps/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_auto / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"uneven_batch: {args.ninst} instances, half N-body N~U{{3..64}} "
+                               f"(central mass + N-1 bodies), half FPUT alpha=0.25 n~U{{8..512}}, "
+                               f"h from the step table, {args.traj_steps} steps each",
+                   "step_table": "tuning/gb300.json" if tuned else "built-in defaults",
+                   "tiling": "autotuned: one launch per size bucket on its own stream, team from "
+                             "the tile table" if tiles else "bucketed, library team per bucket",
+                   "buckets": [{"label": b.label, "instances": b.count, "dmax": b.dmax, "team": b.team}
+                               for b in plan.buckets],
+                   "l2": "L2 flushed with a 256 MiB write before every timed step",
+                   "parallelism": f"dp{world} (independent shards, no collective on the data path)"},
+        "value_all": args.steps * steps_all / t_auto,
+        "fixed_tiling": {"value_all": args.steps * steps_all / t_fixed, "ms_per_step": 1e3 * t_fixed / args.steps,
+                         "team": "library choice for the largest dimension (one launch)",
+                         "speedup_autotuned": t_fixed / t_auto, "results_bitwise_equal": same},
+        "accuracy": {"tol": TOL, "instances_within_tol": float(ok.mean()),
+                     "status_nonzero": int((st != 0).sum()),
+                     "dH_max_median": float(np.median(dH)), "dH_max_p90": float(np.percentile(dH, 90))},
+        "sweeps_per_step": float(iters.sum() / max(steps.sum(), 1)),
+        "gpu_launches": args.steps * runner.launches(),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_source": "FP64 FMA-chain probe (irkgl_probe_fp64_fma) measured live, "
+                                    "2 flops per FMA",
+                     "kernel": "irkgl_wide_kernel (all bucket launches, concurrent; time of the region)",
+                     "flops_per_launch": flops},
+        "clocks": clk,
+    }
+    if not args.skip_extras:
+        # e2e through the public API: pinned host inputs -> device, run, outputs -> host
+        hq0 = torch.tensor(w["q0"]).pin_memory()
+        hv0 = torch.tensor(w["v0"]).pin_memory()
+        hp = torch.tensor(w["params"]).pin_memory()
+        hq = torch.empty_like(hq0).pin_memory()
+        hv = torch.empty_like(hv0).pin_memory()
+        hst = torch.empty(args.ninst, dtype=torch.int32).pin_memory()
+        hdh = torch.empty(args.ninst, dtype=torch.float64).pin_memory()
+        et = []
+        for _ in range(args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            q0.copy_(hq0, non_blocking=True)
+            v0.copy_(hv0, non_blocking=True)
+            params.copy_(hp, non_blocking=True)
+            runner.run(out)
+            hq.copy_(out.q, non_blocking=True)
+            hv.copy_(out.v, non_blocking=True)
+            hst.copy_(out.status, non_blocking=True)
+            hdh.copy_(out.dH_max, non_blocking=True)
+            torch.cuda.synchronize()
+            et.append(time.perf_counter() - t0)
+        h2d = sum(t.numel() * t.element_size() for t in (hq0, hv0, hp))
+        d2h = sum(t.numel() * t.element_size() for t in (hq, hv, hst, hdh))
+        line["e2e"] = {"value": args.steps * steps_ok / pdist.reduce_max(sum(et)), "unit": "traj-steps/s",
+                       "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                       "api": "ragged.RaggedRunner over irkgl_integrate_ragged, pinned host copies "
+                              "inside the timed region"}
+        if rank == 0 and world == 1:
+            from oracle import cbind
+            cores = os.cpu_count() or 1
+            # bounded sample: 128 instances evenly spaced over the plan order
+            # (all buckets), 40 steps each, one instance per thread task
+            sel = plan.perm[np.linspace(0, args.ninst - 1, min(128, args.ninst)).astype(int)]
+            import concurrent.futures as cf
+            kinds = {2: cbind.NBODY, 3: cbind.FPUT, 5: cbind.HARMONIC}
+            nsamp = 40
+
+            def one(k):
+                o, d = int(w["offset"][k]), int(w["dim"][k])
+                po, pn = int(w["param_offset"][k]), int(w["nparams"][k])
+                cbind.run(kinds[int(w["kind"][k])], w["params"][po:po + pn], w["q0"][o:o + d],
+                          w["v0"][o:o + d], w["h"][k], nsamp)
+
+            cbind.lib()
+            t0 = time.perf_counter()
+            with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+                list(ex.map(one, sel))
+            dt = time.perf_counter() - t0
+            line["cpu_baseline"] = {"value": len(sel) * nsamp / dt, "unit": "traj-steps/s", "cores": cores,
+                                    "kind": "oracle",
+                                    "sample": f"{len(sel)} instances evenly spaced over the size buckets, "
+                                              f"{nsamp} steps each, {dt:.1f} s wall on {cores} threads"}
+    if rank == 0:
+        print(json.dumps(line))
+    runner.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
 # --------------------------------------------------------------------------
 # GPU arm
 # --------------------------------------------------------------------------
@@ -203,6 +386,11 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+
+    if args.traj_steps is None:
+        args.traj_steps = {"nbody6": 10000, "uneven": 1000}.get(args.workload, 10000)
+    if args.workload == "uneven":
+        return run_uneven(args)
 
     import torch
     import torch.distributed as dist

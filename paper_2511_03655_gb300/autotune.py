@@ -7,8 +7,11 @@ error max_n |(H_n - H_{n-1})/H_{n-1}| (Eq. DHlocmax) is about 1e-14 (its
 reference step size for Table tab:overhead).  For every (kind, size bucket)
 the tuner runs short pilot integrations on the GPU with the local-error
 monitor over a geometric ladder of steps and keeps the largest step whose
-pilots all stay at or below 1e-14.  N-body steps are stored as a fraction
-of the innermost orbital period; FPUT steps are absolute.
+pilots all stay at or below the target: 1e-14, or twice the roundoff floor
+of H where evaluating H in FP64 alone loses more than that (the floor is
+the error at the smallest step of the ladder; N-body systems with many
+pair terms reach it).  N-body steps are stored as a fraction of the
+innermost orbital period; FPUT steps are absolute.
 
 Tile table.  For the batched register kernel it times every compiled
 lanes-per-trajectory tile on a pilot batch of each (kind, dim); for ragged
@@ -19,6 +22,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import time
 
@@ -30,6 +34,7 @@ from . import irkgl, workloads
 HERE = os.path.dirname(os.path.abspath(__file__))
 TABLE = os.path.join(HERE, "tuning", "gb300.json")
 TARGET_LOCAL = 1e-14
+WIDE_MAX_SLOTS = {32: 2, 64: 4, 128: 4, 256: 4}  # compiled wide-kernel shapes (k_wide.cu)
 
 
 def load_table(path: str = TABLE) -> dict | None:
@@ -80,37 +85,57 @@ def _run_ragged(w, team=0, local=False, timed=False):
     return out, dt
 
 
+def _pilot_dH(descs, steps) -> float:
+    """Largest local energy error (Eq. DHlocmax) over the pilots; inf if any failed."""
+    out, _ = _run_ragged(_ragged(descs, steps), local=True)
+    if not (out.status.cpu().numpy() == 0).all():
+        return math.inf
+    return float(out.dH_max.cpu().numpy().max())
+
+
+def _choose(ladder, dH):
+    """Largest step of the ladder whose local error meets the target.  The
+    target is 1e-14, raised to twice the roundoff floor (the error at the
+    smallest step, where truncation is far below roundoff) when evaluating
+    H in FP64 already loses more than that (N-body with many pair terms)."""
+    floor = dH[0]
+    target = max(TARGET_LOCAL, 2.0 * floor)
+    ok = [x for x, e in zip(ladder, dH) if e <= target]
+    return (max(ok) if ok else ladder[0]), floor, target, bool(ok)
+
+
 def step_table(quick: bool = False) -> dict:
     pilots, steps = (4, 300) if quick else (8, 1000)
-    table = {"nbody": {"fraction_of_inner_period": {}}, "fput": {"by_bucket": {}}}
+    table = {"nbody": {"fraction_of_inner_period": {}, "detail": {}},
+             "fput": {"by_bucket": {}, "detail": {}}}
     # N-body: fraction of the innermost period
-    fracs = [0.0025, 0.0035, 0.005, 0.007, 0.01]
+    fracs = [0.0025, 0.0035, 0.005, 0.007, 0.01, 0.014, 0.02]
     for nb in ([4, 8, 16] if quick else [3, 6, 12, 24, 48, 64]):
-        best = fracs[0]
+        dH = []
         for f in fracs:
             descs = []
             for k in range(pilots):
-                s = workloads.nbody_system(nb, seed_id=50000 + 97 * nb + k)
-                descs.append((irkgl.RHS_NBODY, [1.0] + list(s["masses"]), s["q"], s["v"],
-                              f * s["period_inner"]))
-            out, _ = _run_ragged(_ragged(descs, steps), local=True)
-            ok = (out.status.cpu().numpy() == 0).all() and out.dH_max.cpu().numpy().max() <= TARGET_LOCAL
-            if ok:
-                best = f
+                sy = workloads.nbody_system(nb, seed_id=50000 + 97 * nb + k)
+                descs.append((irkgl.RHS_NBODY, [1.0] + list(sy["masses"]), sy["q"], sy["v"],
+                              f * sy["period_inner"]))
+            dH.append(_pilot_dH(descs, steps))
+        best, floor, target, met = _choose(fracs, dH)
         table["nbody"]["fraction_of_inner_period"][str(nb)] = best
+        table["nbody"]["detail"][str(nb)] = {"dH_loc": dict(zip(map(str, fracs), dH)),
+                                             "roundoff_floor": floor, "target": target, "met": met}
     # FPUT: absolute step per size bucket
-    hs = [0.1, 0.15, 0.2, 0.3, 0.4, 0.5]
+    hs = [0.1, 0.15, 0.2, 0.3, 0.4, 0.5, 0.7, 1.0]
     for n in ([16, 128] if quick else [16, 32, 64, 128, 256, 512]):
-        best = hs[0]
+        c = workloads.fput_chain(n)
+        dH = []
         for h in hs:
-            c = workloads.fput_chain(n)
             descs = [(irkgl.RHS_FPUT, c["params"], c["q"] * (1 + 1e-3 * k), c["v"], h)
                      for k in range(pilots)]
-            out, _ = _run_ragged(_ragged(descs, steps), local=True)
-            ok = (out.status.cpu().numpy() == 0).all() and out.dH_max.cpu().numpy().max() <= TARGET_LOCAL
-            if ok:
-                best = h
+            dH.append(_pilot_dH(descs, steps))
+        best, floor, target, met = _choose(hs, dH)
         table["fput"]["by_bucket"][str(n)] = best
+        table["fput"]["detail"][str(n)] = {"dH_loc": dict(zip(map(str, hs), dH)),
+                                           "roundoff_floor": floor, "target": target, "met": met}
     return table
 
 
@@ -133,28 +158,42 @@ def tile_table(quick: bool = False) -> dict:
         integ.close()
     res["register"]["kepler/2"] = {"lanes_per_traj": min(times, key=times.get),
                                    "seconds": {str(k): v for k, v in times.items()}}
-    # wide kernel: team size per size bucket of a ragged batch
-    for label, kw in (("nbody<=64", dict(nmax_body=64, nmax_chain=8)),
-                      ("fput<=512", dict(nmax_body=3, nmax_chain=512))):
-        wb = workloads.uneven_batch(ninst=64 if quick else 256, steps=100, **kw)
-        wb = {k: (v[wb["kind"] == (2 if label.startswith("nbody") else 3)]
-                  if isinstance(v, np.ndarray) and len(v) == len(wb["kind"]) else v)
-              for k, v in wb.items()}
-        # re-pack after filtering
-        descs = []
-        for k in range(len(wb["kind"])):
-            o, d = int(wb["offset"][k]), int(wb["dim"][k])
-            po, pn = int(wb["param_offset"][k]), int(wb["nparams"][k])
-            descs.append((int(wb["kind"][k]), wb["params"][po:po + pn], wb["q0"][o:o + d],
-                          wb["v0"][o:o + d], float(wb["h"][k])))
-        rb = _ragged(descs, 100)
+    # wide kernel: team size per size bucket of a ragged batch (the buckets of
+    # ragged.RaggedPlan); each bucket's pilot instances are timed alone
+    from . import ragged
+    wb = workloads.uneven_batch(ninst=256 if quick else 1024, steps=40 if quick else 100)
+    plan = ragged.RaggedPlan(wb)
+    wp = plan.permuted()
+    params = torch.tensor(wb["params"], device="cuda")
+    q0, v0 = torch.tensor(wb["q0"], device="cuda"), torch.tensor(wb["v0"], device="cuda")
+    inst_all = irkgl.instances_tensor(wp, "cuda")
+    out = irkgl.RaggedOutputs.allocate(len(wb["q0"]), len(wp["kind"]))
+    for b in plan.buckets:
+        inst = inst_all[b.start * ragged.INSTANCE_BYTES:(b.start + b.count) * ragged.INSTANCE_BYTES]
         tt = {}
         for team in (32, 64, 128, 256):
-            if team * (2 if team in (32, 256) else 4) < int(rb["dim"].max()):
+            if team * WIDE_MAX_SLOTS[team] < b.dmax:
                 continue
-            _, dt = _run_ragged(rb, team=team, timed=True)
-            tt[team] = dt
-        res["wide"][label] = {"team": min(tt, key=tt.get), "seconds": {str(k): v for k, v in tt.items()}}
+            ctx = irkgl.irkgl_create(irkgl.RHS_HARMONIC, [1.0], 1, 0.1)
+            irkgl.irkgl_set_option(ctx, irkgl.OPT_WIDE_TEAM, team)
+            view = irkgl.RaggedOutputs(q=out.q, v=out.v, q_lo=out.q_lo, v_lo=out.v_lo, r_prev=out.r_prev,
+                                       dH_max=out.dH_max[b.start:b.start + b.count],
+                                       iters=out.iters[b.start:b.start + b.count],
+                                       steps=out.steps[b.start:b.start + b.count],
+                                       status=out.status[b.start:b.start + b.count])
+            try:
+                irkgl.irkgl_integrate_ragged(ctx, inst, b.count, b.dmax, params, q0, v0, view)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                irkgl.irkgl_integrate_ragged(ctx, inst, b.count, b.dmax, params, q0, v0, view)
+                torch.cuda.synchronize()
+                tt[team] = time.perf_counter() - t0
+            except irkgl.IrkglError:
+                pass  # shape not available for this dimension (shared memory)
+            finally:
+                irkgl.irkgl_destroy(ctx)
+        res["wide"][b.label] = {"team": min(tt, key=tt.get), "seconds": {str(k): v for k, v in tt.items()},
+                                "pilot_instances": b.count}
     return res
 
 

@@ -213,7 +213,7 @@ def uneven_batch(ninst: int = 4096, steps: int = 10000, seed_id: int = 4, nmax_b
         if k % 2 == 0:
             nb = 3 + int(u[0, k] * (nmax_body - 2))
             sysd = nbody_system(nb, seed_id=10000 + k)
-            h = table["nbody"]["fraction_of_inner_period"] * sysd["period_inner"]
+            h = _nbody_fraction(table, nb) * sysd["period_inner"]
             kinds.append(2)
             dims.append(3 * nb)
             params.append([1.0] + list(sysd["masses"]))
@@ -239,6 +239,20 @@ def uneven_batch(ninst: int = 4096, steps: int = 10000, seed_id: int = 4, nmax_b
             "h": np.array(hs), "nsteps": np.full(ninst, steps, dtype=np.int64),
             "params": np.concatenate([np.asarray(p, dtype=np.float64) for p in params]),
             "q0": np.concatenate(qs), "v0": np.concatenate(vs)}
+
+
+def _nbody_fraction(table: dict, nb: int) -> float:
+    """Step as a fraction of the innermost period: a number, or a table by
+    body count (the entry for the smallest tabulated count >= nb, else the
+    largest count)."""
+    f = table["nbody"]["fraction_of_inner_period"]
+    if not isinstance(f, dict):
+        return float(f)
+    keys = sorted(int(k) for k in f)
+    for k in keys:
+        if k >= nb:
+            return float(f[str(k)])
+    return float(f[str(keys[-1])])
 
 
 def _bucket(n: int) -> str:

@@ -128,3 +128,29 @@ def test_bad_descriptor_reported(torch_cuda):
     st = out.status.cpu().numpy()
     assert st[3] != 0 and (np.delete(st, 3) == 0).all()
     integ.close()
+
+
+def test_bucketed_launches_equal_single_launch_bitwise(torch_cuda):
+    """ragged.RaggedRunner: one launch per size bucket (own team, own stream)
+    gives the bits of one launch of the whole batch, and of the unbucketed
+    call in the caller's instance order."""
+    from paper_2511_03655_gb300 import irkgl, ragged
+    torch = torch_cuda
+    w = small_batch(ninst=40, steps=60, nmax_body=40, nmax_chain=300)
+    tiles = {"nbody:3-8": {"team": 64}, "fput:1-64": {"team": 32}, "fput:257-512": {"team": 256}}
+    plan = ragged.RaggedPlan(w, tiles=tiles)
+    assert len(plan.buckets) >= 3
+    runner = ragged.RaggedRunner(plan, torch.tensor(w["params"], device="cuda"),
+                                 torch.tensor(w["q0"], device="cuda"), torch.tensor(w["v0"], device="cuda"))
+    a = irkgl.RaggedOutputs.allocate(len(w["q0"]), len(w["kind"]))
+    b = irkgl.RaggedOutputs.allocate(len(w["q0"]), len(w["kind"]))
+    runner.run(a)
+    runner.single(b)
+    torch.cuda.synchronize()
+    for f in ("q", "v", "q_lo", "v_lo", "r_prev", "dH_max", "iters", "steps", "status"):
+        assert torch.equal(getattr(a, f), getattr(b, f)), f
+    ref = run_gpu(torch, w)
+    assert torch.equal(a.q, ref.q) and torch.equal(a.v, ref.v)
+    for f in ("iters", "status", "dH_max"):
+        assert np.array_equal(plan.unpermute(getattr(a, f).cpu().numpy()), getattr(ref, f).cpu().numpy()), f
+    runner.close()
