@@ -22,6 +22,8 @@ BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD_DIR, "liborc.so")
 
 KEPLER, NBODY, FPUT, HENON_HEILES, HARMONIC, HH_FORCED = 1, 2, 3, 4, 5, 6
+SCHWARZSCHILD, HARMONIC1 = 7, 8  # first-order (mu form), D = 4 and 2
+DIM1 = {SCHWARZSCHILD: 4, HARMONIC1: 2}
 _lock = threading.Lock()
 _lib = None
 
@@ -64,6 +66,14 @@ def lib():
             L.orc_run_t.restype = ctypes.c_int
             L.orc_run_t.argtypes = (L.orc_run.argtypes[:11] + [P(ctypes.c_double), P(ctypes.c_double)]
                                     + L.orc_run.argtypes[11:])
+            L.orc_run1.restype = ctypes.c_int
+            L.orc_run1.argtypes = [
+                P(OrcTab), ctypes.c_int, P(ctypes.c_double), ctypes.c_int, ctypes.c_int,
+                P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double),
+                P(ctypes.c_longlong), ctypes.c_int, P(ctypes.c_int), ctypes.c_int,
+                P(ctypes.c_longlong), P(ctypes.c_double), P(ctypes.c_int), P(ctypes.c_longlong)]
+            L.orc_hamiltonian1.restype = ctypes.c_double
+            L.orc_hamiltonian1.argtypes = [ctypes.c_int, P(ctypes.c_double), P(ctypes.c_double)]
             L.orc_hamiltonian.restype = ctypes.c_double
             L.orc_hamiltonian.argtypes = [ctypes.c_int, P(ctypes.c_double), ctypes.c_int,
                                           P(ctypes.c_double), P(ctypes.c_double)]
@@ -147,3 +157,45 @@ def hamiltonian(kind: int, params, q, v) -> float:
     v = np.ascontiguousarray(np.asarray(v, dtype=np.float64))
     return lib().orc_hamiltonian(kind, _ptr(params, ctypes.c_double), q.shape[-1],
                                  _ptr(q, ctypes.c_double), _ptr(v, ctypes.c_double))
+
+
+def run1(kind: int, params, y, h, nsteps, *, y_lo=None, l_prev=None, iters_len: int = 0,
+         kmax: int = 100, tab: dict | None = None):
+    """Advance a batch of first-order trajectories with the C oracle
+    (SCHWARZSCHILD: y = (r, theta, p_r, p_theta); HARMONIC1: y = (q, p)).
+    y: (batch, D).  params: (P,) shared or (batch, P).  Returns y, y_lo,
+    l_prev (batch, 8, D), iters, iters_total, dH_max, status, steps."""
+    D = DIM1[kind]
+    y = np.array(y, dtype=np.float64, order="C", copy=True).reshape(-1, D)
+    batch = y.shape[0]
+    y_lo = (np.zeros_like(y) if y_lo is None
+            else np.array(y_lo, dtype=np.float64, order="C", copy=True).reshape(batch, D))
+    l_prev = (np.zeros((batch, 8, D)) if l_prev is None
+              else np.array(l_prev, dtype=np.float64, order="C", copy=True).reshape(batch, 8, D))
+    params = np.ascontiguousarray(np.asarray(params, dtype=np.float64))
+    pstride = params.shape[-1] if params.ndim == 2 else 0
+    hh = np.ascontiguousarray(np.broadcast_to(np.asarray(h, dtype=np.float64), (batch,)))
+    ns = np.ascontiguousarray(np.broadcast_to(np.asarray(nsteps, dtype=np.int64), (batch,)))
+    iters = np.zeros((batch, max(iters_len, 1)), dtype=np.int32)
+    tot = np.zeros(batch, dtype=np.int64)
+    dH = np.zeros(batch, dtype=np.float64)
+    st = np.zeros(batch, dtype=np.int32)
+    steps = np.zeros(batch, dtype=np.int64)
+    t = table(tab)
+    rc = lib().orc_run1(ctypes.byref(t), kind, _ptr(params, ctypes.c_double), pstride, batch,
+                        _ptr(y, ctypes.c_double), _ptr(y_lo, ctypes.c_double),
+                        _ptr(l_prev, ctypes.c_double), _ptr(hh, ctypes.c_double),
+                        _ptr(ns, ctypes.c_longlong), kmax,
+                        _ptr(iters, ctypes.c_int) if iters_len > 0 else None, iters_len,
+                        _ptr(tot, ctypes.c_longlong), _ptr(dH, ctypes.c_double),
+                        _ptr(st, ctypes.c_int), _ptr(steps, ctypes.c_longlong))
+    if rc != 0:
+        raise ValueError(f"orc_run1 failed ({rc})")
+    return {"y": y, "y_lo": y_lo, "l_prev": l_prev, "iters": iters[:, :iters_len],
+            "iters_total": tot, "dH_max": dH, "status": st, "steps": steps}
+
+
+def hamiltonian1(kind: int, params, y) -> float:
+    params = np.ascontiguousarray(np.asarray(params, dtype=np.float64))
+    y = np.ascontiguousarray(np.asarray(y, dtype=np.float64))
+    return lib().orc_hamiltonian1(kind, _ptr(params, ctypes.c_double), _ptr(y, ctypes.c_double))

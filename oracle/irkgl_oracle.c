@@ -428,3 +428,164 @@ int orc_run(const orc_tab* tab, int kind, const double* params, int pstride, int
 double orc_hamiltonian(int kind, const double* params, int d, const double* q, const double* v) {
   return rhs_H(kind, params, d, q, v);
 }
+
+/* ======================================================================
+ * First-order form (Eq. Yi2 with Eqs. IRK_init / IRK_FP, stopping rule on
+ * all D components, compensated update Eq. yn2): the same operation
+ * sequence as oracle/first_order.py.
+ * ====================================================================== */
+enum {
+  ORC1_SCHWARZSCHILD = 7, /* Eq. Ham_SBH, y = (r, theta, p_r, p_theta), params {E, L, beta} */
+  ORC1_HARMONIC = 8       /* q' = p, p' = -omega^2 q, params {omega} */
+};
+
+static void rhs_f1(int kind, const double* p, const double* y, double* f) {
+  if (kind == ORC1_SCHWARZSCHILD) {
+    double r = y[0], th = y[1], pr = y[2], pth = y[3];
+    double sn = sin(th), cs = cos(th);
+    double s = sn * sn;
+    double u = 1.0 - 2.0 / r;
+    double r2 = r * r;
+    double r3 = r2 * r;
+    double E2 = p[0] * p[0], L2 = p[1] * p[1], b2 = p[2] * p[2];
+    double dr = pr * pr / r2 + E2 / (r2 * (u * u)) - pth * pth / r3 - L2 / (r3 * s) + b2 * r * s / 4.0;
+    double dth = (-L2 / (r2 * (s * s)) + b2 * r2 / 4.0) * (sn * cs);
+    f[0] = u * pr;
+    f[1] = pth / r2;
+    f[2] = -dr;
+    f[3] = -dth;
+  } else { /* ORC1_HARMONIC */
+    f[0] = y[1];
+    f[1] = -(p[0] * p[0] * y[0]);
+  }
+}
+
+static double rhs_H1(int kind, const double* p, const double* y) {
+  if (kind == ORC1_SCHWARZSCHILD) {
+    double r = y[0], th = y[1], pr = y[2], pth = y[3];
+    double sn = sin(th);
+    double s = sn * sn;
+    double u = 1.0 - 2.0 / r;
+    double a = p[1] - p[2] / 2.0 * (r * r) * s;
+    return u * (pr * pr) / 2.0 - p[0] * p[0] / (2.0 * u) + pth * pth / (2.0 * (r * r)) +
+           a * a / (2.0 * (r * r) * s);
+  }
+  return (y[1] * y[1] + p[0] * p[0] * y[0] * y[0]) / 2.0;
+}
+
+static int dim1(int kind) { return kind == ORC1_SCHWARZSCHILD ? 4 : 2; }
+
+/* One first-order step; work sized 4*S*D + 2*D doubles. */
+static int one_step1(const orc_tab* t, int kind, const double* p, int D, double h, int kmax,
+                     double* y, double* ylo, double* lp, int* kout, double* work) {
+  double* Y = work;          /* S*D */
+  double* Yn = Y + S * D;    /* S*D */
+  double* F = Yn + S * D;    /* S*D */
+  double* L = F + S * D;     /* S*D */
+  double* dmin = L + S * D;  /* D */
+  double* dprev = dmin + D;  /* D */
+  /* init, Eq. IRK_init */
+  for (int i = 0; i < S; i++)
+    for (int l = 0; l < D; l++) {
+      double acc = t->nu[i * S] * lp[l];
+      for (int j = 1; j < S; j++) acc = acc + t->nu[i * S + j] * lp[j * D + l];
+      Y[i * D + l] = y[l] + acc;
+    }
+  for (int l = 0; l < D; l++) {
+    dmin[l] = INFINITY;
+    dprev[l] = INFINITY;
+  }
+  int k = 0;
+  for (;;) {
+    k++;
+    for (int i = 0; i < S; i++) rhs_f1(kind, p, Y + i * D, F + i * D);
+    for (int i = 0; i < S; i++)
+      for (int l = 0; l < D; l++) L[i * D + l] = h * (t->b[i] * F[i * D + l]);
+    int finite = 1;
+    for (int i = 0; i < S; i++)
+      for (int l = 0; l < D; l++) {
+        double acc = t->mu[i * S] * L[l];
+        for (int j = 1; j < S; j++) acc = acc + t->mu[i * S + j] * L[j * D + l];
+        double x = y[l] + acc;
+        Yn[i * D + l] = x;
+        if (!isfinite(x)) finite = 0;
+      }
+    if (!finite) {
+      *kout = k;
+      return ORC_NONFINITE;
+    }
+    int stop = 1;
+    for (int l = 0; l < D; l++) {
+      double delta = 0.0;
+      for (int i = 0; i < S; i++) {
+        double a = fabs(Yn[i * D + l] - Y[i * D + l]);
+        if (a > delta) delta = a;
+      }
+      double m = dprev[l] <= delta ? dprev[l] : delta;
+      int cond = (delta == 0.0) || (dmin[l] <= m);
+      stop = stop && cond;
+      dmin[l] = dmin[l] <= dprev[l] ? dmin[l] : dprev[l];
+      dprev[l] = delta;
+    }
+    memcpy(Y, Yn, sizeof(double) * S * D);
+    if (stop) break;
+    if (k >= kmax) {
+      *kout = k;
+      return ORC_MAXITER;
+    }
+  }
+  *kout = k;
+  for (int l = 0; l < D; l++) {
+    double sL = L[l];
+    for (int i = 1; i < S; i++) sL = sL + L[i * D + l];
+    two_sum_add(&y[l], &ylo[l], sL);
+  }
+  memcpy(lp, L, sizeof(double) * S * D);
+  return ORC_OK;
+}
+
+/*
+ * Advance `batch` first-order trajectories (D = 4 for ORC1_SCHWARZSCHILD,
+ * 2 for ORC1_HARMONIC) by nsteps[t] steps of size h[t], in place: y, y_lo
+ * [batch*D], l_prev [batch*8*D].  Optional outputs as for orc_run
+ * (dH_max relative to H at entry).  Single-threaded.  Returns 0, -1 on
+ * allocation failure, -2 for an unknown kind.
+ */
+int orc_run1(const orc_tab* tab, int kind, const double* params, int pstride, int batch, double* y,
+             double* y_lo, double* l_prev, const double* h, const long long* nsteps, int kmax,
+             int* iters, int iters_stride, long long* iters_total, double* dH_max, int* status,
+             long long* steps_done) {
+  if (kind != ORC1_SCHWARZSCHILD && kind != ORC1_HARMONIC) return -2;
+  const int D = dim1(kind);
+  double* work = (double*)malloc(sizeof(double) * (4 * S * D + 2 * D));
+  if (!work) return -1;
+  for (int t = 0; t < batch; t++) {
+    const double* p = params + (size_t)t * pstride;
+    double* yy = y + (size_t)t * D;
+    double* yl = y_lo + (size_t)t * D;
+    double* lp = l_prev + (size_t)t * S * D;
+    double H0 = rhs_H1(kind, p, yy);
+    double dmax = 0.0;
+    long long tot = 0, n = 0;
+    int st = ORC_OK;
+    for (n = 0; n < nsteps[t]; n++) {
+      int k = 0;
+      st = one_step1(tab, kind, p, D, h[t], kmax, yy, yl, lp, &k, work);
+      if (iters && n < iters_stride) iters[(size_t)t * iters_stride + n] = k;
+      tot += k;
+      if (st != ORC_OK) break;
+      double dH = fabs((rhs_H1(kind, p, yy) - H0) / H0);
+      if (dH > dmax) dmax = dH;
+    }
+    if (iters_total) iters_total[t] = tot;
+    if (dH_max) dH_max[t] = dmax;
+    if (status) status[t] = st;
+    if (steps_done) steps_done[t] = n;
+  }
+  free(work);
+  return 0;
+}
+
+double orc_hamiltonian1(int kind, const double* params, const double* y) {
+  return rhs_H1(kind, params, y);
+}

@@ -10,9 +10,11 @@ the library's choice for the bucket's largest dimension.  ``RaggedRunner``
 launches every bucket on its own CUDA stream (each launch is a persistent
 grid over all SMs, so buckets overlap at their tails) and joins them.
 
-Team shapes give bit-identical results (the per-component arithmetic and
-the summation orders do not depend on the team size), so a bucketed run
-equals one launch of the whole batch bit for bit; only the time differs.
+Team shapes give bit-identical states, sweep counts and statuses (the
+per-component arithmetic and the summation orders of the method do not
+depend on the team size), so a bucketed run equals one launch of the whole
+batch bit for bit in those; only the energy monitor's sum of H over the
+team (per-warp partials) rounds differently, so dH_max agrees to roundoff.
 
 Instance descriptors are re-ordered on the host; the packed state arrays
 keep their layout (descriptors carry absolute offsets), and per-instance

@@ -19,9 +19,11 @@ Workloads (sizes as in the benchmark configurations):
                    G = 1; heliocentric elements with GM = 1 + m_i, shifted to the
                    barycentre at rest; 16,384 copies, copy 0 exact and the others with
                    positions scaled by (1 + 1e-8 xi), xi ~ U[-1, 1] per component;
-                   h = 0.5 % of the innermost period, 1e5 steps.  (A synthetic
-                   stand-in for the paper's 6-body outer Solar System, whose DE430
-                   initial conditions are not available here.)
+                   h = 0.5 % of the innermost period, 1e5 steps; masses and axes are
+                   redrawn until neighbours are >= 8 mutual Hill radii apart, as in
+                   the outer Solar System.  (A synthetic stand-in for the paper's
+                   6-body outer Solar System, whose DE430 initial conditions are not
+                   available here.)
   fput_chain       FPUT alpha chain, n interior particles, fixed ends, alpha = 0.25,
                    unit harmonic energy in mode 1: q_j = A sin(j pi/(n+1)),
                    A = 2/(omega_1 sqrt(n+1)), omega_1 = 2 sin(pi/(2(n+1))), v = 0.
@@ -147,13 +149,31 @@ def _kepler_elements_to_state(a, e, inc, node, peri, M, mu):
     return pos, vel
 
 
-def nbody_system(nbodies: int = 6, seed_id: int = 3, amin: float = 5.0, amax: float = 40.0):
+def _min_hill_separation(a, m) -> float:
+    """Smallest gap between neighbouring semi-major axes, in mutual Hill
+    radii ((m_i + m_j)/3)^(1/3) (a_i + a_j)/2 (central mass 1)."""
+    o = np.argsort(a)
+    gaps = [(a[y] - a[x]) / (((m[x] + m[y]) / 3.0) ** (1.0 / 3.0) * (a[x] + a[y]) / 2.0)
+            for x, y in zip(o[:-1], o[1:])]
+    return min(gaps) if gaps else math.inf
+
+
+def nbody_system(nbodies: int = 6, seed_id: int = 3, amin: float = 5.0, amax: float = 40.0,
+                 min_hill: float | None = None):
     """One planetary system: central mass 1 plus nbodies - 1 bodies (G = 1),
-    barycentric positions q and velocities v (flattened [3 * nbodies])."""
+    barycentric positions q and velocities v (flattened [3 * nbodies]).
+    With min_hill, masses and semi-major axes are redrawn (from the next
+    seed stream) until neighbouring orbits are at least min_hill mutual Hill
+    radii apart, as the planets of the outer Solar System are (8 or more)."""
     k = nbodies - 1
-    u = uniform(SEED_BASE + seed_id, 7 * k).reshape(7, k)
-    m = 10.0 ** (-5.0 + 2.0 * u[0])
-    a = np.exp(np.log(amin) + (np.log(amax) - np.log(amin)) * u[1])
+    for attempt in range(1000):
+        u = uniform(SEED_BASE + seed_id + 7919 * attempt, 7 * k).reshape(7, k)
+        m = 10.0 ** (-5.0 + 2.0 * u[0])
+        a = np.exp(np.log(amin) + (np.log(amax) - np.log(amin)) * u[1])
+        if min_hill is None or _min_hill_separation(a, m) >= min_hill:
+            break
+    else:
+        raise ValueError(f"no {nbodies}-body system with {min_hill} mutual Hill radii spacing in [{amin}, {amax}]")
     e = 0.05 * u[2]
     inc = np.deg2rad(2.0) * u[3]
     node, peri, M = 2 * math.pi * u[4], 2 * math.pi * u[5], 2 * math.pi * u[6]
@@ -170,8 +190,8 @@ def nbody_system(nbodies: int = 6, seed_id: int = 3, amin: float = 5.0, amax: fl
 
 
 def nbody_ensemble(copies: int = 16384, nbodies: int = 6, steps: int = 100000, seed_id: int = 3,
-                   perturb: float = 1e-8, h_fraction: float = 0.005):
-    sysd = nbody_system(nbodies, seed_id)
+                   perturb: float = 1e-8, h_fraction: float = 0.005, min_hill: float | None = 8.0):
+    sysd = nbody_system(nbodies, seed_id, min_hill=min_hill)
     d = 3 * nbodies
     xi = 2.0 * uniform(SEED_BASE + seed_id + 500, copies * d).reshape(copies, d) - 1.0
     xi[0] = 0.0
