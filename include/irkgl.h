@@ -69,11 +69,17 @@ typedef enum {
   IRKGL_RHS_FPUT = 3,          /* d = n: FPUT alpha chain, fixed ends; params = {alpha} */
   IRKGL_RHS_HENON_HEILES = 4,  /* d = 2: Henon-Heiles (Sec. 5.1);    params = {lambda} */
   IRKGL_RHS_HARMONIC = 5,      /* any d: g = -omega^2 q;             params = {omega} */
-  IRKGL_RHS_HENON_HEILES_FORCED = 6 /* d = 2: the non-autonomous example of Sec. 3,
+  IRKGL_RHS_HENON_HEILES_FORCED = 6, /* d = 2: the non-autonomous example of Sec. 3,
                                   g(t, q) with lambda + xi sin t in place of lambda;
                                   params = {lambda, xi}.  Evaluated at the stage times
                                   t_n + c_i h.  Time starts at 0 except through
                                   irkgl_advance_t; the energy monitor is off (dH_max = 0) */
+  /* First-order systems y' = f(y) (the mu form of Eq. Yi2; use the irkgl_*1 calls,
+     dim = D, the full state dimension): */
+  IRKGL_RHS_SCHWARZSCHILD = 7, /* D = 4: charged particle near a Schwarzschild black hole in a
+                                  magnetic field, Eq. Ham_SBH; y = (r, theta, p_r, p_theta);
+                                  params = {E, L, beta} */
+  IRKGL_RHS_HARMONIC1 = 8      /* D = 2: q' = p, p' = -omega^2 q; params = {omega} */
 } irkgl_rhs_kind;
 
 typedef struct {
@@ -100,6 +106,18 @@ typedef struct {
   long long* steps;   /* [batch] steps completed */
   int* status;        /* [batch] IRKGL_STATUS_* */
 } irkgl_outputs;
+
+/* Outputs of irkgl_integrate1 (first-order kinds; device pointers, NULL =
+ * not wanted except y). */
+typedef struct {
+  double* y;          /* [batch][D] final state (hi parts of the compensated pairs) */
+  double* y_lo;       /* [batch][D] compensation parts */
+  double* l_prev;     /* [batch][8][D] L of the last completed step (for a resumed run) */
+  double* dH_max;     /* [batch] max over monitored steps of |(H_n - H_0)/H_0| */
+  long long* iters;   /* [batch] total fixed-point sweeps */
+  long long* steps;   /* [batch] steps completed */
+  int* status;        /* [batch] IRKGL_STATUS_* */
+} irkgl_outputs1;
 
 /* One instance of a ragged batch (irkgl_integrate_ragged): its own right-hand
  * side, dimension, step and horizon.  States of all instances are packed
@@ -211,6 +229,30 @@ int irkgl_advance_t(struct irkgl_ctx* ctx, double* q, double* v, double* q_lo, d
                     double* r_prev, double* t, double* t_lo, const double* h,
                     const long long* nsteps, long long* iters, int* status, int batch,
                     void* cuda_stream);
+
+/* First-order systems y' = f(y) (IRKGL_RHS_SCHWARZSCHILD, IRKGL_RHS_HARMONIC1), in the
+ * exactly-symplectic mu form of Sec. 2.4 (Eq. Yi2): per step the guess
+ * Y_i = y + sum_j nu_ij Lprev_j (Eq. IRK_init), sweeps L_i = h b_i f(Y_i),
+ * Y_i = y + sum_j mu_ij L_j (Eq. IRK_FP) until Eq. stopping holds on all D
+ * components, then y += sum_i L_i with a compensated pair (Eq. yn2, Sec. 5).
+ * The context is created by irkgl_create with dim = D.  Second-order calls
+ * on such a context, and these calls on a second-order context, return
+ * IRKGL_ERR_INVALID.
+ *
+ * irkgl_integrate1: y0 [batch][D] device, per-trajectory nsteps (or
+ * nsteps_all), h (or NULL for the context's), order (or NULL); outputs as in
+ * irkgl_outputs1.  Lprev starts at zero. */
+int irkgl_integrate1(struct irkgl_ctx* ctx, const double* y0, int batch, const long long* nsteps,
+                     long long nsteps_all, const double* h, const int* order,
+                     const irkgl_outputs1* out, void* cuda_stream);
+
+/* irkgl_advance1: continue device-resident first-order trajectories in place
+ * (y, y_lo [batch][D], l_prev [batch][8][D], all required), carrying H0 /
+ * dH_max / iters like irkgl_advance, so chunked runs give the bits of one
+ * run. */
+int irkgl_advance1(struct irkgl_ctx* ctx, double* y, double* y_lo, double* l_prev, const double* h,
+                   const long long* nsteps, double* H0, int h0_init, double* dH_max,
+                   long long* iters, int* status, int batch, void* cuda_stream);
 
 /* Integrate `batch` independent initial states (device arrays q0, v0
  * [batch][dim], R_prev = 0, lo = 0) in one persistent launch.

@@ -14,12 +14,15 @@
 #include <mutex>
 
 #include "irkgl.h"
+#include "irkgl_first_order.cuh"
 #include "irkgl_kernels.h"
 #include "irkgl_wide.cuh"
 #include "irkgl_tables.h"
 
 using irkgl::Coef;
+using irkgl::Coef1;
 using irkgl::KArgs;
+using irkgl::KArgs1;
 
 namespace {
 
@@ -52,10 +55,26 @@ const KernelEntry* find_kernel(int kind, int dim, int lpt, int block, int mix = 
 
 // Built-in default tile per (kind, dim): the smallest LPT that is compiled,
 // preferring 2 for d = 2 (both components' compensated updates in one pass).
+const irkgl::KernelEntry1* find_kernel1(int kind, int dim, int lpt, int block) {
+  const irkgl::KernelTable1 t = irkgl::kernels_first_order();
+  for (int i = 0; i < t.count; i++) {
+    const irkgl::KernelEntry1& e = t.entries[i];
+    if (e.kind == kind && e.dim == dim && e.lpt == lpt && e.block == block) return &e;
+  }
+  return nullptr;
+}
+
+// Right-hand sides of first-order systems y' = f(y) (the mu form).
+bool first_order_kind(int kind) {
+  return kind == IRKGL_RHS_SCHWARZSCHILD || kind == IRKGL_RHS_HARMONIC1;
+}
+
 int default_lpt(int kind, int dim) {
   const int prefs[] = {2, 1, 8, 4};
   for (int p : prefs)
-    if (find_kernel(kind, dim, p, 128)) return p;
+    if (first_order_kind(kind) ? find_kernel1(kind, dim, p, 128) != nullptr
+                               : find_kernel(kind, dim, p, 128) != nullptr)
+      return p;
   return 0;
 }
 
@@ -99,6 +118,7 @@ struct irkgl_ctx {
   int device;
   int sm_count;
   Coef coef;
+  Coef1 coef1;  // first-order kinds: b, mu, nu
   double* d_params;
   int nparams;
   unsigned* d_counter;
@@ -171,6 +191,10 @@ static int check_rhs(const irkgl_rhs& f, int dim) {
       return dim == 2 ? IRKGL_OK : IRKGL_ERR_INVALID;
     case IRKGL_RHS_HENON_HEILES_FORCED:
       return (dim == 2 && f.nparams == 2) ? IRKGL_OK : IRKGL_ERR_INVALID;
+    case IRKGL_RHS_SCHWARZSCHILD:
+      return (dim == 4 && f.nparams == 3) ? IRKGL_OK : IRKGL_ERR_INVALID;
+    case IRKGL_RHS_HARMONIC1:
+      return (dim == 2 && f.nparams == 1) ? IRKGL_OK : IRKGL_ERR_INVALID;
     case IRKGL_RHS_HARMONIC:
     case IRKGL_RHS_FPUT:
       return IRKGL_OK;
@@ -217,6 +241,11 @@ int irkgl_create(irkgl_ctx** out, irkgl_rhs f, int dim, double h, const irkgl_co
     c->coef.b[i] = tab.b[i];
   }
   for (int x = 0; x < 64; x++) c->coef.eta[x] = tab.eta[x];
+  for (int i = 0; i < 8; i++) c->coef1.b[i] = tab.b[i];
+  for (int x = 0; x < 64; x++) {
+    c->coef1.mu[x] = tab.mu[x];
+    c->coef1.nu[x] = tab.nu[x];
+  }
   c->default_tables = is_default_table(&tab) ? 1 : 0;
   if (c->default_tables) {
     for (int x = 0; x < 64; x++) c->coef.W[x] = IRKGL_TAB_W[x];
@@ -295,6 +324,10 @@ int irkgl_set_option(irkgl_ctx* c, int option, long long value) {
 
 int irkgl_get_tile(irkgl_ctx* c) {
   if (!c) return IRKGL_ERR_INVALID;
+  if (first_order_kind(c->kind)) {
+    const int lpt = c->lpt ? c->lpt : default_lpt(c->kind, c->dim);
+    return find_kernel1(c->kind, c->dim, lpt, c->block) ? lpt : 0;
+  }
   if (c->mix) return find_kernel(c->kind, c->dim, 1, c->block, 1) ? 1 : 0;
   return c->lpt ? c->lpt : default_lpt(c->kind, c->dim);
 }
@@ -303,6 +336,7 @@ int irkgl_get_tile(irkgl_ctx* c) {
 static bool time_dependent_kind(int kind) { return kind == IRKGL_RHS_HENON_HEILES_FORCED; }
 
 static int run(irkgl_ctx* c, KArgs& a, cudaStream_t st) {
+  if (first_order_kind(c->kind)) return IRKGL_ERR_INVALID;  // use the irkgl_*1 calls
   if (c->mix && !c->default_tables) return IRKGL_ERR_UNSUPPORTED;
   const int lpt = c->mix ? 1 : (c->lpt ? c->lpt : default_lpt(c->kind, c->dim));
   const KernelEntry* ke = lpt ? find_kernel(c->kind, c->dim, lpt, c->block, c->mix) : nullptr;
@@ -429,6 +463,93 @@ int irkgl_advance_t(irkgl_ctx* c, double* q, double* v, double* q_lo, double* v_
   a.status = status;
   a.accumulate = 1;
   return run(c, a, static_cast<cudaStream_t>(stream));
+}
+
+static int run1(irkgl_ctx* c, KArgs1& a, cudaStream_t st) {
+  if (!first_order_kind(c->kind)) return IRKGL_ERR_INVALID;
+  if (c->mix) return IRKGL_ERR_UNSUPPORTED;
+  const int lpt = c->lpt ? c->lpt : default_lpt(c->kind, c->dim);
+  const irkgl::KernelEntry1* ke = lpt ? find_kernel1(c->kind, c->dim, lpt, c->block) : nullptr;
+  if (!ke) return IRKGL_ERR_UNSUPPORTED;
+  a.counter = c->d_counter;
+  a.params = c->d_params;
+  a.kmax = c->kmax;
+  a.monitor = c->monitor;
+  const int traj_per_block = c->block / lpt;
+  const long long need = (static_cast<long long>(a.batch) + traj_per_block - 1) / traj_per_block;
+  int grid = c->grid_blocks;
+  if (grid <= 0) {
+    int per_sm = 0;
+    IRKGL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ke->fn, c->block, 0));
+    if (per_sm < 1) per_sm = 1;
+    grid = per_sm * c->sm_count;
+  }
+  if (grid > need) grid = static_cast<int>(need);
+  if (grid < 1) grid = 1;
+  IRKGL_CUDA(cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned), st));
+  ke->launch(dim3(grid), dim3(c->block), st, a, c->coef1);
+  IRKGL_CUDA(cudaGetLastError());
+  return IRKGL_OK;
+}
+
+int irkgl_integrate1(irkgl_ctx* c, const double* y0, int batch, const long long* nsteps,
+                     long long nsteps_all, const double* h, const int* order,
+                     const irkgl_outputs1* out, void* stream) {
+  if (!c || batch < 0 || !out) return IRKGL_ERR_INVALID;
+  if (!first_order_kind(c->kind)) return IRKGL_ERR_INVALID;
+  if (batch == 0) return IRKGL_OK;
+  if (!y0 || !out->y) return IRKGL_ERR_INVALID;
+  if (!nsteps && nsteps_all < 0) return IRKGL_ERR_INVALID;
+  KArgs1 a;
+  std::memset(&a, 0, sizeof(a));
+  a.batch = batch;
+  a.y_in = y0;
+  a.y_out = out->y;
+  a.ylo_out = out->y_lo;
+  a.lp_out = out->l_prev;
+  a.nsteps = nsteps;
+  a.nsteps_all = nsteps_all;
+  a.h = h;
+  a.h_all = c->h;
+  a.order = order;
+  a.iters_total = out->iters;
+  a.dH_max = out->dH_max;
+  a.status = out->status;
+  a.steps_done = out->steps;
+  return run1(c, a, static_cast<cudaStream_t>(stream));
+}
+
+int irkgl_advance1(irkgl_ctx* c, double* y, double* y_lo, double* l_prev, const double* h,
+                   const long long* nsteps, double* H0, int h0_init, double* dH_max,
+                   long long* iters, int* status, int batch, void* stream) {
+  if (!c || batch < 0) return IRKGL_ERR_INVALID;
+  if (!first_order_kind(c->kind)) return IRKGL_ERR_INVALID;
+  if (batch == 0) return IRKGL_OK;
+  if (!y || !y_lo || !l_prev || !nsteps) return IRKGL_ERR_INVALID;
+  if (dH_max && !H0) return IRKGL_ERR_INVALID;
+  KArgs1 a;
+  std::memset(&a, 0, sizeof(a));
+  a.batch = batch;
+  a.y_in = y;
+  a.ylo_in = y_lo;
+  a.lp_in = l_prev;
+  a.y_out = y;
+  a.ylo_out = y_lo;
+  a.lp_out = l_prev;
+  a.nsteps = nsteps;
+  a.h = h;
+  a.h_all = c->h;
+  a.iters_total = iters;
+  a.dH_max = dH_max;
+  a.status = status;
+  a.H0_io = H0;
+  a.h0_init = h0_init ? 1 : 0;
+  a.accumulate = 1;
+  const int saved_monitor = c->monitor;
+  if (!dH_max) c->monitor = 0;
+  const int rc = run1(c, a, static_cast<cudaStream_t>(stream));
+  c->monitor = saved_monitor;
+  return rc;
 }
 
 int irkgl_integrate(irkgl_ctx* c, const double* q0, const double* v0, int batch,

@@ -23,6 +23,7 @@ ERR_INVALID, ERR_NOMEM, ERR_CUDA, ERR_UNSUPPORTED = -1, -2, -3, -4
 STATUS_OK, STATUS_MAXITER, STATUS_NONFINITE = 0, 1, 2
 RHS_KEPLER, RHS_NBODY, RHS_FPUT, RHS_HENON_HEILES, RHS_HARMONIC = 1, 2, 3, 4, 5
 RHS_HENON_HEILES_FORCED = 6  # g(t, q): lambda + xi sin t (params = [lambda, xi])
+RHS_SCHWARZSCHILD, RHS_HARMONIC1 = 7, 8  # first-order kinds (dim = D): the irkgl_*1 calls
 OPT_LANES_PER_TRAJ, OPT_KMAX, OPT_MONITOR_EVERY, OPT_BLOCK_THREADS, OPT_GRID_BLOCKS = 1, 2, 3, 4, 5
 OPT_WIDE_TEAM = 6
 OPT_MONITOR_LOCAL = 7
@@ -64,6 +65,11 @@ class irkgl_outputs(ctypes.Structure):
                 ("dH_max", _P), ("iters", _P), ("steps", _P), ("status", _P)]
 
 
+class irkgl_outputs1(ctypes.Structure):
+    _fields_ = [("y", _P), ("y_lo", _P), ("l_prev", _P), ("dH_max", _P), ("iters", _P),
+                ("steps", _P), ("status", _P)]
+
+
 _lib = None
 
 
@@ -88,6 +94,9 @@ def load(path: str | None = None, build_if_missing: bool = False):
     L.irkgl_integrate.argtypes = [_P, _P, _P, ctypes.c_int, _P, ctypes.c_longlong, _P, _P,
                                   ctypes.POINTER(irkgl_outputs), _P]
     L.irkgl_integrate_host.argtypes = L.irkgl_integrate.argtypes
+    L.irkgl_integrate1.argtypes = [_P, _P, ctypes.c_int, _P, ctypes.c_longlong, _P, _P,
+                                   ctypes.POINTER(irkgl_outputs1), _P]
+    L.irkgl_advance1.argtypes = [_P, _P, _P, _P, _P, _P, _P, ctypes.c_int, _P, _P, _P, ctypes.c_int, _P]
     L.irkgl_destroy.argtypes = [_P]
     L.irkgl_destroy.restype = None
     L.irkgl_strerror.argtypes = [ctypes.c_int]
@@ -371,6 +380,60 @@ class RaggedOutputs:
                              _ptr(self.status, i32, None, "out.status"))
 
 
+@dataclass
+class Outputs1:
+    """Outputs of the first-order calls (device tensors, [B, D] / [B])."""
+    y: torch.Tensor
+    y_lo: torch.Tensor | None = None
+    l_prev: torch.Tensor | None = None
+    dH_max: torch.Tensor | None = None
+    iters: torch.Tensor | None = None
+    steps: torch.Tensor | None = None
+    status: torch.Tensor | None = None
+
+    @staticmethod
+    def allocate(batch: int, D: int, device="cuda"):
+        f = dict(dtype=torch.float64, device=device)
+        return Outputs1(y=torch.empty((batch, D), **f), y_lo=torch.empty((batch, D), **f),
+                        l_prev=torch.empty((batch, 8, D), **f), dH_max=torch.empty(batch, **f),
+                        iters=torch.empty(batch, dtype=torch.int64, device=device),
+                        steps=torch.empty(batch, dtype=torch.int64, device=device),
+                        status=torch.empty(batch, dtype=torch.int32, device=device))
+
+    def _struct(self, batch, D):
+        f64, i64, i32 = torch.float64, torch.int64, torch.int32
+        return irkgl_outputs1(_ptr(self.y, f64, (batch, D), "out.y"), _ptr(self.y_lo, f64, (batch, D), "out.y_lo"),
+                              _ptr(self.l_prev, f64, (batch, 8, D), "out.l_prev"),
+                              _ptr(self.dH_max, f64, (batch,), "out.dH_max"),
+                              _ptr(self.iters, i64, (batch,), "out.iters"),
+                              _ptr(self.steps, i64, (batch,), "out.steps"),
+                              _ptr(self.status, i32, (batch,), "out.status"))
+
+
+def irkgl_integrate1(ctx: int, D: int, y0, out: Outputs1, nsteps=None, nsteps_all: int = 0, h=None,
+                     order=None, stream=None):
+    """First-order kinds: y0 [B, D] device; nsteps int64 [B] (or nsteps_all); h [B]; order int32 [B]."""
+    B = y0.shape[0]
+    st = out._struct(B, D)
+    _check(load().irkgl_integrate1(
+        _P(ctx), _ptr(y0, torch.float64, (B, D), "y0"), B, _ptr(nsteps, torch.int64, (B,), "nsteps"),
+        int(nsteps_all), _ptr(h, torch.float64, (B,), "h"), _ptr(order, torch.int32, (B,), "order"),
+        ctypes.byref(st), _stream(stream)))
+
+
+def irkgl_advance1(ctx: int, D: int, y, y_lo, l_prev, nsteps, h=None, H0=None, h0_init: bool = False,
+                   dH_max=None, iters=None, status=None, stream=None):
+    """Continue first-order trajectories in place (y, y_lo [B, D], l_prev [B, 8, D])."""
+    B = y.shape[0]
+    f64 = torch.float64
+    _check(load().irkgl_advance1(
+        _P(ctx), _ptr(y, f64, (B, D), "y"), _ptr(y_lo, f64, (B, D), "y_lo"),
+        _ptr(l_prev, f64, (B, 8, D), "l_prev"), _ptr(h, f64, (B,), "h"),
+        _ptr(nsteps, torch.int64, (B,), "nsteps"), _ptr(H0, f64, (B,), "H0"), int(bool(h0_init)),
+        _ptr(dH_max, f64, (B,), "dH_max"), _ptr(iters, torch.int64, (B,), "iters"),
+        _ptr(status, torch.int32, (B,), "status"), B, _stream(stream)))
+
+
 def irkgl_integrate_ragged(ctx: int, inst: torch.Tensor, ninst: int, dmax: int, params, q0, v0,
                            out: RaggedOutputs, order=None, stream=None):
     """Ragged batch (device tensors): inst from instances_tensor(); packed
@@ -454,6 +517,14 @@ class Integrator:
         out = out or Outputs.allocate(q0.shape[0], self.dim, device=q0.device)
         irkgl_integrate(self.ctx, self.dim, q0, v0, out, **kw)
         return out
+
+    def integrate1(self, y0, out=None, **kw) -> Outputs1:
+        out = out or Outputs1.allocate(y0.shape[0], self.dim, device=y0.device)
+        irkgl_integrate1(self.ctx, self.dim, y0, out, **kw)
+        return out
+
+    def advance1(self, *args, **kw):
+        return irkgl_advance1(self.ctx, self.dim, *args, **kw)
 
     def integrate_host(self, q0, v0, out=None, **kw) -> Outputs:
         out = out or Outputs.allocate(q0.shape[0], self.dim, device="cpu")

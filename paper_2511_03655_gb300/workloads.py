@@ -120,6 +120,25 @@ def henon_heiles_ensemble(batch: int, energy: float = 1.0 / 12, seed_id: int = 7
     return np.array(q), np.array(v), t0
 
 
+SBH_PARAMS = (0.995, 4.6, 8.9e-4)  # E, L, beta of Sec. 5.1
+
+
+def schwarzschild_ensemble(batch: int, r_lo: float = 9.5, r_hi: float = 16.0, seed_id: int = 8,
+                           params=SBH_PARAMS):
+    """`batch` initial states of the Schwarzschild black-hole system of
+    Sec. 5.1 (Eq. Ham_SBH), y = (r, theta, p_r, p_theta): r0 ~ U[r_lo, r_hi),
+    theta = pi/2, p_r = 0 and p_theta > 0 from the energy condition H = -1/2
+    (the paper's single orbit is r0 = 11).  Returns y0 [batch, 4]."""
+    E, L, beta = params
+    r = r_lo + (r_hi - r_lo) * uniform(SEED_BASE + seed_id, batch)
+    u = 1.0 - 2.0 / r
+    a = L - 0.5 * beta * r * r
+    p2 = 2.0 * r * r * (-0.5 + E * E / (2.0 * u) - a * a / (2.0 * r * r))
+    if np.any(p2 <= 0):
+        raise ValueError("r range admits no p_theta with H = -1/2")
+    return np.stack([r, np.full(batch, math.pi / 2), np.zeros(batch), np.sqrt(p2)], axis=1)
+
+
 def similarity_order(key: np.ndarray, descending: bool = True) -> np.ndarray:
     """Processing order that puts trajectories with similar `key` (e.g. the
     eccentricity, or an estimated cost) next to each other, costliest first."""
