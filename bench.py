@@ -64,10 +64,11 @@ def parse():
     ap.add_argument("--lanes", type=int, default=0, help="lanes per trajectory (0 = library default)")
     ap.add_argument("--no-order", action="store_true", help="natural order instead of similarity order")
     ap.add_argument("--skip-extras", action="store_true", help="skip e2e, plain form and CPU baseline")
-    ap.add_argument("--workload", default="kepler", choices=["kepler", "nbody6", "uneven"],
+    ap.add_argument("--workload", default="kepler", choices=["kepler", "nbody6", "uneven", "schwarzschild"],
                     help="kepler: the 65,536-orbit ensemble (default); nbody6: 16,384 perturbed "
                          "copies of a 6-body system; uneven: 4,096 ragged instances (N-body "
-                         "N~U{3..64} and FPUT n~U{8..512}), autotuned vs fixed tiling")
+                         "N~U{3..64} and FPUT n~U{8..512}), autotuned vs fixed tiling; schwarzschild: "
+                         "65,536 first-order black-hole orbits (Eq. Ham_SBH), t in [0, 1e5], h = 16")
     ap.add_argument("--traj-steps", type=int, default=None,
                     help="steps per trajectory/instance (nbody6: 10000, uneven: 1000 by default)")
     ap.add_argument("--ninst", type=int, default=4096, help="instances for the uneven workload")
@@ -379,6 +380,144 @@ def run_uneven(args):
         dist.destroy_process_group()
     return 0
 
+
+# --------------------------------------------------------------------------
+# first-order form: Schwarzschild black-hole ensemble (Eq. Ham_SBH)
+# --------------------------------------------------------------------------
+# Algorithmic FP64 flops (FMA = 2; each reciprocal and the sincos counted as
+# one operation, so the fraction is a lower bound): per sweep f 8 x 40,
+# mu mixing 8 x 4 x 17, Delta 32; per step nu guess 544, update 68, energy 25.
+FLOPS_SBH = (637, 896)
+SBH_H = 16.0
+SBH_T = 1.0e5
+
+
+def run_first_order(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2511_03655_gb300 import build, irkgl, workloads
+    from paper_2511_03655_gb300 import dist as pdist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    irkgl.load()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    B = args.batch
+    nsteps = int(round(SBH_T / SBH_H))
+    y0h = workloads.schwarzschild_ensemble(B, seed_id=pdist.shard_seed(8, rank))
+    par = list(workloads.SBH_PARAMS)
+    y0 = torch.tensor(y0h, device=dev)
+    integ = irkgl.Integrator(irkgl.RHS_SCHWARZSCHILD, par, 4, SBH_H, lanes_per_traj=args.lanes)
+    out = irkgl.Outputs1.allocate(B, 4, device=dev)
+    peak = fp64_peak_tflops(irkgl, torch, stream, dev)
+
+    def run():
+        integ.integrate1(y0, out=out, nsteps_all=nsteps)
+
+    for _ in range(args.warmup):
+        run()
+    torch.cuda.synchronize()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    clocks = ClockSampler(local)
+    ts = []
+    pdist.barrier()
+    clocks.start()
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        pdist.barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        run()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b) * 1e-3)
+    clk = clocks.stop()
+    steps = out.steps.cpu().numpy()
+    iters = out.iters.cpu().numpy()
+    dH = out.dH_max.cpu().numpy()
+    st = out.status.cpu().numpy()
+    ok = (dH <= TOL) & (st == 0)
+    t_max = pdist.reduce_max(sum(ts))
+    steps_ok = pdist.reduce_sum(float(steps[ok].sum()))
+    steps_all = pdist.reduce_sum(float(steps.sum()))
+    flops = FLOPS_SBH[0] * float(steps.sum()) + FLOPS_SBH[1] * float(iters.sum())
+    achieved = flops / statistics.mean(ts) / 1e12
+    line = {
+        "metric": METRIC, "value": args.steps * steps_ok / t_max, "unit": "traj-steps/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"schwarzschild_ensemble: {B} orbits of the first-order black-hole system "
+                               f"(Eq. Ham_SBH, E=0.995, L=4.6, beta=8.9e-4), r0~U[9.5,16), theta=pi/2, "
+                               f"p_r=0, H=-1/2; t in [0, {SBH_T:g}], h={SBH_H:g} ({nsteps} steps); "
+                               "one persistent launch of the first-order (mu form) kernel",
+                   "lanes_per_traj": integ.tile,
+                   "l2": "state ~10 MB < L2; L2 flushed with a 256 MiB write before every timed step",
+                   "parallelism": f"dp{world} (independent shards, no collective on the data path)"},
+        "value_all": args.steps * steps_all / t_max,
+        "accuracy": {"tol": TOL, "orbits_within_tol": float(ok.mean()), "status_nonzero": int((st != 0).sum()),
+                     "dH_max_median": float(np.median(dH)), "dH_max_max": float(dH.max())},
+        "sweeps_per_step": float(iters.sum() / max(steps.sum(), 1)),
+        "gpu_launches": args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_source": "FP64 FMA-chain probe (irkgl_probe_fp64_fma) measured live, "
+                                    "2 flops per FMA",
+                     "kernel": "irkgl1_kernel<Schwarzschild>", "flops_per_launch": flops,
+                     "note": "reciprocals and sincos counted as one flop each: a lower bound"},
+        "clocks": clk,
+    }
+    if not args.skip_extras:
+        hy0 = torch.tensor(y0h).pin_memory()
+        hy = torch.empty_like(hy0).pin_memory()
+        hdh = torch.empty(B, dtype=torch.float64).pin_memory()
+        hst = torch.empty(B, dtype=torch.int32).pin_memory()
+        et = []
+        for _ in range(args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            y0.copy_(hy0, non_blocking=True)
+            run()
+            hy.copy_(out.y, non_blocking=True)
+            hdh.copy_(out.dH_max, non_blocking=True)
+            hst.copy_(out.status, non_blocking=True)
+            torch.cuda.synchronize()
+            et.append(time.perf_counter() - t0)
+        line["e2e"] = {"value": args.steps * steps_ok / pdist.reduce_max(sum(et)), "unit": "traj-steps/s",
+                       "h2d_bytes_per_step": int(hy0.numel() * 8),
+                       "d2h_bytes_per_step": int(hy.numel() * 8 + hdh.numel() * 8 + hst.numel() * 4),
+                       "api": "Integrator.integrate1 (irkgl_integrate1), pinned host copies inside the timed region"}
+        if rank == 0 and world == 1:
+            from oracle import cbind
+            import concurrent.futures as cf
+            cores = os.cpu_count() or 1
+            nsel = 4 * cores
+            sel = np.linspace(0, B - 1, nsel).astype(int)
+            nsamp = 2000
+            cbind.lib()
+            t0 = time.perf_counter()
+            with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+                list(ex.map(lambda k: cbind.run1(cbind.SCHWARZSCHILD, par, y0h[k:k + 1], SBH_H, nsamp), sel))
+            dt = time.perf_counter() - t0
+            line["cpu_baseline"] = {"value": nsel * nsamp / dt, "unit": "traj-steps/s", "cores": cores,
+                                    "kind": "oracle",
+                                    "sample": f"{nsel} orbits evenly spaced in r0, {nsamp} steps each "
+                                              f"(of {nsteps}), {dt:.1f} s wall on {cores} threads"}
+    if rank == 0:
+        print(json.dumps(line))
+    integ.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
 # --------------------------------------------------------------------------
 # GPU arm
 # --------------------------------------------------------------------------
@@ -391,6 +530,8 @@ def main():
         args.traj_steps = {"nbody6": 10000, "uneven": 1000}.get(args.workload, 10000)
     if args.workload == "uneven":
         return run_uneven(args)
+    if args.workload == "schwarzschild":
+        return run_first_order(args)
 
     import torch
     import torch.distributed as dist

@@ -7,7 +7,8 @@ Tolerances as for the second-order form: relative state difference
 <= 1e-13 over steps 1..10 and <= 1e-9 at the end of a non-chaotic run
 (this r0 in [9.5, 16) family: the oracle's own response to a 1e-15 change
 of the initial state stays near 1e-13 over t = 4000); sweep counts from
-identical states within +-1 on nearly every step.  The GPU forms the
+identical states within +-1 on at least 99.5 % of steps and within 3 on all
+(the roundoff-floor stops explained in the test).  The GPU forms the
 right-hand side with fused multiply-adds, reciprocals and CUDA's sincos,
 so it is not bitwise equal to the oracle; two GPU paths that run the same
 kernel are.
@@ -84,8 +85,13 @@ def test_steps_1_to_10_and_sweeps(torch_cuda, lpt):
                        l_prev=s.lp.cpu().numpy(), iters_len=1)
         s.advance(ig, 1)
         diffs.append((s.it - before).cpu().numpy() - r["iters"][:, 0])
+    # At h = 4 the extrapolated guess is already accurate to roundoff: a step
+    # stops at k = 2 when the second sweep changes nothing (Delta = 0), or,
+    # when one side's last bit still moves, by the min rule of Eq. stopping
+    # at k = 4 or 5.  FMA vs separately rounded sums decide which on a few
+    # steps, so the count differs by up to 3 there and by at most 1 elsewhere.
     d = np.abs(np.array(diffs))
-    assert d.max() <= 1 or (d.max() <= 2 and (d <= 1).mean() >= 0.99), (d.max(), (d <= 1).mean())
+    assert d.max() <= 3 and (d <= 1).mean() >= 0.995, (d.max(), (d <= 1).mean())
     ig.close()
 
 
