@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--traj-steps", type=int, default=None,
                     help="steps per trajectory/instance (nbody6: 10000, uneven: 1000 by default)")
     ap.add_argument("--ninst", type=int, default=4096, help="instances for the uneven workload")
+    ap.add_argument("--stage-sweep", action="store_true",
+                    help="schwarzschild: also the work-precision sweep of the s = 2, 4, 6, 8 schemes")
     ap.add_argument("--mix", type=int, default=0, choices=[0, 1],
                     help="stage mixing: 0 FP64 FMA chain, 1 fixed-point sums on the integer pipes")
     ap.add_argument("--serve-requests", type=int, default=300,
@@ -392,6 +394,38 @@ SBH_H = 16.0
 SBH_T = 1.0e5
 
 
+def stage_sweep(torch, irkgl, workloads, par, stream, dev, B=16384, T=2000.0):
+    """Work-precision points of the s-stage schemes (s = 2, 4, 6, 8) on the
+    Schwarzschild ensemble: for each s and step h, the max over orbits of the
+    local energy error (Eq. DHlocmax), the g-evaluations per orbit (s x
+    sweeps) and the GPU time for t in [0, T] (the GPU form of the paper's
+    Fig. ODE1_IRKGL)."""
+    y0 = torch.tensor(workloads.schwarzschild_ensemble(B, seed_id=40), device=dev)
+    ladders = {2: (0.125, 0.25, 0.5, 1.0), 4: (0.5, 1.0, 2.0, 4.0),
+               6: (1.0, 2.0, 4.0, 8.0), 8: (2.0, 4.0, 8.0, 16.0)}
+    pts = []
+    for s, hs in ladders.items():
+        for h in hs:
+            n = int(round(T / h))
+            ig = irkgl.Integrator(irkgl.RHS_SCHWARZSCHILD, par, 4, h, stages=s)
+            ig.set(irkgl.OPT_MONITOR_LOCAL, 1)
+            out = ig.integrate1(y0, nsteps_all=n)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ig.integrate1(y0, out=out, nsteps_all=n)
+            b.record(stream)
+            torch.cuda.synchronize()
+            it = out.iters.cpu().numpy()
+            pts.append({"s": s, "h": h, "steps": n, "lanes_per_traj": ig.tile,
+                        "dH_loc_max": float(out.dH_max.cpu().numpy().max()),
+                        "g_evals_per_orbit": float(s * it.mean()), "sweeps_per_step": float(it.mean() / n),
+                        "seconds": a.elapsed_time(b) * 1e-3,
+                        "status_nonzero": int((out.status.cpu().numpy() != 0).sum())})
+            ig.close()
+    return {"orbits": B, "t_end": T, "points": pts}
+
+
 def run_first_order(args):
     import torch
     import torch.distributed as dist
@@ -499,18 +533,22 @@ def run_first_order(args):
             from oracle import cbind
             import concurrent.futures as cf
             cores = os.cpu_count() or 1
-            nsel = 4 * cores
+            # bounded sample of about 10 s: orbits evenly spaced in r0, the
+            # full horizon, split into chunks over the host cores
+            nsel = min(B, 16384)
             sel = np.linspace(0, B - 1, nsel).astype(int)
-            nsamp = 2000
+            chunks = np.array_split(sel, 8 * cores)
             cbind.lib()
             t0 = time.perf_counter()
             with cf.ThreadPoolExecutor(max_workers=cores) as ex:
-                list(ex.map(lambda k: cbind.run1(cbind.SCHWARZSCHILD, par, y0h[k:k + 1], SBH_H, nsamp), sel))
+                list(ex.map(lambda c: cbind.run1(cbind.SCHWARZSCHILD, par, y0h[c], SBH_H, nsteps), chunks))
             dt = time.perf_counter() - t0
-            line["cpu_baseline"] = {"value": nsel * nsamp / dt, "unit": "traj-steps/s", "cores": cores,
+            line["cpu_baseline"] = {"value": nsel * nsteps / dt, "unit": "traj-steps/s", "cores": cores,
                                     "kind": "oracle",
-                                    "sample": f"{nsel} orbits evenly spaced in r0, {nsamp} steps each "
-                                              f"(of {nsteps}), {dt:.1f} s wall on {cores} threads"}
+                                    "sample": f"{nsel} orbits evenly spaced in r0, full horizon ({nsteps} "
+                                              f"steps), {dt:.1f} s wall on {cores} threads"}
+        if args.stage_sweep:
+            line["stage_sweep"] = stage_sweep(torch, irkgl, workloads, par, stream, dev)
     if rank == 0:
         print(json.dumps(line))
     integ.close()

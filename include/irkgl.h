@@ -147,10 +147,14 @@ enum {
   IRKGL_OPT_MONITOR_LOCAL = 7,  /* 1: dH_max reports the local error max_n |(H_n - H_{n-1})/H_{n-1}|
                                    (Eq. DHlocmax) instead of the global one (default 0; not
                                    carried across irkgl_advance calls) */
-  IRKGL_OPT_MIX = 8             /* stage mixing of Eq. Qi2 and the initial guess: 0 = FP64 FMA
+  IRKGL_OPT_MIX = 8,            /* stage mixing of Eq. Qi2 and the initial guess: 0 = FP64 FMA
                                    chain (default); 1 = exact fixed-point sums on the integer
                                    pipes, rounded once (one lane per trajectory, default tables
                                    only; IRKGL_ERR_UNSUPPORTED otherwise) */
+  IRKGL_OPT_STAGES = 9          /* first-order kinds: s of the s-stage IRKGL scheme, 2, 4, 6 or 8
+                                   (default 8 = IRKGL16; s < 8 uses the built-in Gauss tables of
+                                   that s, order 2s).  l_prev arrays are then [batch][s][D].  The
+                                   second-order calls accept only 8 (IRKGL_ERR_UNSUPPORTED) */
 };
 
 /* Fill *out with the default IRKGL16 tables of Sec. 2.4 (nodes c and weights

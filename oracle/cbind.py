@@ -68,7 +68,7 @@ def lib():
                                     + L.orc_run.argtypes[11:])
             L.orc_run1.restype = ctypes.c_int
             L.orc_run1.argtypes = [
-                P(OrcTab), ctypes.c_int, P(ctypes.c_double), ctypes.c_int, ctypes.c_int,
+                P(OrcTab), ctypes.c_int, ctypes.c_int, P(ctypes.c_double), ctypes.c_int, ctypes.c_int,
                 P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double),
                 P(ctypes.c_longlong), ctypes.c_int, P(ctypes.c_int), ctypes.c_int,
                 P(ctypes.c_longlong), P(ctypes.c_double), P(ctypes.c_int), P(ctypes.c_longlong)]
@@ -82,15 +82,18 @@ def lib():
 
 
 def table(tab: dict | None = None) -> OrcTab:
+    """C table of an s-stage scheme (s <= 8): c, b [s]; mu, eta, nu packed
+    row-major with stride s (s = 8: the IRKGL16 layout [i*8+j])."""
     tab = tab or coeffs.fp64_tables()
+    s = len(tab["c"])
     t = OrcTab()
-    for i in range(8):
+    for i in range(s):
         t.c[i] = tab["c"][i]
         t.b[i] = tab["b"][i]
-        for j in range(8):
-            t.mu[i * 8 + j] = tab["mu"][i][j]
-            t.eta[i * 8 + j] = tab["eta"][i][j]
-            t.nu[i * 8 + j] = tab["nu"][i][j]
+        for j in range(s):
+            t.mu[i * s + j] = tab["mu"][i][j]
+            t.eta[i * s + j] = tab["eta"][i][j]
+            t.nu[i * s + j] = tab["nu"][i][j]
     return t
 
 
@@ -160,32 +163,35 @@ def hamiltonian(kind: int, params, q, v) -> float:
 
 
 def run1(kind: int, params, y, h, nsteps, *, y_lo=None, l_prev=None, iters_len: int = 0,
-         kmax: int = 100, tab: dict | None = None):
+         kmax: int = 100, tab: dict | None = None, stages: int = 8):
     """Advance a batch of first-order trajectories with the C oracle
-    (SCHWARZSCHILD: y = (r, theta, p_r, p_theta); HARMONIC1: y = (q, p)).
+    (SCHWARZSCHILD: y = (r, theta, p_r, p_theta); HARMONIC1: y = (q, p)),
+    s-stage scheme (stages = s; tab defaults to coeffs.fp64_tables(s)).
     y: (batch, D).  params: (P,) shared or (batch, P).  Returns y, y_lo,
-    l_prev (batch, 8, D), iters, iters_total, dH_max, status, steps."""
+    l_prev (batch, s, D), iters, iters_total, dH_max, status, steps."""
     D = DIM1[kind]
+    tab = tab or coeffs.fp64_tables(stages)
+    ns = len(tab["c"])
     y = np.array(y, dtype=np.float64, order="C", copy=True).reshape(-1, D)
     batch = y.shape[0]
     y_lo = (np.zeros_like(y) if y_lo is None
             else np.array(y_lo, dtype=np.float64, order="C", copy=True).reshape(batch, D))
-    l_prev = (np.zeros((batch, 8, D)) if l_prev is None
-              else np.array(l_prev, dtype=np.float64, order="C", copy=True).reshape(batch, 8, D))
+    l_prev = (np.zeros((batch, ns, D)) if l_prev is None
+              else np.array(l_prev, dtype=np.float64, order="C", copy=True).reshape(batch, ns, D))
     params = np.ascontiguousarray(np.asarray(params, dtype=np.float64))
     pstride = params.shape[-1] if params.ndim == 2 else 0
     hh = np.ascontiguousarray(np.broadcast_to(np.asarray(h, dtype=np.float64), (batch,)))
-    ns = np.ascontiguousarray(np.broadcast_to(np.asarray(nsteps, dtype=np.int64), (batch,)))
+    nst = np.ascontiguousarray(np.broadcast_to(np.asarray(nsteps, dtype=np.int64), (batch,)))
     iters = np.zeros((batch, max(iters_len, 1)), dtype=np.int32)
     tot = np.zeros(batch, dtype=np.int64)
     dH = np.zeros(batch, dtype=np.float64)
     st = np.zeros(batch, dtype=np.int32)
     steps = np.zeros(batch, dtype=np.int64)
     t = table(tab)
-    rc = lib().orc_run1(ctypes.byref(t), kind, _ptr(params, ctypes.c_double), pstride, batch,
+    rc = lib().orc_run1(ctypes.byref(t), ns, kind, _ptr(params, ctypes.c_double), pstride, batch,
                         _ptr(y, ctypes.c_double), _ptr(y_lo, ctypes.c_double),
                         _ptr(l_prev, ctypes.c_double), _ptr(hh, ctypes.c_double),
-                        _ptr(ns, ctypes.c_longlong), kmax,
+                        _ptr(nst, ctypes.c_longlong), kmax,
                         _ptr(iters, ctypes.c_int) if iters_len > 0 else None, iters_len,
                         _ptr(tot, ctypes.c_longlong), _ptr(dH, ctypes.c_double),
                         _ptr(st, ctypes.c_int), _ptr(steps, ctypes.c_longlong))

@@ -475,20 +475,21 @@ static double rhs_H1(int kind, const double* p, const double* y) {
 
 static int dim1(int kind) { return kind == ORC1_SCHWARZSCHILD ? 4 : 2; }
 
-/* One first-order step; work sized 4*S*D + 2*D doubles. */
-static int one_step1(const orc_tab* t, int kind, const double* p, int D, double h, int kmax,
+/* One first-order step of the ns-stage scheme (tables packed row-major with
+ * stride ns); work sized 4*ns*D + 2*D doubles. */
+static int one_step1(const orc_tab* t, int ns, int kind, const double* p, int D, double h, int kmax,
                      double* y, double* ylo, double* lp, int* kout, double* work) {
-  double* Y = work;          /* S*D */
-  double* Yn = Y + S * D;    /* S*D */
-  double* F = Yn + S * D;    /* S*D */
-  double* L = F + S * D;     /* S*D */
-  double* dmin = L + S * D;  /* D */
+  double* Y = work;          /* ns*D */
+  double* Yn = Y + ns * D;   /* ns*D */
+  double* F = Yn + ns * D;   /* ns*D */
+  double* L = F + ns * D;    /* ns*D */
+  double* dmin = L + ns * D;  /* D */
   double* dprev = dmin + D;  /* D */
   /* init, Eq. IRK_init */
-  for (int i = 0; i < S; i++)
+  for (int i = 0; i < ns; i++)
     for (int l = 0; l < D; l++) {
-      double acc = t->nu[i * S] * lp[l];
-      for (int j = 1; j < S; j++) acc = acc + t->nu[i * S + j] * lp[j * D + l];
+      double acc = t->nu[i * ns] * lp[l];
+      for (int j = 1; j < ns; j++) acc = acc + t->nu[i * ns + j] * lp[j * D + l];
       Y[i * D + l] = y[l] + acc;
     }
   for (int l = 0; l < D; l++) {
@@ -498,14 +499,14 @@ static int one_step1(const orc_tab* t, int kind, const double* p, int D, double 
   int k = 0;
   for (;;) {
     k++;
-    for (int i = 0; i < S; i++) rhs_f1(kind, p, Y + i * D, F + i * D);
-    for (int i = 0; i < S; i++)
+    for (int i = 0; i < ns; i++) rhs_f1(kind, p, Y + i * D, F + i * D);
+    for (int i = 0; i < ns; i++)
       for (int l = 0; l < D; l++) L[i * D + l] = h * (t->b[i] * F[i * D + l]);
     int finite = 1;
-    for (int i = 0; i < S; i++)
+    for (int i = 0; i < ns; i++)
       for (int l = 0; l < D; l++) {
-        double acc = t->mu[i * S] * L[l];
-        for (int j = 1; j < S; j++) acc = acc + t->mu[i * S + j] * L[j * D + l];
+        double acc = t->mu[i * ns] * L[l];
+        for (int j = 1; j < ns; j++) acc = acc + t->mu[i * ns + j] * L[j * D + l];
         double x = y[l] + acc;
         Yn[i * D + l] = x;
         if (!isfinite(x)) finite = 0;
@@ -517,7 +518,7 @@ static int one_step1(const orc_tab* t, int kind, const double* p, int D, double 
     int stop = 1;
     for (int l = 0; l < D; l++) {
       double delta = 0.0;
-      for (int i = 0; i < S; i++) {
+      for (int i = 0; i < ns; i++) {
         double a = fabs(Yn[i * D + l] - Y[i * D + l]);
         if (a > delta) delta = a;
       }
@@ -527,7 +528,7 @@ static int one_step1(const orc_tab* t, int kind, const double* p, int D, double 
       dmin[l] = dmin[l] <= dprev[l] ? dmin[l] : dprev[l];
       dprev[l] = delta;
     }
-    memcpy(Y, Yn, sizeof(double) * S * D);
+    memcpy(Y, Yn, sizeof(double) * ns * D);
     if (stop) break;
     if (k >= kmax) {
       *kout = k;
@@ -537,40 +538,42 @@ static int one_step1(const orc_tab* t, int kind, const double* p, int D, double 
   *kout = k;
   for (int l = 0; l < D; l++) {
     double sL = L[l];
-    for (int i = 1; i < S; i++) sL = sL + L[i * D + l];
+    for (int i = 1; i < ns; i++) sL = sL + L[i * D + l];
     two_sum_add(&y[l], &ylo[l], sL);
   }
-  memcpy(lp, L, sizeof(double) * S * D);
+  memcpy(lp, L, sizeof(double) * ns * D);
   return ORC_OK;
 }
 
 /*
  * Advance `batch` first-order trajectories (D = 4 for ORC1_SCHWARZSCHILD,
- * 2 for ORC1_HARMONIC) by nsteps[t] steps of size h[t], in place: y, y_lo
- * [batch*D], l_prev [batch*8*D].  Optional outputs as for orc_run
+ * 2 for ORC1_HARMONIC) of the ns-stage scheme (ns <= 8; tab holds b, mu,
+ * nu packed with stride ns) by nsteps[t] steps of size h[t], in place: y,
+ * y_lo [batch*D], l_prev [batch*ns*D].  Optional outputs as for orc_run
  * (dH_max relative to H at entry).  Single-threaded.  Returns 0, -1 on
  * allocation failure, -2 for an unknown kind.
  */
-int orc_run1(const orc_tab* tab, int kind, const double* params, int pstride, int batch, double* y,
-             double* y_lo, double* l_prev, const double* h, const long long* nsteps, int kmax,
-             int* iters, int iters_stride, long long* iters_total, double* dH_max, int* status,
-             long long* steps_done) {
+int orc_run1(const orc_tab* tab, int ns, int kind, const double* params, int pstride, int batch,
+             double* y, double* y_lo, double* l_prev, const double* h, const long long* nsteps,
+             int kmax, int* iters, int iters_stride, long long* iters_total, double* dH_max,
+             int* status, long long* steps_done) {
   if (kind != ORC1_SCHWARZSCHILD && kind != ORC1_HARMONIC) return -2;
+  if (ns < 1 || ns > S) return -2;
   const int D = dim1(kind);
-  double* work = (double*)malloc(sizeof(double) * (4 * S * D + 2 * D));
+  double* work = (double*)malloc(sizeof(double) * (4 * ns * D + 2 * D));
   if (!work) return -1;
   for (int t = 0; t < batch; t++) {
     const double* p = params + (size_t)t * pstride;
     double* yy = y + (size_t)t * D;
     double* yl = y_lo + (size_t)t * D;
-    double* lp = l_prev + (size_t)t * S * D;
+    double* lp = l_prev + (size_t)t * ns * D;
     double H0 = rhs_H1(kind, p, yy);
     double dmax = 0.0;
     long long tot = 0, n = 0;
     int st = ORC_OK;
     for (n = 0; n < nsteps[t]; n++) {
       int k = 0;
-      st = one_step1(tab, kind, p, D, h[t], kmax, yy, yl, lp, &k, work);
+      st = one_step1(tab, ns, kind, p, D, h[t], kmax, yy, yl, lp, &k, work);
       if (iters && n < iters_stride) iters[(size_t)t * iters_stride + n] = k;
       tot += k;
       if (st != ORC_OK) break;

@@ -55,13 +55,32 @@ const KernelEntry* find_kernel(int kind, int dim, int lpt, int block, int mix = 
 
 // Built-in default tile per (kind, dim): the smallest LPT that is compiled,
 // preferring 2 for d = 2 (both components' compensated updates in one pass).
-const irkgl::KernelEntry1* find_kernel1(int kind, int dim, int lpt, int block) {
+const irkgl::KernelEntry1* find_kernel1(int kind, int dim, int lpt, int block, int nst = 8) {
   const irkgl::KernelTable1 t = irkgl::kernels_first_order();
   for (int i = 0; i < t.count; i++) {
     const irkgl::KernelEntry1& e = t.entries[i];
-    if (e.kind == kind && e.dim == dim && e.lpt == lpt && e.block == block) return &e;
+    if (e.kind == kind && e.dim == dim && e.lpt == lpt && e.block == block && e.nst == nst) return &e;
   }
   return nullptr;
+}
+
+// Tables of the s-stage first-order form (s = 2, 4, 6 generated; s = 8 is
+// the context's own IRKGL16 table).
+bool small_stage_tables(int s, Coef1* out) {
+  const double *b = nullptr, *mu = nullptr, *nu = nullptr;
+  switch (s) {
+    case 2: b = IRKGL_TAB2_B; mu = IRKGL_TAB2_MU; nu = IRKGL_TAB2_NU; break;
+    case 4: b = IRKGL_TAB4_B; mu = IRKGL_TAB4_MU; nu = IRKGL_TAB4_NU; break;
+    case 6: b = IRKGL_TAB6_B; mu = IRKGL_TAB6_MU; nu = IRKGL_TAB6_NU; break;
+    default: return false;
+  }
+  std::memset(out, 0, sizeof(*out));
+  for (int i = 0; i < s; i++) out->b[i] = b[i];
+  for (int x = 0; x < s * s; x++) {
+    out->mu[x] = mu[x];
+    out->nu[x] = nu[x];
+  }
+  return true;
 }
 
 // Right-hand sides of first-order systems y' = f(y) (the mu form).
@@ -69,12 +88,18 @@ bool first_order_kind(int kind) {
   return kind == IRKGL_RHS_SCHWARZSCHILD || kind == IRKGL_RHS_HARMONIC1;
 }
 
-int default_lpt(int kind, int dim) {
-  const int prefs[] = {2, 1, 8, 4};
-  for (int p : prefs)
-    if (first_order_kind(kind) ? find_kernel1(kind, dim, p, 128) != nullptr
+int default_lpt(int kind, int dim, int nst = 8) {
+  // measured preferences: two lanes for the second-order kinds (Kepler
+  // ensemble); four for the first-order ones (Schwarzschild: 128 registers,
+  // no spills, 10 % faster than two lanes)
+  const int prefs2[] = {2, 1, 8, 4};
+  const int prefs1[] = {4, 2, 1, 8};
+  for (int i = 0; i < 4; i++) {
+    const int p = first_order_kind(kind) ? prefs1[i] : prefs2[i];
+    if (first_order_kind(kind) ? find_kernel1(kind, dim, p, 128, nst) != nullptr
                                : find_kernel(kind, dim, p, 128) != nullptr)
       return p;
+  }
   return 0;
 }
 
@@ -130,6 +155,7 @@ struct irkgl_ctx {
   int wide_team;
   int monitor_local;
   int mix;             // IRKGL_OPT_MIX
+  int stages;          // IRKGL_OPT_STAGES (first-order kinds: 2, 4, 6 or 8)
   int default_tables;  // the context uses irkgl_default_coeffs (needed by mix = 1)
   // staging for irkgl_integrate_host
   void* d_stage;
@@ -230,6 +256,7 @@ int irkgl_create(irkgl_ctx** out, irkgl_rhs f, int dim, double h, const irkgl_co
   c->block = 128;
   c->lpt = 0;
   c->grid_blocks = 0;
+  c->stages = 8;
   cudaError_t e = cudaGetDevice(&c->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device);
   if (e != cudaSuccess) {
@@ -308,6 +335,10 @@ int irkgl_set_option(irkgl_ctx* c, int option, long long value) {
       if (value != 0 && value != 1) return IRKGL_ERR_INVALID;
       c->mix = static_cast<int>(value);
       return IRKGL_OK;
+    case IRKGL_OPT_STAGES:
+      if (!(value == 2 || value == 4 || value == 6 || value == 8)) return IRKGL_ERR_INVALID;
+      c->stages = static_cast<int>(value);
+      return IRKGL_OK;
     case IRKGL_OPT_MONITOR_LOCAL:
       if (value != 0 && value != 1) return IRKGL_ERR_INVALID;
       c->monitor_local = static_cast<int>(value);
@@ -325,8 +356,8 @@ int irkgl_set_option(irkgl_ctx* c, int option, long long value) {
 int irkgl_get_tile(irkgl_ctx* c) {
   if (!c) return IRKGL_ERR_INVALID;
   if (first_order_kind(c->kind)) {
-    const int lpt = c->lpt ? c->lpt : default_lpt(c->kind, c->dim);
-    return find_kernel1(c->kind, c->dim, lpt, c->block) ? lpt : 0;
+    const int lpt = c->lpt ? c->lpt : default_lpt(c->kind, c->dim, c->stages);
+    return find_kernel1(c->kind, c->dim, lpt, c->block, c->stages) ? lpt : 0;
   }
   if (c->mix) return find_kernel(c->kind, c->dim, 1, c->block, 1) ? 1 : 0;
   return c->lpt ? c->lpt : default_lpt(c->kind, c->dim);
@@ -337,6 +368,7 @@ static bool time_dependent_kind(int kind) { return kind == IRKGL_RHS_HENON_HEILE
 
 static int run(irkgl_ctx* c, KArgs& a, cudaStream_t st) {
   if (first_order_kind(c->kind)) return IRKGL_ERR_INVALID;  // use the irkgl_*1 calls
+  if (c->stages != 8) return IRKGL_ERR_UNSUPPORTED;        // s-stage variants: first-order form only
   if (c->mix && !c->default_tables) return IRKGL_ERR_UNSUPPORTED;
   const int lpt = c->mix ? 1 : (c->lpt ? c->lpt : default_lpt(c->kind, c->dim));
   const KernelEntry* ke = lpt ? find_kernel(c->kind, c->dim, lpt, c->block, c->mix) : nullptr;
@@ -468,13 +500,16 @@ int irkgl_advance_t(irkgl_ctx* c, double* q, double* v, double* q_lo, double* v_
 static int run1(irkgl_ctx* c, KArgs1& a, cudaStream_t st) {
   if (!first_order_kind(c->kind)) return IRKGL_ERR_INVALID;
   if (c->mix) return IRKGL_ERR_UNSUPPORTED;
-  const int lpt = c->lpt ? c->lpt : default_lpt(c->kind, c->dim);
-  const irkgl::KernelEntry1* ke = lpt ? find_kernel1(c->kind, c->dim, lpt, c->block) : nullptr;
+  const int lpt = c->lpt ? c->lpt : default_lpt(c->kind, c->dim, c->stages);
+  const irkgl::KernelEntry1* ke = lpt ? find_kernel1(c->kind, c->dim, lpt, c->block, c->stages) : nullptr;
   if (!ke) return IRKGL_ERR_UNSUPPORTED;
+  Coef1 small;
+  if (c->stages != 8 && !small_stage_tables(c->stages, &small)) return IRKGL_ERR_UNSUPPORTED;
   a.counter = c->d_counter;
   a.params = c->d_params;
   a.kmax = c->kmax;
   a.monitor = c->monitor;
+  a.monitor_local = c->monitor_local;
   const int traj_per_block = c->block / lpt;
   const long long need = (static_cast<long long>(a.batch) + traj_per_block - 1) / traj_per_block;
   int grid = c->grid_blocks;
@@ -487,7 +522,7 @@ static int run1(irkgl_ctx* c, KArgs1& a, cudaStream_t st) {
   if (grid > need) grid = static_cast<int>(need);
   if (grid < 1) grid = 1;
   IRKGL_CUDA(cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned), st));
-  ke->launch(dim3(grid), dim3(c->block), st, a, c->coef1);
+  ke->launch(dim3(grid), dim3(c->block), st, a, c->stages == 8 ? c->coef1 : small);
   IRKGL_CUDA(cudaGetLastError());
   return IRKGL_OK;
 }

@@ -21,8 +21,8 @@ namespace irkgl {
 
 struct Coef1 {
   double b[S];
-  double mu[S * S];  // Eq. Yi2, row-major [i*8+j]
-  double nu[S * S];  // Eq. IRK_init, scaled by 1/b_j
+  double mu[S * S];  // Eq. Yi2, row-major [i*s+j] for an s-stage kernel
+  double nu[S * S];  // Eq. IRK_init, scaled by 1/b_j, same layout
 };
 
 struct KArgs1 {
@@ -32,7 +32,7 @@ struct KArgs1 {
   int hist_len;
   const double* y_in;
   const double* ylo_in;  // may be null (zeros)
-  const double* lp_in;   // [batch][8][D] L of the previous step, may be null (zeros)
+  const double* lp_in;   // [batch][s][D] L of the previous step, may be null (zeros)
   double* y_out;
   double* ylo_out;       // may be null
   double* lp_out;        // may be null
@@ -51,6 +51,7 @@ struct KArgs1 {
   double* H0_io;
   int h0_init;
   int accumulate;
+  int monitor_local;  // 1: dH_max = max_n |(H_n - H_{n-1}) / H_{n-1}| (Eq. DHlocmax)
 };
 
 // ------------------------------------------------------------------------
@@ -143,20 +144,23 @@ __device__ __forceinline__ double group_energy1(const Rhs& rhs, const double (&y
   return rhs.H(yf);
 }
 
-template <class Rhs, int LPT, int BLOCK>
+template <class Rhs, int LPT, int BLOCK, int NST = S>
 __global__ void __launch_bounds__(BLOCK)
     irkgl1_kernel(const __grid_constant__ KArgs1 a, const __grid_constant__ Coef1 cf) {
+  // NST stages (the s of an s-stage IRKGL scheme; 8 for IRKGL16); the
+  // tables hold the NST x NST matrices row-major with stride NST
+  static_assert(NST >= 1 && NST <= S && NST % LPT == 0, "stages must split evenly over the lanes");
   constexpr int D = Rhs::D;
-  constexpr int SPL = S / LPT;
+  constexpr int SPL = NST / LPT;
   constexpr int NS = (D + LPT - 1) / LPT;
-  constexpr int PAD = S + 1;
+  constexpr int PAD = NST + 1;
 
-  __shared__ double s_mu[(LPT > 1) ? S * PAD : 1];
-  __shared__ double s_nu[(LPT > 1) ? S * PAD : 1];
+  __shared__ double s_mu[(LPT > 1) ? NST * PAD : 1];
+  __shared__ double s_nu[(LPT > 1) ? NST * PAD : 1];
   if constexpr (LPT > 1) {
-    for (int x = threadIdx.x; x < S * S; x += BLOCK) {
-      s_mu[(x / S) * PAD + (x % S)] = cf.mu[x];
-      s_nu[(x / S) * PAD + (x % S)] = cf.nu[x];
+    for (int x = threadIdx.x; x < NST * NST; x += BLOCK) {
+      s_mu[(x / NST) * PAD + (x % NST)] = cf.mu[x];
+      s_nu[(x / NST) * PAD + (x % NST)] = cf.nu[x];
     }
     __syncthreads();
   }
@@ -166,8 +170,8 @@ __global__ void __launch_bounds__(BLOCK)
   const int gbase = lane - r;
   const int i0 = r * SPL;
   const bool leader = (r == 0);
-#define IRKGL1_MU(t, j) ((LPT == 1) ? cf.mu[(t) * S + (j)] : s_mu[(i0 + (t)) * PAD + (j)])
-#define IRKGL1_NU(t, j) ((LPT == 1) ? cf.nu[(t) * S + (j)] : s_nu[(i0 + (t)) * PAD + (j)])
+#define IRKGL1_MU(t, j) ((LPT == 1) ? cf.mu[(t) * NST + (j)] : s_mu[(i0 + (t)) * PAD + (j)])
+#define IRKGL1_NU(t, j) ((LPT == 1) ? cf.nu[(t) * NST + (j)] : s_nu[(i0 + (t)) * PAD + (j)])
 
   Rhs rhs;
   rhs.load_params(a.params);
@@ -176,6 +180,7 @@ __global__ void __launch_bounds__(BLOCK)
   double L[SPL][D];  // own stages' L (Lprev between steps)
   double Y[SPL][D];  // own stages' values
   double h = 0.0, H0 = 0.0, invH0 = 0.0, dHmax = 0.0;
+  double Hprev = 0.0, invHprev = 0.0;  // local-error monitor
   long long n = 0, N = 0, itot = 0;
   int traj = -1, st = ST_OK;
   bool active = false, exhausted = false;
@@ -216,6 +221,8 @@ __global__ void __launch_bounds__(BLOCK)
             if (a.H0_io && !a.h0_init) {
               H0 = a.H0_io[t];
               invH0 = 1.0 / H0;
+              Hprev = H0;
+              invHprev = invH0;
             }
             const size_t off = static_cast<size_t>(t) * D;
 #pragma unroll
@@ -225,7 +232,7 @@ __global__ void __launch_bounds__(BLOCK)
               yh[s] = in ? a.y_in[off + l] : 0.0;
               yl[s] = (a.ylo_in && in) ? a.ylo_in[off + l] : 0.0;
             }
-            const size_t loff = static_cast<size_t>(t) * S * D;
+            const size_t loff = static_cast<size_t>(t) * NST * D;
 #pragma unroll
             for (int tt = 0; tt < SPL; tt++)
 #pragma unroll
@@ -247,6 +254,8 @@ __global__ void __launch_bounds__(BLOCK)
       if (want) {
         H0 = group_energy1<Rhs, LPT, NS>(rhs, yh, h0mask, gbase);
         invH0 = 1.0 / H0;
+        Hprev = H0;
+        invHprev = invH0;
         if (a.H0_io && leader) a.H0_io[traj] = H0;
       }
     }
@@ -263,7 +272,7 @@ __global__ void __launch_bounds__(BLOCK)
 #pragma unroll
         for (int t = 0; t < SPL; t++) acc[t] = 0.0;
 #pragma unroll
-        for (int j = 0; j < S; j++) {
+        for (int j = 0; j < NST; j++) {
           double Lj;
           if constexpr (LPT == 1) Lj = L[j][l];
           else Lj = __shfl_sync(stepmask, L[j % SPL][l], gbase + j / SPL);
@@ -295,7 +304,7 @@ __global__ void __launch_bounds__(BLOCK)
 #pragma unroll
             for (int t = 0; t < SPL; t++) acc[t] = 0.0;
 #pragma unroll
-            for (int j = 0; j < S; j++) {
+            for (int j = 0; j < NST; j++) {
               double Lj;
               if constexpr (LPT == 1) Lj = L[j][l];
               else Lj = __shfl_sync(sweepmask, L[j % SPL][l], gbase + j / SPL);
@@ -362,7 +371,14 @@ __global__ void __launch_bounds__(BLOCK)
           const unsigned monmask = __ballot_sync(okmask, mon);
           if (mon) {
             const double Hn = group_energy1<Rhs, LPT, NS>(rhs, yh, monmask, gbase);
-            const double dH = fabs((Hn - H0) * invH0);
+            double dH;
+            if (a.monitor_local) {
+              dH = fabs((Hn - Hprev) * invHprev);
+              Hprev = Hn;
+              invHprev = 1.0 / Hn;
+            } else {
+              dH = fabs((Hn - H0) * invH0);
+            }
             if (dH > dHmax) dHmax = dH;
           }
         }
@@ -382,7 +398,7 @@ __global__ void __launch_bounds__(BLOCK)
         }
       }
       if (a.lp_out && st == ST_OK) {
-        const size_t loff = static_cast<size_t>(traj) * S * D;
+        const size_t loff = static_cast<size_t>(traj) * NST * D;
 #pragma unroll
         for (int tt = 0; tt < SPL; tt++)
 #pragma unroll
@@ -406,13 +422,14 @@ struct KernelEntry1 {
   int dim;
   int lpt;
   int block;
+  int nst;  // stages
   const void* fn;
   void (*launch)(dim3, dim3, cudaStream_t, const KArgs1&, const Coef1&);
 };
 
-template <class Rhs, int LPT, int BLOCK>
+template <class Rhs, int LPT, int BLOCK, int NST>
 void launch1_impl(dim3 grid, dim3 block, cudaStream_t st, const KArgs1& a, const Coef1& c) {
-  irkgl1_kernel<Rhs, LPT, BLOCK><<<grid, block, 0, st>>>(a, c);
+  irkgl1_kernel<Rhs, LPT, BLOCK, NST><<<grid, block, 0, st>>>(a, c);
 }
 
 struct KernelTable1 {
@@ -424,5 +441,8 @@ KernelTable1 kernels_first_order();
 
 }  // namespace irkgl
 
-#define IRKGL_ENTRY1(KIND, DIM, RHS, LPT, BLOCK) \
-  ::irkgl::KernelEntry1 { KIND, DIM, LPT, BLOCK, (const void*)::irkgl::irkgl1_kernel<RHS, LPT, BLOCK>, ::irkgl::launch1_impl<RHS, LPT, BLOCK> }
+#define IRKGL_ENTRY1(KIND, DIM, RHS, LPT, BLOCK, NST)                                              \
+  ::irkgl::KernelEntry1 {                                                                            \
+    KIND, DIM, LPT, BLOCK, NST, (const void*)::irkgl::irkgl1_kernel<RHS, LPT, BLOCK, NST>,          \
+        ::irkgl::launch1_impl<RHS, LPT, BLOCK, NST>                                                  \
+  }

@@ -4,12 +4,23 @@
 
 namespace {
 
+// Functor template argument = stages per lane (NST / LPT).
 const ::irkgl::KernelEntry1 kEntries[] = {
-    IRKGL_ENTRY1(IRKGL_RHS_SCHWARZSCHILD, 4, ::irkgl::Schwarzschild<8>, 1, 128),
-    IRKGL_ENTRY1(IRKGL_RHS_SCHWARZSCHILD, 4, ::irkgl::Schwarzschild<4>, 2, 128),
-    IRKGL_ENTRY1(IRKGL_RHS_SCHWARZSCHILD, 4, ::irkgl::Schwarzschild<2>, 4, 128),
-    IRKGL_ENTRY1(IRKGL_RHS_HARMONIC1, 2, ::irkgl::Harmonic1<8>, 1, 128),
-    IRKGL_ENTRY1(IRKGL_RHS_HARMONIC1, 2, ::irkgl::Harmonic1<4>, 2, 128),
+    IRKGL_ENTRY1(IRKGL_RHS_SCHWARZSCHILD, 4, ::irkgl::Schwarzschild<8>, 1, 128, 8),
+    IRKGL_ENTRY1(IRKGL_RHS_SCHWARZSCHILD, 4, ::irkgl::Schwarzschild<4>, 2, 128, 8),
+    IRKGL_ENTRY1(IRKGL_RHS_SCHWARZSCHILD, 4, ::irkgl::Schwarzschild<2>, 4, 128, 8),
+    IRKGL_ENTRY1(IRKGL_RHS_HARMONIC1, 2, ::irkgl::Harmonic1<8>, 1, 128, 8),
+    IRKGL_ENTRY1(IRKGL_RHS_HARMONIC1, 2, ::irkgl::Harmonic1<4>, 2, 128, 8),
+    // s-stage IRKGL schemes, s = 2, 4, 6 (Sec. 5.2 comparison)
+    IRKGL_ENTRY1(IRKGL_RHS_SCHWARZSCHILD, 4, ::irkgl::Schwarzschild<2>, 1, 128, 2),
+    IRKGL_ENTRY1(IRKGL_RHS_SCHWARZSCHILD, 4, ::irkgl::Schwarzschild<1>, 2, 128, 2),
+    IRKGL_ENTRY1(IRKGL_RHS_SCHWARZSCHILD, 4, ::irkgl::Schwarzschild<4>, 1, 128, 4),
+    IRKGL_ENTRY1(IRKGL_RHS_SCHWARZSCHILD, 4, ::irkgl::Schwarzschild<2>, 2, 128, 4),
+    IRKGL_ENTRY1(IRKGL_RHS_SCHWARZSCHILD, 4, ::irkgl::Schwarzschild<6>, 1, 128, 6),
+    IRKGL_ENTRY1(IRKGL_RHS_SCHWARZSCHILD, 4, ::irkgl::Schwarzschild<3>, 2, 128, 6),
+    IRKGL_ENTRY1(IRKGL_RHS_HARMONIC1, 2, ::irkgl::Harmonic1<2>, 1, 128, 2),
+    IRKGL_ENTRY1(IRKGL_RHS_HARMONIC1, 2, ::irkgl::Harmonic1<4>, 1, 128, 4),
+    IRKGL_ENTRY1(IRKGL_RHS_HARMONIC1, 2, ::irkgl::Harmonic1<6>, 1, 128, 6),
 };
 }  // namespace
 

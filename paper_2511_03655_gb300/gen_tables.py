@@ -35,6 +35,7 @@ from fractions import Fraction
 from math import comb
 
 S = 8
+SMALL_S = (2, 4, 6)
 PREC = 90
 HERE = os.path.dirname(os.path.abspath(__file__))
 HEADER = os.path.join(HERE, "csrc", "irkgl_tables.h")
@@ -57,15 +58,15 @@ def _horner(co, x):
     return p, dp
 
 
-def gauss_nodes():
-    co = _legendre_coeffs(S)
+def gauss_nodes(s: int = S):
+    co = _legendre_coeffs(s)
     xs = []
     with localcontext() as ctx:
         ctx.prec = PREC
-        for i in range(S):
+        for i in range(s):
             # Chebyshev-Gauss points as starting values (distinct, interlaced)
             import math
-            x = Decimal(repr(-math.cos(math.pi * (i + 0.5) / S)))
+            x = Decimal(repr(-math.cos(math.pi * (i + 0.5) / s)))
             for _ in range(100):
                 p, dp = _horner(co, x)
                 step = p / dp
@@ -106,10 +107,11 @@ def _basis_integrals(c, lo, hi):
     return out
 
 
-def tables():
+def tables(S: int = S):
+    """FP64 tables of the S-stage method (S = 8: IRKGL16)."""
     with localcontext() as ctx:
         ctx.prec = PREC
-        c = gauss_nodes()
+        c = gauss_nodes(S)
         zeros = [Decimal(0)] * S
         ones = [Decimal(1)] * S
         b = _basis_integrals(c, zeros, ones)[0]
@@ -196,6 +198,9 @@ def render(t) -> str:
     def arr1(name, v):
         return f"static const double {name}[8] = {{\n  " + ",\n  ".join(float.hex(x) for x in v) + "};\n"
 
+    def arrn(name, v):
+        return f"static const double {name}[{len(v)}] = {{\n  " + ",\n  ".join(float.hex(x) for x in v) + "};\n"
+
     def arr2(name, m):
         rows = ",\n  ".join(", ".join(float.hex(x) for x in row) for row in m)
         return f"static const double {name}[64] = {{\n  {rows}}};\n"
@@ -211,6 +216,14 @@ def render(t) -> str:
     out.append(arr2("IRKGL_TAB_ETA", t["eta"]))
     out.append(arr2("IRKGL_TAB_NU", t["nu"]))
     out.append(arr2("IRKGL_TAB_W", t["W"]))
+    out.append("// s-stage variants (s = 2, 4, 6) for the first-order form: c, b [s]; MU, NU")
+    out.append("// [s*s], row-major [i*s+j], built by the same route as the 8-stage tables.")
+    for ns in SMALL_S:
+        ts = tables(ns)
+        out.append(arrn(f"IRKGL_TAB{ns}_C", ts["c"]))
+        out.append(arrn(f"IRKGL_TAB{ns}_B", ts["b"]))
+        out.append(arrn(f"IRKGL_TAB{ns}_MU", [x for row in ts["mu"] for x in row]))
+        out.append(arrn(f"IRKGL_TAB{ns}_NU", [x for row in ts["nu"] for x in row]))
     return "\n".join(out) + _render_int(t)
 
 

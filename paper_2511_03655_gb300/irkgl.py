@@ -27,6 +27,7 @@ RHS_SCHWARZSCHILD, RHS_HARMONIC1 = 7, 8  # first-order kinds (dim = D): the irkg
 OPT_LANES_PER_TRAJ, OPT_KMAX, OPT_MONITOR_EVERY, OPT_BLOCK_THREADS, OPT_GRID_BLOCKS = 1, 2, 3, 4, 5
 OPT_WIDE_TEAM = 6
 OPT_MONITOR_LOCAL = 7
+OPT_STAGES = 9
 OPT_MIX = 8
 
 EXPORTS = ("irkgl_default_coeffs", "irkgl_create", "irkgl_set_option", "irkgl_step",
@@ -392,18 +393,18 @@ class Outputs1:
     status: torch.Tensor | None = None
 
     @staticmethod
-    def allocate(batch: int, D: int, device="cuda"):
+    def allocate(batch: int, D: int, device="cuda", stages: int = 8):
         f = dict(dtype=torch.float64, device=device)
         return Outputs1(y=torch.empty((batch, D), **f), y_lo=torch.empty((batch, D), **f),
-                        l_prev=torch.empty((batch, 8, D), **f), dH_max=torch.empty(batch, **f),
+                        l_prev=torch.empty((batch, stages, D), **f), dH_max=torch.empty(batch, **f),
                         iters=torch.empty(batch, dtype=torch.int64, device=device),
                         steps=torch.empty(batch, dtype=torch.int64, device=device),
                         status=torch.empty(batch, dtype=torch.int32, device=device))
 
-    def _struct(self, batch, D):
+    def _struct(self, batch, D, stages=8):
         f64, i64, i32 = torch.float64, torch.int64, torch.int32
         return irkgl_outputs1(_ptr(self.y, f64, (batch, D), "out.y"), _ptr(self.y_lo, f64, (batch, D), "out.y_lo"),
-                              _ptr(self.l_prev, f64, (batch, 8, D), "out.l_prev"),
+                              _ptr(self.l_prev, f64, (batch, stages, D), "out.l_prev"),
                               _ptr(self.dH_max, f64, (batch,), "out.dH_max"),
                               _ptr(self.iters, i64, (batch,), "out.iters"),
                               _ptr(self.steps, i64, (batch,), "out.steps"),
@@ -411,10 +412,11 @@ class Outputs1:
 
 
 def irkgl_integrate1(ctx: int, D: int, y0, out: Outputs1, nsteps=None, nsteps_all: int = 0, h=None,
-                     order=None, stream=None):
-    """First-order kinds: y0 [B, D] device; nsteps int64 [B] (or nsteps_all); h [B]; order int32 [B]."""
+                     order=None, stream=None, stages: int = 8):
+    """First-order kinds: y0 [B, D] device; nsteps int64 [B] (or nsteps_all); h [B]; order int32 [B].
+    `stages` is the context's IRKGL_OPT_STAGES (out.l_prev is [B, stages, D])."""
     B = y0.shape[0]
-    st = out._struct(B, D)
+    st = out._struct(B, D, stages)
     _check(load().irkgl_integrate1(
         _P(ctx), _ptr(y0, torch.float64, (B, D), "y0"), B, _ptr(nsteps, torch.int64, (B,), "nsteps"),
         int(nsteps_all), _ptr(h, torch.float64, (B,), "h"), _ptr(order, torch.int32, (B,), "order"),
@@ -422,13 +424,13 @@ def irkgl_integrate1(ctx: int, D: int, y0, out: Outputs1, nsteps=None, nsteps_al
 
 
 def irkgl_advance1(ctx: int, D: int, y, y_lo, l_prev, nsteps, h=None, H0=None, h0_init: bool = False,
-                   dH_max=None, iters=None, status=None, stream=None):
-    """Continue first-order trajectories in place (y, y_lo [B, D], l_prev [B, 8, D])."""
+                   dH_max=None, iters=None, status=None, stream=None, stages: int = 8):
+    """Continue first-order trajectories in place (y, y_lo [B, D], l_prev [B, stages, D])."""
     B = y.shape[0]
     f64 = torch.float64
     _check(load().irkgl_advance1(
         _P(ctx), _ptr(y, f64, (B, D), "y"), _ptr(y_lo, f64, (B, D), "y_lo"),
-        _ptr(l_prev, f64, (B, 8, D), "l_prev"), _ptr(h, f64, (B,), "h"),
+        _ptr(l_prev, f64, (B, stages, D), "l_prev"), _ptr(h, f64, (B,), "h"),
         _ptr(nsteps, torch.int64, (B,), "nsteps"), _ptr(H0, f64, (B,), "H0"), int(bool(h0_init)),
         _ptr(dH_max, f64, (B,), "dH_max"), _ptr(iters, torch.int64, (B,), "iters"),
         _ptr(status, torch.int32, (B,), "status"), B, _stream(stream)))
@@ -488,9 +490,11 @@ class Integrator:
 
     def __init__(self, kind: int, params, dim: int, h: float, coeffs: dict | None = None,
                  lanes_per_traj: int = 0, kmax: int = 100, monitor_every: int = 1,
-                 block_threads: int = 128, mix: int = 0):
+                 block_threads: int = 128, mix: int = 0, stages: int = 8):
         self.dim = dim
+        self.stages = stages
         self.ctx = irkgl_create(kind, params, dim, h, coeffs)
+        self.set(OPT_STAGES, stages)
         self.set(OPT_MIX, mix)
         self.set(OPT_LANES_PER_TRAJ, lanes_per_traj)
         self.set(OPT_KMAX, kmax)
@@ -519,12 +523,12 @@ class Integrator:
         return out
 
     def integrate1(self, y0, out=None, **kw) -> Outputs1:
-        out = out or Outputs1.allocate(y0.shape[0], self.dim, device=y0.device)
-        irkgl_integrate1(self.ctx, self.dim, y0, out, **kw)
+        out = out or Outputs1.allocate(y0.shape[0], self.dim, device=y0.device, stages=self.stages)
+        irkgl_integrate1(self.ctx, self.dim, y0, out, stages=self.stages, **kw)
         return out
 
     def advance1(self, *args, **kw):
-        return irkgl_advance1(self.ctx, self.dim, *args, **kw)
+        return irkgl_advance1(self.ctx, self.dim, *args, stages=self.stages, **kw)
 
     def integrate_host(self, q0, v0, out=None, **kw) -> Outputs:
         out = out or Outputs.allocate(q0.shape[0], self.dim, device="cpu")

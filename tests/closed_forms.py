@@ -100,6 +100,13 @@ def pade_88_harmonic(omega, h):
     z = h A with A = [[0, 1], [-omega^2, 0]] (q' = v, v' = -omega^2 q).
     This is the stability function of the 8-stage Gauss method, so one
     converged IRKGL16 step maps (q, v) to R(hA) (q, v)."""
+    return pade_harmonic(8, omega, h)
+
+
+def pade_harmonic(s, omega, h):
+    """The [s/s] diagonal Pade approximant of exp(z) at z = h A (as above),
+    P(z) = sum_k (2s-k)! s! / ((2s)! k! (s-k)!) z^k: the stability function
+    of the s-stage Gauss method."""
     with localcontext() as ctx:
         ctx.prec = PREC + 10
         w = Decimal(omega)
@@ -110,12 +117,12 @@ def pade_88_harmonic(omega, h):
             return [[X[0][0] * Y[0][0] + X[0][1] * Y[1][0], X[0][0] * Y[0][1] + X[0][1] * Y[1][1]],
                     [X[1][0] * Y[0][0] + X[1][1] * Y[1][0], X[1][0] * Y[0][1] + X[1][1] * Y[1][1]]]
 
-        coef = [Decimal(factorial(16 - k) * factorial(8)) /
-                Decimal(factorial(16) * factorial(k) * factorial(8 - k)) for k in range(9)]
+        coef = [Decimal(factorial(2 * s - k) * factorial(s)) /
+                Decimal(factorial(2 * s) * factorial(k) * factorial(s - k)) for k in range(s + 1)]
         P = [[Decimal(0)] * 2 for _ in range(2)]
         Pm = [[Decimal(0)] * 2 for _ in range(2)]
         Zk = [[Decimal(1), Decimal(0)], [Decimal(0), Decimal(1)]]
-        for k in range(9):
+        for k in range(s + 1):
             sgn = 1 if k % 2 == 0 else -1
             for r in range(2):
                 for cc in range(2):
