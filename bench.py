@@ -402,7 +402,7 @@ def stage_sweep(torch, irkgl, workloads, par, stream, dev, B=16384, T=2000.0):
     Fig. ODE1_IRKGL)."""
     y0 = torch.tensor(workloads.schwarzschild_ensemble(B, seed_id=40), device=dev)
     ladders = {2: (0.125, 0.25, 0.5, 1.0), 4: (0.5, 1.0, 2.0, 4.0),
-               6: (1.0, 2.0, 4.0, 8.0), 8: (2.0, 4.0, 8.0, 16.0)}
+               6: (2.0, 4.0, 8.0, 12.0, 16.0), 8: (4.0, 8.0, 16.0, 24.0, 32.0)}
     pts = []
     for s, hs in ladders.items():
         for h in hs:

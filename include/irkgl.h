@@ -258,6 +258,24 @@ int irkgl_advance1(struct irkgl_ctx* ctx, double* y, double* y_lo, double* l_pre
                    const long long* nsteps, double* H0, int h0_init, double* dH_max,
                    long long* iters, int* status, int batch, void* cuda_stream);
 
+/* Explicit symplectic splitting baselines (Sec. 4, not IRKGL): the drift
+ * q += (a_j h) v and kick v += (b_j h) g(q) flows of Eq. flowAB in the
+ * sequence of Eq. high_order_splitting, with compensated (TwoSum + Fast2Sum)
+ * q and v pairs, one thread per trajectory.  For the GPU form of the
+ * paper's time-per-g-evaluation comparison (Table tab:overhead).
+ *   scheme  IRKGL_SPLIT_STRANG (Eq. Strang, 1 g evaluation per step) or
+ *           IRKGL_SPLIT_SUZ90 (Suzuki's fourth-order composition of five Strang
+ *           steps, 5 evaluations per step)
+ * Compiled for Kepler and Henon-Heiles (dim 2) and the 6-body problem (dim 18);
+ * other contexts return IRKGL_ERR_UNSUPPORTED, first-order ones
+ * IRKGL_ERR_INVALID.  Arguments as in irkgl_integrate; out->iters receives
+ * the number of g evaluations, out->r_prev is not written; out->dH_max
+ * follows the context's monitor options (IRKGL_OPT_MONITOR_LOCAL: Eq. DHlocmax). */
+enum { IRKGL_SPLIT_STRANG = 1, IRKGL_SPLIT_SUZ90 = 2 };
+int irkgl_split_integrate(struct irkgl_ctx* ctx, int scheme, const double* q0, const double* v0,
+                          int batch, const long long* nsteps, long long nsteps_all, const double* h,
+                          const irkgl_outputs* out, void* cuda_stream);
+
 /* Integrate `batch` independent initial states (device arrays q0, v0
  * [batch][dim], R_prev = 0, lo = 0) in one persistent launch.
  *   nsteps  [batch] steps per trajectory (device), or NULL to use nsteps_all

@@ -74,6 +74,12 @@ def lib():
                 P(ctypes.c_longlong), P(ctypes.c_double), P(ctypes.c_int), P(ctypes.c_longlong)]
             L.orc_hamiltonian1.restype = ctypes.c_double
             L.orc_hamiltonian1.argtypes = [ctypes.c_int, P(ctypes.c_double), P(ctypes.c_double)]
+            L.orc_split.restype = ctypes.c_int
+            L.orc_split.argtypes = [
+                P(ctypes.c_double), P(ctypes.c_double), ctypes.c_int, ctypes.c_int, P(ctypes.c_double),
+                ctypes.c_int, ctypes.c_int, ctypes.c_int, P(ctypes.c_double), P(ctypes.c_double),
+                P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_longlong),
+                ctypes.c_int, P(ctypes.c_double), P(ctypes.c_int), P(ctypes.c_longlong)]
             L.orc_hamiltonian.restype = ctypes.c_double
             L.orc_hamiltonian.argtypes = [ctypes.c_int, P(ctypes.c_double), ctypes.c_int,
                                           P(ctypes.c_double), P(ctypes.c_double)]
@@ -205,3 +211,35 @@ def hamiltonian1(kind: int, params, y) -> float:
     params = np.ascontiguousarray(np.asarray(params, dtype=np.float64))
     y = np.ascontiguousarray(np.asarray(y, dtype=np.float64))
     return lib().orc_hamiltonian1(kind, _ptr(params, ctypes.c_double), _ptr(y, ctypes.c_double))
+
+
+def run_split(scheme: str, kind: int, params, q, v, h, nsteps, *, q_lo=None, v_lo=None, local=False):
+    """Explicit splitting baseline (oracle/splitting.py) in C: scheme
+    "strang" or "suz90", second-order kinds.  Returns q, v, q_lo, v_lo,
+    dH_max, status, steps."""
+    from . import splitting
+    a, b = splitting.coefficients(scheme)
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    q = np.array(q, dtype=np.float64, order="C", copy=True)
+    v = np.array(v, dtype=np.float64, order="C", copy=True)
+    if q.ndim == 1:
+        q, v = q[None, :], v[None, :]
+    batch, d = q.shape
+    q_lo = np.zeros_like(q) if q_lo is None else np.array(q_lo, dtype=np.float64, order="C", copy=True).reshape(batch, d)
+    v_lo = np.zeros_like(q) if v_lo is None else np.array(v_lo, dtype=np.float64, order="C", copy=True).reshape(batch, d)
+    params = np.ascontiguousarray(np.asarray(params, dtype=np.float64))
+    pstride = params.shape[-1] if params.ndim == 2 else 0
+    hh = np.ascontiguousarray(np.broadcast_to(np.asarray(h, dtype=np.float64), (batch,)))
+    ns = np.ascontiguousarray(np.broadcast_to(np.asarray(nsteps, dtype=np.int64), (batch,)))
+    dH = np.zeros(batch)
+    st = np.zeros(batch, dtype=np.int32)
+    steps = np.zeros(batch, dtype=np.int64)
+    rc = lib().orc_split(_ptr(a, ctypes.c_double), _ptr(b, ctypes.c_double), len(b), kind,
+                         _ptr(params, ctypes.c_double), pstride, d, batch, _ptr(q, ctypes.c_double),
+                         _ptr(v, ctypes.c_double), _ptr(q_lo, ctypes.c_double), _ptr(v_lo, ctypes.c_double),
+                         _ptr(hh, ctypes.c_double), _ptr(ns, ctypes.c_longlong), int(bool(local)),
+                         _ptr(dH, ctypes.c_double), _ptr(st, ctypes.c_int), _ptr(steps, ctypes.c_longlong))
+    if rc != 0:
+        raise MemoryError("oracle allocation failed")
+    return {"q": q, "v": v, "q_lo": q_lo, "v_lo": v_lo, "dH_max": dH, "status": st, "steps": steps}

@@ -592,3 +592,54 @@ int orc_run1(const orc_tab* tab, int ns, int kind, const double* params, int pst
 double orc_hamiltonian1(int kind, const double* params, const double* y) {
   return rhs_H1(kind, params, y);
 }
+
+/* ======================================================================
+ * Explicit splitting baselines (Sec. 4, Eqs. flowAB, high_order_splitting):
+ * the same operation sequence as oracle/splitting.py.  a[0..s], b[0..s-1].
+ * ====================================================================== */
+int orc_split(const double* a, const double* b, int s, int kind, const double* params, int pstride,
+              int d, int batch, double* q, double* v, double* q_lo, double* v_lo, const double* h,
+              const long long* nsteps, int local, double* dH_max, int* status,
+              long long* steps_done) {
+  double* G = (double*)malloc(sizeof(double) * (size_t)d);
+  if (!G) return -1;
+  for (int t = 0; t < batch; t++) {
+    const double* p = params + (size_t)t * pstride;
+    double* qq = q + (size_t)t * d;
+    double* vv = v + (size_t)t * d;
+    double* ql = q_lo + (size_t)t * d;
+    double* vl = v_lo + (size_t)t * d;
+    double H0 = rhs_H(kind, p, d, qq, vv), Hp = H0, dmax = 0.0;
+    long long n = 0;
+    int st = ORC_OK;
+    for (n = 0; n < nsteps[t]; n++) {
+      const double hh = h[t];
+      for (int j = 0; j < s; j++) {
+        const double ah = a[j] * hh;
+        for (int l = 0; l < d; l++) two_sum_add(&qq[l], &ql[l], ah * vv[l]);
+        rhs_g(kind, p, d, qq, G, 0.0);
+        const double bh = b[j] * hh;
+        for (int l = 0; l < d; l++) two_sum_add(&vv[l], &vl[l], bh * G[l]);
+      }
+      const double ah = a[s] * hh;
+      for (int l = 0; l < d; l++) two_sum_add(&qq[l], &ql[l], ah * vv[l]);
+      int finite = 1;
+      for (int l = 0; l < d; l++)
+        if (!isfinite(qq[l]) || !isfinite(vv[l])) finite = 0;
+      if (!finite) {
+        st = ORC_NONFINITE;
+        break;
+      }
+      const double Hn = rhs_H(kind, p, d, qq, vv);
+      const double ref = local ? Hp : H0;
+      const double dH = fabs((Hn - ref) / ref);
+      if (dH > dmax) dmax = dH;
+      Hp = Hn;
+    }
+    if (dH_max) dH_max[t] = dmax;
+    if (status) status[t] = st;
+    if (steps_done) steps_done[t] = n;
+  }
+  free(G);
+  return 0;
+}

@@ -16,6 +16,7 @@
 #include "irkgl.h"
 #include "irkgl_first_order.cuh"
 #include "irkgl_kernels.h"
+#include "irkgl_split.cuh"
 #include "irkgl_wide.cuh"
 #include "irkgl_tables.h"
 
@@ -585,6 +586,55 @@ int irkgl_advance1(irkgl_ctx* c, double* y, double* y_lo, double* l_prev, const 
   const int rc = run1(c, a, static_cast<cudaStream_t>(stream));
   c->monitor = saved_monitor;
   return rc;
+}
+
+int irkgl_split_integrate(irkgl_ctx* c, int scheme, const double* q0, const double* v0, int batch,
+                          const long long* nsteps, long long nsteps_all, const double* h,
+                          const irkgl_outputs* out, void* stream) {
+  if (!c || batch < 0 || !out) return IRKGL_ERR_INVALID;
+  if (first_order_kind(c->kind)) return IRKGL_ERR_INVALID;
+  if (scheme != IRKGL_SPLIT_STRANG && scheme != IRKGL_SPLIT_SUZ90) return IRKGL_ERR_INVALID;
+  if (batch == 0) return IRKGL_OK;
+  if (!q0 || !v0 || !out->q || !out->v) return IRKGL_ERR_INVALID;
+  if (!nsteps && nsteps_all < 0) return IRKGL_ERR_INVALID;
+  const int nk = scheme == IRKGL_SPLIT_STRANG ? 1 : 5;
+  const irkgl::SplitTable tab = irkgl::kernels_split();
+  const irkgl::SplitEntry* se = nullptr;
+  for (int i = 0; i < tab.count && !se; i++)
+    if (tab.entries[i].kind == c->kind && tab.entries[i].dim == c->dim && tab.entries[i].nk == nk)
+      se = &tab.entries[i];
+  if (!se) return IRKGL_ERR_UNSUPPORTED;
+  irkgl::SplitCoef sc;
+  std::memset(&sc, 0, sizeof(sc));
+  const double* A = nk == 1 ? IRKGL_SPLIT_STRANG_A : IRKGL_SPLIT_SUZ90_A;
+  const double* B = nk == 1 ? IRKGL_SPLIT_STRANG_B : IRKGL_SPLIT_SUZ90_B;
+  for (int j = 0; j <= nk; j++) sc.a[j] = A[j];
+  for (int j = 0; j < nk; j++) sc.b[j] = B[j];
+  KArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.batch = batch;
+  a.monitor = time_dependent_kind(c->kind) ? 0 : c->monitor;
+  a.monitor_local = c->monitor_local;
+  a.q_in = q0;
+  a.v_in = v0;
+  a.q_out = out->q;
+  a.v_out = out->v;
+  a.qlo_out = out->q_lo;
+  a.vlo_out = out->v_lo;
+  a.nsteps = nsteps;
+  a.nsteps_all = nsteps_all;
+  a.h = h;
+  a.h_all = c->h;
+  a.iters_total = out->iters;
+  a.dH_max = out->dH_max;
+  a.status = out->status;
+  a.steps_done = out->steps;
+  a.params = c->d_params;
+  const long long threads = static_cast<long long>(batch) * se->lanes;
+  const int grid = static_cast<int>((threads + 127) / 128);
+  se->launch(dim3(grid), dim3(128), static_cast<cudaStream_t>(stream), a, sc);
+  IRKGL_CUDA(cudaGetLastError());
+  return IRKGL_OK;
 }
 
 int irkgl_integrate(irkgl_ctx* c, const double* q0, const double* v0, int batch,

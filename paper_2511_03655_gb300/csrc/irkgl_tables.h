@@ -226,6 +226,30 @@ static const double IRKGL_TAB6_NU[36] = {
   -0x1.677fee84612cap+10,
   0x1.2954c75d3fd8bp+10};
 
+// Explicit splitting baselines (Sec. 4, Eq. high_order_splitting): drift weights a[s+1],
+// kick weights b[s]; Strang (s = 1) and Suzuki's fourth-order composition (s = 5).
+static const double IRKGL_SPLIT_STRANG_A[2] = {
+  0x1.0000000000000p-1,
+  0x1.0000000000000p-1};
+
+static const double IRKGL_SPLIT_STRANG_B[1] = {
+  0x1.0000000000000p+0};
+
+static const double IRKGL_SPLIT_SUZ90_A[6] = {
+  0x1.a87044d5670efp-3,
+  0x1.a87044d5670efp-2,
+  -0x1.f2a19d006a59dp-4,
+  -0x1.f2a19d006a59dp-4,
+  0x1.a87044d5670efp-2,
+  0x1.a87044d5670efp-3};
+
+static const double IRKGL_SPLIT_SUZ90_B[5] = {
+  0x1.a87044d5670efp-2,
+  0x1.a87044d5670efp-2,
+  -0x1.50e089aace1dfp-1,
+  0x1.a87044d5670efp-2,
+  0x1.a87044d5670efp-2};
+
 // Integer forms for the fixed-point mixing (see gen_tables.int_tables):
 // |ETA_ij| * 2^63 (exact), round(|W_ij| * 2^50); signs; per-row
 // corrections sum_j (+-m_ij) 2^61 as 128-bit two's complement words.

@@ -138,6 +138,22 @@ def tables(S: int = S):
     return {"c": cf, "b": bf, "mu": mu, "eta": eta, "nu": nu, "W": Wf}
 
 
+def split_tables():
+    """Drift/kick weights of symmetric compositions of Strang steps with
+    weights gamma (a_1 = gamma_1/2, a_j = (gamma_{j-1} + gamma_j)/2,
+    a_{s+1} = gamma_s/2, b_j = gamma_j).  Suzuki's fourth-order weights:
+    p = 1/(4 - 4^(1/3)) four times around 1 - 4p."""
+    out = {}
+    with localcontext() as ctx:
+        ctx.prec = PREC
+        cube_root_4 = Decimal(4) ** (Decimal(1) / Decimal(3))
+        p = Decimal(1) / (Decimal(4) - cube_root_4)
+        for name, g in (("STRANG", [Decimal(1)]), ("SUZ90", [p, p, 1 - 4 * p, p, p])):
+            a = [g[0] / 2] + [(g[j - 1] + g[j]) / 2 for j in range(1, len(g))] + [g[-1] / 2]
+            out[name] = ([float(x) for x in a], [float(x) for x in g])
+    return out
+
+
 ETA_SHIFT = 63   # eta_ij = +-n_ij * 2^-63, n_ij exact (|eta| in [2^-11, 1))
 W_SHIFT = 50     # W_ij ~ +-w_ij * 2^-50, w_ij = round(|W_ij| 2^50) (only seeds the guess)
 R_BIAS = 61      # fixed-point R values are offset by 2^61 to make them non-negative
@@ -224,6 +240,11 @@ def render(t) -> str:
         out.append(arrn(f"IRKGL_TAB{ns}_B", ts["b"]))
         out.append(arrn(f"IRKGL_TAB{ns}_MU", [x for row in ts["mu"] for x in row]))
         out.append(arrn(f"IRKGL_TAB{ns}_NU", [x for row in ts["nu"] for x in row]))
+    out.append("// Explicit splitting baselines (Sec. 4, Eq. high_order_splitting): drift weights a[s+1],")
+    out.append("// kick weights b[s]; Strang (s = 1) and Suzuki's fourth-order composition (s = 5).")
+    for name, (a, b) in split_tables().items():
+        out.append(arrn(f"IRKGL_SPLIT_{name}_A", a))
+        out.append(arrn(f"IRKGL_SPLIT_{name}_B", b))
     return "\n".join(out) + _render_int(t)
 
 

@@ -28,6 +28,7 @@ OPT_LANES_PER_TRAJ, OPT_KMAX, OPT_MONITOR_EVERY, OPT_BLOCK_THREADS, OPT_GRID_BLO
 OPT_WIDE_TEAM = 6
 OPT_MONITOR_LOCAL = 7
 OPT_STAGES = 9
+SPLIT_STRANG, SPLIT_SUZ90 = 1, 2
 OPT_MIX = 8
 
 EXPORTS = ("irkgl_default_coeffs", "irkgl_create", "irkgl_set_option", "irkgl_step",
@@ -95,6 +96,8 @@ def load(path: str | None = None, build_if_missing: bool = False):
     L.irkgl_integrate.argtypes = [_P, _P, _P, ctypes.c_int, _P, ctypes.c_longlong, _P, _P,
                                   ctypes.POINTER(irkgl_outputs), _P]
     L.irkgl_integrate_host.argtypes = L.irkgl_integrate.argtypes
+    L.irkgl_split_integrate.argtypes = [_P, ctypes.c_int, _P, _P, ctypes.c_int, _P, ctypes.c_longlong, _P,
+                                        ctypes.POINTER(irkgl_outputs), _P]
     L.irkgl_integrate1.argtypes = [_P, _P, ctypes.c_int, _P, ctypes.c_longlong, _P, _P,
                                    ctypes.POINTER(irkgl_outputs1), _P]
     L.irkgl_advance1.argtypes = [_P, _P, _P, _P, _P, _P, _P, ctypes.c_int, _P, _P, _P, ctypes.c_int, _P]
@@ -322,6 +325,19 @@ def irkgl_integrate(ctx: int, dim: int, q0, v0, out: Outputs, nsteps=None, nstep
         _ptr(order, torch.int32, (B,), "order"), ctypes.byref(st), _stream(stream)))
 
 
+def irkgl_split_integrate(ctx: int, dim: int, scheme: int, q0, v0, out: Outputs, nsteps=None,
+                          nsteps_all: int = 0, h=None, stream=None):
+    """Explicit splitting baseline (SPLIT_STRANG / SPLIT_SUZ90) on the context's
+    right-hand side; device tensors as in irkgl_integrate; out.iters = g evaluations."""
+    B = q0.shape[0]
+    f64 = torch.float64
+    st = out._struct(B, dim)
+    _check(load().irkgl_split_integrate(
+        _P(ctx), int(scheme), _ptr(q0, f64, (B, dim), "q0"), _ptr(v0, f64, (B, dim), "v0"), B,
+        _ptr(nsteps, torch.int64, (B,), "nsteps"), int(nsteps_all), _ptr(h, f64, (B,), "h"),
+        ctypes.byref(st), _stream(stream)))
+
+
 def irkgl_integrate_host(ctx: int, dim: int, q0, v0, out: Outputs, nsteps=None,
                          nsteps_all: int = 0, h=None, order=None, stream=None):
     """Host (CPU, ideally pinned) tensors; synchronous; copies inside the call."""
@@ -529,6 +545,11 @@ class Integrator:
 
     def advance1(self, *args, **kw):
         return irkgl_advance1(self.ctx, self.dim, *args, stages=self.stages, **kw)
+
+    def split_integrate(self, scheme, q0, v0, out=None, **kw) -> Outputs:
+        out = out or Outputs.allocate(q0.shape[0], self.dim, device=q0.device)
+        irkgl_split_integrate(self.ctx, self.dim, scheme, q0, v0, out, **kw)
+        return out
 
     def integrate_host(self, q0, v0, out=None, **kw) -> Outputs:
         out = out or Outputs.allocate(q0.shape[0], self.dim, device="cpu")
