@@ -64,11 +64,14 @@ def parse():
     ap.add_argument("--lanes", type=int, default=0, help="lanes per trajectory (0 = library default)")
     ap.add_argument("--no-order", action="store_true", help="natural order instead of similarity order")
     ap.add_argument("--skip-extras", action="store_true", help="skip e2e, plain form and CPU baseline")
-    ap.add_argument("--workload", default="kepler", choices=["kepler", "nbody6", "uneven", "schwarzschild"],
+    ap.add_argument("--workload", default="kepler",
+                    choices=["kepler", "nbody6", "uneven", "schwarzschild", "overhead"],
                     help="kepler: the 65,536-orbit ensemble (default); nbody6: 16,384 perturbed "
                          "copies of a 6-body system; uneven: 4,096 ragged instances (N-body "
                          "N~U{3..64} and FPUT n~U{8..512}), autotuned vs fixed tiling; schwarzschild: "
-                         "65,536 first-order black-hole orbits (Eq. Ham_SBH), t in [0, 1e5], h = 16")
+                         "65,536 first-order black-hole orbits (Eq. Ham_SBH), t in [0, 1e5], h = 16; "
+                         "overhead: GPU time per g-evaluation of IRKGL16 over that of the explicit "
+                         "splitting methods (Henon-Heiles and 6-body ensembles)")
     ap.add_argument("--traj-steps", type=int, default=None,
                     help="steps per trajectory/instance (nbody6: 10000, uneven: 1000 by default)")
     ap.add_argument("--ninst", type=int, default=4096, help="instances for the uneven workload")
@@ -547,13 +550,111 @@ def run_first_order(args):
                                     "kind": "oracle",
                                     "sample": f"{nsel} orbits evenly spaced in r0, full horizon ({nsteps} "
                                               f"steps), {dt:.1f} s wall on {cores} threads"}
-        if args.stage_sweep:
-            line["stage_sweep"] = stage_sweep(torch, irkgl, workloads, par, stream, dev)
+    if args.stage_sweep:
+        line["stage_sweep"] = stage_sweep(torch, irkgl, workloads, par, stream, dev)
     if rank == 0:
         print(json.dumps(line))
     integ.close()
     if world > 1:
         dist.destroy_process_group()
+    return 0
+
+
+# --------------------------------------------------------------------------
+# time per g-evaluation, IRKGL16 vs explicit splitting (Table tab:overhead)
+# --------------------------------------------------------------------------
+def run_overhead(args):
+    """For each second-order problem, IRKGL16 at its reference step (the
+    largest step of a ladder whose local energy error, Eq. DHlocmax, stays
+    <= 1e-14 on a pilot run; the paper's reference for Table tab:overhead)
+    and the Strang / SUZ90 splitting schemes at steps of similar cost, all
+    on the same ensemble: GPU time / g-evaluations, and IRKGL16's value
+    normalized by the splitting methods' (the GPU form of the CPU-FCN
+    ratio)."""
+    import torch
+
+    from paper_2511_03655_gb300 import build, irkgl, workloads
+    torch.cuda.set_device(0)
+    build.build()
+    irkgl.load()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) * 1e-3 / reps
+
+    problems = []
+    q, v, _ = workloads.henon_heiles_ensemble(65536)
+    problems.append(("henon_heiles", irkgl.RHS_HENON_HEILES, [1.0], 2, q, v, 1.0,
+                     (0.1, 0.15, 0.2, 0.3, 0.4, 0.5, 0.7), 2000))
+    e = workloads.nbody_ensemble(copies=16384, steps=1)
+    T0 = float(e["h"][0]) / 0.005  # innermost period
+    problems.append(("nbody6", irkgl.RHS_NBODY, e["params"], 18, e["q0"], e["v0"], T0,
+                     (0.0025, 0.005, 0.01, 0.015, 0.02, 0.03), 1000))
+    res = {}
+    for name, kind, par, d, q0h, v0h, scale, ladder, nsteps in problems:
+        q0, v0 = torch.tensor(q0h, device=dev), torch.tensor(v0h, device=dev)
+        B = q0.shape[0]
+        # reference step: pilot on 1024 trajectories with the local monitor
+        pilot = irkgl.Integrator(kind, par, d, 1.0)
+        pilot.set(irkgl.OPT_MONITOR_LOCAL, 1)
+        href, dl = None, {}
+        for f in ladder:
+            o = pilot.integrate(q0[:1024], v0[:1024], nsteps_all=200,
+                                h=torch.full((1024,), f * scale, dtype=torch.float64, device=dev))
+            torch.cuda.synchronize()
+            ok = (o.status.cpu().numpy() == 0).all()
+            dl[f] = float(o.dH_max.cpu().numpy().max()) if ok else float("inf")
+            if ok and dl[f] <= 1e-14:
+                href = f * scale
+        pilot.close()
+        href = href or ladder[0] * scale
+        ig = irkgl.Integrator(kind, par, d, href)
+        out = irkgl.Outputs.allocate(B, d, device=dev)
+        t_irk = timed(lambda: ig.integrate(q0, v0, out=out, nsteps_all=nsteps), args.steps)
+        sweeps = float(out.iters.cpu().numpy().sum())
+        irk_per_g = t_irk / (8.0 * sweeps)
+        row = {"h_ref": href, "dH_loc_pilot": dl, "irkgl16": {
+            "seconds": t_irk, "traj_steps_per_s": B * nsteps / t_irk, "sweeps_per_step": sweeps / (B * nsteps),
+            "g_evals": 8.0 * sweeps, "ns_per_g_eval": 1e9 * irk_per_g,
+            "dH_max_global": float(out.dH_max.cpu().numpy().max())}}
+        ig.close()
+        for scheme, sid, nk in (("strang", irkgl.SPLIT_STRANG, 1), ("suz90", irkgl.SPLIT_SUZ90, 5)):
+            sp = irkgl.Integrator(kind, par, d, href / 4 if nk == 1 else href / 2)
+            so = irkgl.Outputs.allocate(B, d, device=dev)
+            ns = nsteps * 4 if nk == 1 else nsteps * 2
+            t_sp = timed(lambda: sp.split_integrate(sid, q0, v0, out=so, nsteps_all=ns), args.steps)
+            g = float(so.iters.cpu().numpy().sum())
+            row[scheme] = {"h": href / 4 if nk == 1 else href / 2, "seconds": t_sp, "g_evals": g,
+                           "ns_per_g_eval": 1e9 * t_sp / g,
+                           "dH_max_global": float(so.dH_max.cpu().numpy().max())}
+            row[f"ratio_vs_{scheme}"] = irk_per_g / (t_sp / g)
+            sp.close()
+        res[name] = row
+    hh = res["henon_heiles"]["irkgl16"]
+    line = {
+        "metric": METRIC, "value": hh["traj_steps_per_s"], "unit": "traj-steps/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * hh["seconds"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "henon_heiles_ensemble: 65,536 orbits at H = 1/12 (Sec. 5.1), IRKGL16 at its "
+                               "reference step (dH_loc <= 1e-14), 2000 steps; plus the 6-body ensemble "
+                               "(16,384 copies), and both against Strang / SUZ90 splitting",
+                   "l2": "states < L2; each timing averages repeated launches"},
+        "gpu_launches": args.steps,
+        "time_per_g_eval": res,
+        "note": "ratio_vs_* = IRKGL16 GPU time per g-evaluation / the splitting scheme's (the paper's "
+                "normalized CPU-FCN ratio, Table tab:overhead: 0.6 for its SIMD CPU form)",
+    }
+    print(json.dumps(line))
     return 0
 
 # --------------------------------------------------------------------------
@@ -570,6 +671,8 @@ def main():
         return run_uneven(args)
     if args.workload == "schwarzschild":
         return run_first_order(args)
+    if args.workload == "overhead":
+        return run_overhead(args)
 
     import torch
     import torch.distributed as dist
