@@ -593,13 +593,15 @@ def run_overhead(args):
         return a.elapsed_time(b) * 1e-3 / reps
 
     problems = []
-    q, v, _ = workloads.henon_heiles_ensemble(65536)
+    # ensembles large enough to fill the GPU with the one-thread-per-orbit
+    # splitting kernels too
+    q, v, _ = workloads.henon_heiles_ensemble(262144)
     problems.append(("henon_heiles", irkgl.RHS_HENON_HEILES, [1.0], 2, q, v, 1.0,
-                     (0.1, 0.15, 0.2, 0.3, 0.4, 0.5, 0.7), 2000))
-    e = workloads.nbody_ensemble(copies=16384, steps=1)
+                     (0.2, 0.3, 0.4, 0.5, 0.7, 1.0, 1.4, 2.0), 1000))
+    e = workloads.nbody_ensemble(copies=65536, steps=1)
     T0 = float(e["h"][0]) / 0.005  # innermost period
     problems.append(("nbody6", irkgl.RHS_NBODY, e["params"], 18, e["q0"], e["v0"], T0,
-                     (0.0025, 0.005, 0.01, 0.015, 0.02, 0.03), 1000))
+                     (0.005, 0.01, 0.02, 0.03, 0.05, 0.07, 0.1), 500))
     res = {}
     for name, kind, par, d, q0h, v0h, scale, ladder, nsteps in problems:
         q0, v0 = torch.tensor(q0h, device=dev), torch.tensor(v0h, device=dev)
@@ -645,9 +647,9 @@ def run_overhead(args):
         "metric": METRIC, "value": hh["traj_steps_per_s"], "unit": "traj-steps/s", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * hh["seconds"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "henon_heiles_ensemble: 65,536 orbits at H = 1/12 (Sec. 5.1), IRKGL16 at its "
-                               "reference step (dH_loc <= 1e-14), 2000 steps; plus the 6-body ensemble "
-                               "(16,384 copies), and both against Strang / SUZ90 splitting",
+        "config": {"workload": "henon_heiles_ensemble: 262,144 orbits at H = 1/12 (Sec. 5.1), IRKGL16 at its "
+                               "reference step (dH_loc <= 1e-14), 1000 steps; plus the 6-body ensemble "
+                               "(65,536 copies, 500 steps), and both against Strang / SUZ90 splitting",
                    "l2": "states < L2; each timing averages repeated launches"},
         "gpu_launches": args.steps,
         "time_per_g_eval": res,
@@ -878,7 +880,9 @@ def main():
         descs = workloads.serving_requests(n=args.serve_requests, rate=2000.0, batch_max=512,
                                            horizon_max=3000, nb_max=24, n_max=256)
         served = serve.make_requests(copy.deepcopy(descs))
-        s1 = serve.Server(nstreams=16, chunk_traj_steps=2e5).run(served).summary()
+        srv = serve.Server(nstreams=16, chunk_traj_steps=2e5)
+        s1 = srv.run(served).summary()
+        srv.close()
         plain_r = serve.make_requests(copy.deepcopy(descs))
         s2 = serve.run_plain(plain_r).summary()
         same = all(np.array_equal(a.q, b.q) for a, b in zip(served, plain_r))

@@ -361,6 +361,8 @@ def instances_tensor(w: dict, device) -> torch.Tensor:
                                 int(w["param_offset"][k]), int(w["nparams"][k]), float(w["h"][k]),
                                 int(w["nsteps"][k]))
     raw = torch.frombuffer(bytearray(bytes(arr)), dtype=torch.uint8)
+    if torch.device(device).type == "cuda":
+        return raw.pin_memory().to(device, non_blocking=True)
     return raw.to(device)
 
 

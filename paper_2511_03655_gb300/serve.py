@@ -18,6 +18,12 @@ A chunked run gives the same bits as one uninterrupted launch (the
 continuation carries the compensated state, R_prev, H_0 and the running
 maxima), so a request's result does not depend on what it was mixed with.
 
+The loop never blocks on the device except when a request finishes: inputs
+go up from pinned host buffers with asynchronous copies on the request's
+stream, and library contexts (each holds the work counter of one launch in
+flight) come from a pool and are destroyed only when the server closes,
+since freeing device memory synchronizes the device.
+
 ``run_plain`` is the comparator: the plain per-request GPU form, one request
 at a time in arrival order, each integrated by one launch.
 """
@@ -104,6 +110,7 @@ class _Active:
     ns: torch.Tensor
     inst: torch.Tensor | None = None
     params_dev: torch.Tensor | None = None
+    ckey: tuple = ()
     remaining: int = 0
     started: bool = False
     event: torch.cuda.Event | None = None
@@ -142,6 +149,20 @@ class Server:
         self.max_active = max_active
         self._next_stream = 0
         self._route_cache: dict = {}
+        self._pool: dict = {}  # (kind, params, dim, wide) -> free contexts
+
+    def _take_ctx(self, key, make):
+        free = self._pool.get(key)
+        return free.pop() if free else make()
+
+    def _give_ctx(self, key, ctx):
+        self._pool.setdefault(key, []).append(ctx)
+
+    def close(self):
+        for ctxs in self._pool.values():
+            for c in ctxs:
+                irkgl.irkgl_destroy(c)
+        self._pool = {}
 
     # ---------------------------------------------------------------- admission
     def _admit(self, req: Request, now: float) -> _Active:
@@ -154,10 +175,15 @@ class Server:
         wide = self._route_cache[key]
         B, d = req.batch, req.dim
         f64 = dict(dtype=torch.float64, device=dev)
+        def up(x):
+            # pinned staging + asynchronous copy on the request's stream
+            h = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).pin_memory()
+            return h.to(dev, non_blocking=True)
+
         with torch.cuda.stream(stream):
             a = _Active(req=req, stream=stream, ctx=0, wide=wide,
-                        q=torch.tensor(req.q0, **f64).reshape(B, d).contiguous(),
-                        v=torch.tensor(req.v0, **f64).reshape(B, d).contiguous(),
+                        q=up(req.q0).reshape(B, d),
+                        v=up(req.v0).reshape(B, d),
                         qlo=torch.zeros((B, d), **f64), vlo=torch.zeros((B, d), **f64),
                         rp=torch.zeros((B, 8, d), **f64), h=None,
                         H0=torch.zeros(B, **f64), dH=torch.zeros(B, **f64),
@@ -165,18 +191,23 @@ class Server:
                         st=torch.zeros(B, dtype=torch.int32, device=dev),
                         ns=torch.zeros(B, dtype=torch.int64, device=dev))
             hb = np.broadcast_to(np.asarray(req.h, dtype=np.float64), (B,))
-            a.h = torch.tensor(np.ascontiguousarray(hb), **f64)
+            a.h = up(hb)
             h_first = float(hb[0])
             if wide:
-                a.ctx = irkgl.irkgl_create(irkgl.RHS_HARMONIC, [1.0], 1, h_first)
+                a.ckey = ("wide",)
+                a.ctx = self._take_ctx(a.ckey, lambda: irkgl.irkgl_create(irkgl.RHS_HARMONIC, [1.0], 1, 1.0))
                 w = {"kind": np.full(B, KIND_IDS[req.kind], np.int32), "dim": np.full(B, d, np.int32),
                      "offset": np.arange(B, dtype=np.int64) * d, "param_offset": np.zeros(B, np.int32),
                      "nparams": np.full(B, len(req.params), np.int32), "h": hb,
                      "nsteps": np.zeros(B, np.int64)}
                 a.inst = irkgl.instances_tensor(w, dev)
-                a.params_dev = torch.tensor(np.asarray(req.params, dtype=np.float64), **f64)
+                a.params_dev = up(np.asarray(req.params, dtype=np.float64))
             else:
-                a.ctx = irkgl.irkgl_create(KIND_IDS[req.kind], req.params, d, h_first)
+                # the step size comes per trajectory (a.h), so contexts of the
+                # same system are interchangeable
+                a.ckey = (req.kind, tuple(float(x) for x in req.params), d)
+                a.ctx = self._take_ctx(a.ckey, lambda: irkgl.irkgl_create(KIND_IDS[req.kind], req.params, d,
+                                                                         h_first))
         a.remaining = req.nsteps
         a.nbytes = req.device_bytes()
         req.t_admit = now
@@ -211,7 +242,7 @@ class Server:
             req.dH_max = a.dH.cpu().numpy()
             req.iters = a.it.cpu().numpy()
             req.status = a.st.cpu().numpy()
-        irkgl.irkgl_destroy(a.ctx)
+        self._give_ctx(a.ckey, a.ctx)
         req.t_done = now
 
     # ---------------------------------------------------------------- the loop

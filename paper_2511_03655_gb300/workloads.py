@@ -209,7 +209,13 @@ def nbody_system(nbodies: int = 6, seed_id: int = 3, amin: float = 5.0, amax: fl
 
 
 def nbody_ensemble(copies: int = 16384, nbodies: int = 6, steps: int = 100000, seed_id: int = 3,
-                   perturb: float = 1e-8, h_fraction: float = 0.005, min_hill: float | None = 8.0):
+                   perturb: float = 1e-8, h_fraction: float = 0.005, min_hill: float | str | None = "auto"):
+    """Perturbed copies of one planetary system.  min_hill = "auto" spaces
+    systems of up to 6 bodies (the outer Solar System stand-in) >= 8 mutual
+    Hill radii apart; larger systems rarely fit that spacing in [5, 40] and
+    are drawn unspaced."""
+    if min_hill == "auto":
+        min_hill = 8.0 if nbodies <= 6 else None
     sysd = nbody_system(nbodies, seed_id, min_hill=min_hill)
     d = 3 * nbodies
     xi = 2.0 * uniform(SEED_BASE + seed_id + 500, copies * d).reshape(copies, d) - 1.0

@@ -85,3 +85,26 @@ def test_served_results_match_oracle(server_mod):
         g = np.concatenate([r.q, r.v], axis=1)
         e = np.concatenate([o["q"], o["v"]], axis=1)
         assert (np.abs(g - e).max(axis=1) / np.abs(e).max(axis=1)).max() <= 1e-11, r.kind
+
+
+def test_context_pool_reuse(server_mod):
+    """Contexts return to the pool when a request finishes and are reused:
+    the pool never holds more contexts than requests ran at once, and a
+    second run on the same server creates none."""
+    serve = server_mod
+    descs = small_requests(20)
+    srv = serve.Server(nstreams=4, chunk_traj_steps=1e3)
+    st = srv.run(serve.make_requests(copy.deepcopy(descs)))
+    pooled = sum(len(v) for v in srv._pool.values())
+    assert 1 <= pooled <= st.max_concurrent
+    before = {k: list(v) for k, v in srv._pool.items()}
+    again = serve.make_requests(copy.deepcopy(descs))
+    srv2_stats = srv.run(again)
+    after = {k: list(v) for k, v in srv._pool.items()}
+    assert sum(len(v) for v in after.values()) <= max(pooled, srv2_stats.max_concurrent)
+    assert all(set(before[k]) <= set(after.get(k, [])) for k in before)  # the same contexts came back
+    first = serve.make_requests(copy.deepcopy(descs))
+    serve.Server(nstreams=4, chunk_traj_steps=1e3).run(first)
+    for a, b in zip(first, again):
+        assert np.array_equal(a.q, b.q) and np.array_equal(a.iters, b.iters)
+    srv.close()
