@@ -47,10 +47,14 @@ FLOPS_PER_SWEEP = 424
 # pairwise g and R 3720 + mixing 2592 + Delta 144.
 FLOPS_NBODY6 = (3882, 6456)
 
-# DRAM traffic of the batched kernel from the committed ncu capture, valid only
-# for the kernel source it was taken on (sha256 prefix of irkgl_device.cuh).
-NCU_TRAFFIC_BYTES_PER_LAUNCH = None
-NCU_KERNEL_SHA = None
+# DRAM traffic of the batched kernel from the committed ncu capture
+# (profiles/traffic_irkgl_kernel_kepler_b65536.md: dram__bytes_read.sum +
+# dram__bytes_write.sum of one launch of the full 65,536-orbit batch; the
+# state is read once and kept in registers, so the traffic depends on the
+# batch, not on the horizon), valid only for the kernel source it was taken
+# on (sha256 prefix of irkgl_device.cuh) and for the FP64 mixing.
+NCU_TRAFFIC_BYTES_PER_LAUNCH = 4185600 + 70656
+NCU_KERNEL_SHA = "852ce64a9b6102fb"
 
 
 def parse():
@@ -601,7 +605,7 @@ def run_overhead(args):
     e = workloads.nbody_ensemble(copies=65536, steps=1)
     T0 = float(e["h"][0]) / 0.005  # innermost period
     problems.append(("nbody6", irkgl.RHS_NBODY, e["params"], 18, e["q0"], e["v0"], T0,
-                     (0.005, 0.01, 0.02, 0.03, 0.05, 0.07, 0.1), 500))
+                     (0.02, 0.05, 0.1, 0.15, 0.2, 0.3, 0.4), 500))
     res = {}
     for name, kind, par, d, q0h, v0h, scale, ladder, nsteps in problems:
         q0, v0 = torch.tensor(q0h, device=dev), torch.tensor(v0h, device=dev)
@@ -776,7 +780,8 @@ def main():
 
     flops_launch = fps * float(steps.sum()) + fpw * float(iters.sum())
     achieved = flops_launch / statistics.mean(times) / 1e12
-    traffic = NCU_TRAFFIC_BYTES_PER_LAUNCH if NCU_KERNEL_SHA == kernel_sha() else None
+    traffic = (NCU_TRAFFIC_BYTES_PER_LAUNCH if NCU_KERNEL_SHA == kernel_sha() and args.mix == 0
+               and args.workload == "kepler" and args.batch == 65536 else None)
 
     line = {
         "metric": METRIC, "value": value, "unit": "traj-steps/s", "n_gpus": world,
@@ -883,14 +888,21 @@ def main():
         srv = serve.Server(nstreams=16, chunk_traj_steps=2e5)
         s1 = srv.run(served).summary()
         srv.close()
+        sjf_r = serve.make_requests(copy.deepcopy(descs))
+        srv = serve.Server(nstreams=16, chunk_traj_steps=2e5, policy="sjf", max_active=32)
+        s3 = srv.run(sjf_r).summary()
+        srv.close()
         plain_r = serve.make_requests(copy.deepcopy(descs))
         s2 = serve.run_plain(plain_r).summary()
-        same = all(np.array_equal(a.q, b.q) for a, b in zip(served, plain_r))
+        same = all(np.array_equal(a.q, b.q) and np.array_equal(a.q, c.q)
+                   for a, b, c in zip(served, plain_r, sjf_r))
         line["serving"] = {
             "window": f"{args.serve_requests} Poisson requests at 2000/s from the config-1..4 families, "
                       "batch logU[1,512], horizon logU[1e2,3e3], N-body N<=24, FPUT n<=256 "
                       "(the full config-5 ranges offer ~100x the GPU's capacity)",
-            "continuous_batching": s1, "plain_per_request": s2,
+            "continuous_batching": s1, "continuous_batching_sjf": s3, "plain_per_request": s2,
+            "policies": "continuous_batching: arrival order, all requests share the GPU; "
+                        "continuous_batching_sjf: least estimated work first, at most 32 at once",
             "results_identical_to_plain": bool(same)}
 
     if rank == 0:

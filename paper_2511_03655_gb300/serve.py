@@ -139,9 +139,30 @@ class ServeStats:
                 "peak_device_bytes": self.peak_bytes, "max_concurrent_requests": self.max_concurrent}
 
 
+def estimated_flops(req: Request) -> float:
+    """Work estimate of a request (FP64 flops, about three sweeps per step):
+    the per-step and per-sweep counts of the kernel that will run it."""
+    from . import ragged
+    kind = KIND_IDS[req.kind]
+    if kind == irkgl.RHS_KEPLER:
+        per_step = 413 + 3 * 424
+    else:
+        per_step = ragged.flops_per_step(kind, req.dim) + 3 * ragged.flops_per_sweep(kind, req.dim)
+    return float(req.batch) * req.nsteps * per_step
+
+
 class Server:
+    """policy "fifo" admits waiting requests in arrival order; "sjf" admits
+    the one with the least estimated work first (shortest job first), which
+    lowers the median latency when many requests wait; max_active caps how
+    many requests share the GPU at once."""
+
     def __init__(self, mem_budget_bytes: int = 8 << 30, nstreams: int = 16,
-                 chunk_traj_steps: float = 4e5, max_active: int = 512, device=None):
+                 chunk_traj_steps: float = 4e5, max_active: int = 512, device=None,
+                 policy: str = "fifo"):
+        if policy not in ("fifo", "sjf"):
+            raise ValueError(policy)
+        self.policy = policy
         self.budget = int(mem_budget_bytes)
         self.device = device or torch.device("cuda")
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(nstreams)]
@@ -264,10 +285,13 @@ class Server:
                 i += 1
             # admit in arrival order while memory and slots allow
             while waiting and len(active) < self.max_active:
-                req = waiting[0]
+                j = 0
+                if self.policy == "sjf":
+                    j = min(range(len(waiting)), key=lambda x: estimated_flops(waiting[x]))
+                req = waiting[j]
                 if used + req.device_bytes() > self.budget and active:
                     break
-                waiting.pop(0)
+                waiting.pop(j)
                 a = self._admit(req, now)
                 used += a.nbytes
                 active.append(a)

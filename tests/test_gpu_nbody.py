@@ -78,9 +78,13 @@ def test_nbody_energy_statistics_chaotic_criterion(torch_cuda):
     r = cbind.run(cbind.NBODY, w["params"], w["q0"], w["v0"], h, 10000, nthreads=8)
     g, o = out.dH_max.cpu().numpy(), r["dH_max"]
     assert (out.status.cpu().numpy() == 0).all() and (r["status"] == 0).all()
+    # factor 2 between the ensemble statistics; at the roundoff floor (a few
+    # units of 2^-52, where this well-separated system sits) the GPU's fused
+    # operations and the oracle's separate roundings give different small
+    # multiples of the unit, so the comparison allows 2e-15 absolute there
     for stat in (np.median, lambda x: np.percentile(x, 90), np.max):
         sg, so = stat(g), stat(o)
-        assert sg <= 2 * so and so <= 2 * sg, (sg, so)
+        assert sg <= 2 * so + 2e-15 and so <= 2 * sg + 2e-15, (sg, so)
         if so <= 1e-13:
             assert sg <= 1e-13
     integ.close()

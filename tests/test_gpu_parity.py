@@ -154,15 +154,17 @@ def test_kepler_ensemble_slice(torch_cuda, lpt):
     integ.close()
 
 
-def test_kepler_ensemble_full_size_sampled(torch_cuda):
+@pytest.mark.parametrize("mix", [0, 1])
+def test_kepler_ensemble_full_size_sampled(torch_cuda, mix):
     """The full 65,536-orbit, 100-period workload in the launch configuration
-    the benchmark times; 48 sampled orbits (spread over e) re-run by the
-    oracle must agree within 1e-9 at the end; every orbit completes."""
+    the benchmark times (both stage mixings: FP64 FMA chain and fixed-point);
+    48 sampled orbits (spread over e) re-run by the oracle must agree within
+    1e-9 at the end; every orbit completes."""
     from paper_2511_03655_gb300 import irkgl
     torch = torch_cuda
     w = workloads.kepler_ensemble()
     order = workloads.similarity_order(w["e"])
-    integ = irkgl.Integrator(irkgl.RHS_KEPLER, [1.0], 2, 0.01)
+    integ = irkgl.Integrator(irkgl.RHS_KEPLER, [1.0], 2, 0.01, mix=mix)
     out = integ.integrate(dev(torch, w["q0"]), dev(torch, w["v0"]), nsteps=dev(torch, w["nsteps"]),
                           h=dev(torch, w["h"]), order=dev(torch, order))
     torch.cuda.synchronize()

@@ -108,3 +108,23 @@ def test_context_pool_reuse(server_mod):
     for a, b in zip(first, again):
         assert np.array_equal(a.q, b.q) and np.array_equal(a.iters, b.iters)
     srv.close()
+
+
+def test_sjf_policy_same_results_and_order(server_mod):
+    """Shortest-job-first admission changes only the timing: every request's
+    result is the bits of the first-in-first-out run; with one slot the
+    cheapest waiting request is admitted first."""
+    serve = server_mod
+    descs = small_requests(16)
+    a = serve.make_requests(copy.deepcopy(descs))
+    serve.Server(nstreams=4, chunk_traj_steps=1e3).run(a)
+    b = serve.make_requests(copy.deepcopy(descs))
+    serve.Server(nstreams=4, chunk_traj_steps=1e3, policy="sjf", max_active=1).run(b)
+    for x, y in zip(a, b):
+        assert np.array_equal(x.q, y.q) and np.array_equal(x.iters, y.iters)
+    # admission order under one slot: after the first, each admitted request
+    # was the cheapest among those that had arrived
+    admitted = sorted(b, key=lambda r: r.t_admit)
+    for k in range(1, len(admitted)):
+        waiting_then = [r for r in admitted[k:] if r.arrival <= admitted[k].t_admit]
+        assert serve.estimated_flops(admitted[k]) <= min(serve.estimated_flops(r) for r in waiting_then)
