@@ -364,11 +364,12 @@ def run_uneven(args):
             from oracle import cbind
             cores = os.cpu_count() or 1
             # bounded sample: 128 instances evenly spaced over the plan order
-            # (all buckets), 40 steps each, one instance per thread task
+            # (all buckets), one instance per thread task, the step count
+            # sized from a 20-step pilot to about 10 s of wall time
             sel = plan.perm[np.linspace(0, args.ninst - 1, min(128, args.ninst)).astype(int)]
             import concurrent.futures as cf
             kinds = {2: cbind.NBODY, 3: cbind.FPUT, 5: cbind.HARMONIC}
-            nsamp = 40
+            nsamp = 20
 
             def one(k):
                 o, d = int(w["offset"][k]), int(w["dim"][k])
@@ -377,6 +378,11 @@ def run_uneven(args):
                           w["v0"][o:o + d], w["h"][k], nsamp)
 
             cbind.lib()
+            t0 = time.perf_counter()
+            with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+                list(ex.map(one, sel))
+            pilot = time.perf_counter() - t0
+            nsamp = int(max(20, min(args.traj_steps, 20 * 10.0 / max(pilot, 1e-3))))
             t0 = time.perf_counter()
             with cf.ThreadPoolExecutor(max_workers=cores) as ex:
                 list(ex.map(one, sel))

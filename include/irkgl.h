@@ -143,7 +143,8 @@ enum {
   IRKGL_OPT_BLOCK_THREADS = 4,  /* threads per block: 64, 128 or 256 (default 128) */
   IRKGL_OPT_GRID_BLOCKS = 5,    /* persistent grid size (0 = one full wave, the default) */
   IRKGL_OPT_WIDE_TEAM = 6,      /* ragged batches: threads per instance, 32, 64, 128 or 256
-                                   (0 = chosen from the largest dimension, the default) */
+                                   (0 = 256, the default: fastest or within a few per cent of
+                                   the fastest for every size measured on GB300) */
   IRKGL_OPT_MONITOR_LOCAL = 7,  /* 1: dH_max reports the local error max_n |(H_n - H_{n-1})/H_{n-1}|
                                    (Eq. DHlocmax) instead of the global one (default 0; not
                                    carried across irkgl_advance calls) */

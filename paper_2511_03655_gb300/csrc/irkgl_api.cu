@@ -670,15 +670,19 @@ static int run_wide(irkgl_ctx* c, irkgl::WideArgs& a, int ninst, int dmax, cudaS
   static_assert(sizeof(irkgl_instance) == sizeof(irkgl::WideInstance), "instance layout");
   if (dmax < 1) return IRKGL_ERR_INVALID;
   if (dmax > 1024) return IRKGL_ERR_UNSUPPORTED;
-  // team shape: requested size, else a warp for small instances, else the
-  // smallest block whose threads x slots cover dmax
+  // team shape: the requested team size, else 256-thread teams (the
+  // right-hand side runs team-parallel over (stage, body or particle), and
+  // the autotuner measured the 256-thread team within a few per cent of the
+  // best for every size bucket on GB300); the first shape of that team size
+  // whose threads x slots cover dmax
   const irkgl::WideShape* shapes = nullptr;
   const int ns = irkgl::wide_shapes(&shapes);
   const irkgl::WideShape* ws = nullptr;
+  const int want_team = c->wide_team ? c->wide_team : 256;
   for (int i = 0; i < ns && !ws; i++) {
     const irkgl::WideShape& x = shapes[i];
     if (x.team * x.slots < dmax) continue;
-    if (c->wide_team ? x.team == c->wide_team : true) ws = &x;
+    if (x.team == want_team) ws = &x;
   }
   if (!ws) return IRKGL_ERR_UNSUPPORTED;
   const int teams = ws->block / ws->team;
