@@ -559,8 +559,11 @@ __device__ __forceinline__ double select_own(const double (&arr)[D], int s, int 
   return x;
 }
 
-template <class Rhs, int LPT, int BLOCK, int MIX = 0>
-__global__ void __launch_bounds__(BLOCK)
+// MINB: minimum resident blocks per SM passed to the compiler's register
+// allocator (__launch_bounds__); chosen per compiled tile from timings of the
+// full Kepler ensemble on GB300 (1 = no constraint).
+template <class Rhs, int LPT, int BLOCK, int MIX = 0, int MINB = 1>
+__global__ void __launch_bounds__(BLOCK, MINB)
     irkgl_kernel(const __grid_constant__ KArgs a, const __grid_constant__ Coef cf) {
   static_assert(MIX == 0 || LPT == 1, "fixed-point mixing needs all stages in one lane");
   constexpr int D = Rhs::D;

@@ -21,9 +21,9 @@ struct KernelEntry {
   void (*launch)(dim3, dim3, cudaStream_t, const KArgs&, const Coef&);
 };
 
-template <class Rhs, int LPT, int BLOCK, int MIX>
+template <class Rhs, int LPT, int BLOCK, int MIX, int MINB>
 void launch_impl(dim3 grid, dim3 block, cudaStream_t st, const KArgs& a, const Coef& c) {
-  irkgl_kernel<Rhs, LPT, BLOCK, MIX><<<grid, block, 0, st>>>(a, c);
+  irkgl_kernel<Rhs, LPT, BLOCK, MIX, MINB><<<grid, block, 0, st>>>(a, c);
 }
 
 struct KernelTable {
@@ -38,9 +38,10 @@ KernelTable kernels_nbody();
 
 }  // namespace irkgl
 
-#define IRKGL_ENTRY_MIX(KIND, DIM, RHS, LPT, BLOCK, MIX)                                  \
-  ::irkgl::KernelEntry {                                                                 \
-    KIND, DIM, LPT, BLOCK, MIX, (const void*)::irkgl::irkgl_kernel<RHS, LPT, BLOCK, MIX>, \
-        ::irkgl::launch_impl<RHS, LPT, BLOCK, MIX>                                       \
+#define IRKGL_ENTRY_TUNED(KIND, DIM, RHS, LPT, BLOCK, MIX, MINB)                                 \
+  ::irkgl::KernelEntry {                                                                         \
+    KIND, DIM, LPT, BLOCK, MIX, (const void*)::irkgl::irkgl_kernel<RHS, LPT, BLOCK, MIX, MINB>,  \
+        ::irkgl::launch_impl<RHS, LPT, BLOCK, MIX, MINB>                                         \
   }
+#define IRKGL_ENTRY_MIX(KIND, DIM, RHS, LPT, BLOCK, MIX) IRKGL_ENTRY_TUNED(KIND, DIM, RHS, LPT, BLOCK, MIX, 1)
 #define IRKGL_ENTRY(KIND, DIM, RHS, LPT, BLOCK) IRKGL_ENTRY_MIX(KIND, DIM, RHS, LPT, BLOCK, 0)
