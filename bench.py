@@ -54,9 +54,9 @@ FLOPS_NBODY6 = (3882, 6456)
 # dram__bytes_write.sum of one launch of the full 65,536-orbit batch; the
 # state is read once and kept in registers, so the traffic depends on the
 # batch, not on the horizon), valid only for the kernel source it was taken
-# on (sha256 prefix of irkgl_device.cuh) and for the FP64 mixing.
-NCU_TRAFFIC_BYTES_PER_LAUNCH = {0: 4185600 + 70656}  # by stage mixing
-NCU_KERNEL_SHA = "852ce64a9b6102fb"
+# on (sha256 prefix of irkgl_device.cuh).
+NCU_TRAFFIC_BYTES_PER_LAUNCH = {0: 4389888 + 68864, 1: 4640000 + 595968}  # by stage mixing
+NCU_KERNEL_SHA = "f546dfbba7f613d8"
 
 
 def parse():
