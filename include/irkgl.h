@@ -152,6 +152,13 @@ enum {
                                    chain (default); 1 = exact fixed-point sums on the integer
                                    pipes, rounded once (one lane per trajectory, default tables
                                    only; IRKGL_ERR_UNSUPPORTED otherwise) */
+  IRKGL_OPT_TILE_LAYOUT = 10,   /* second-order kinds with d = 2 (Kepler, Henon-Heiles): 0 = the
+                                   stage-split tiles (default); 1 = the component-split tile: two
+                                   lanes per trajectory, each holding one component of all eight
+                                   stages, so the mixing of Eq. Qi2 uses compile-time coefficients
+                                   and no exchange; bit-identical results to the stage-split tile
+                                   with two lanes (mix 0) or one lane (mix 1).  Other kinds:
+                                   IRKGL_ERR_UNSUPPORTED at the call */
   IRKGL_OPT_STAGES = 9          /* first-order kinds: s of the s-stage IRKGL scheme, 2, 4, 6 or 8
                                    (default 8 = IRKGL16; s < 8 uses the built-in Gauss tables of
                                    that s, order 2s).  l_prev arrays are then [batch][s][D].  The

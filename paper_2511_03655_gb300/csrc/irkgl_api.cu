@@ -42,13 +42,14 @@ int cuda_fail(cudaError_t e) {
 
 using irkgl::KernelEntry;
 
-const KernelEntry* find_kernel(int kind, int dim, int lpt, int block, int mix = 0) {
+const KernelEntry* find_kernel(int kind, int dim, int lpt, int block, int mix = 0, int layout = 0) {
   const irkgl::KernelTable tables[] = {irkgl::kernels_kepler(), irkgl::kernels_henon_heiles(),
                                        irkgl::kernels_harmonic(), irkgl::kernels_nbody()};
   for (const irkgl::KernelTable& t : tables)
     for (int i = 0; i < t.count; i++) {
       const KernelEntry& e = t.entries[i];
-      if (e.kind == kind && e.dim == dim && e.lpt == lpt && e.block == block && e.mix == mix)
+      if (e.kind == kind && e.dim == dim && e.lpt == lpt && e.block == block && e.mix == mix &&
+          e.layout == layout)
         return &e;
     }
   return nullptr;
@@ -157,6 +158,7 @@ struct irkgl_ctx {
   int monitor_local;
   int mix;             // IRKGL_OPT_MIX
   int stages;          // IRKGL_OPT_STAGES (first-order kinds: 2, 4, 6 or 8)
+  int layout;          // IRKGL_OPT_TILE_LAYOUT: 0 stage split, 1 component split
   int default_tables;  // the context uses irkgl_default_coeffs (needed by mix = 1)
   // staging for irkgl_integrate_host
   void* d_stage;
@@ -336,6 +338,10 @@ int irkgl_set_option(irkgl_ctx* c, int option, long long value) {
       if (value != 0 && value != 1) return IRKGL_ERR_INVALID;
       c->mix = static_cast<int>(value);
       return IRKGL_OK;
+    case IRKGL_OPT_TILE_LAYOUT:
+      if (value != 0 && value != 1) return IRKGL_ERR_INVALID;
+      c->layout = static_cast<int>(value);
+      return IRKGL_OK;
     case IRKGL_OPT_STAGES:
       if (!(value == 2 || value == 4 || value == 6 || value == 8)) return IRKGL_ERR_INVALID;
       c->stages = static_cast<int>(value);
@@ -360,6 +366,7 @@ int irkgl_get_tile(irkgl_ctx* c) {
     const int lpt = c->lpt ? c->lpt : default_lpt(c->kind, c->dim, c->stages);
     return find_kernel1(c->kind, c->dim, lpt, c->block, c->stages) ? lpt : 0;
   }
+  if (c->layout) return find_kernel(c->kind, c->dim, 2, c->block, c->mix, 1) ? 2 : 0;
   if (c->mix) return find_kernel(c->kind, c->dim, 1, c->block, 1) ? 1 : 0;
   return c->lpt ? c->lpt : default_lpt(c->kind, c->dim);
 }
@@ -371,8 +378,10 @@ static int run(irkgl_ctx* c, KArgs& a, cudaStream_t st) {
   if (first_order_kind(c->kind)) return IRKGL_ERR_INVALID;  // use the irkgl_*1 calls
   if (c->stages != 8) return IRKGL_ERR_UNSUPPORTED;        // s-stage variants: first-order form only
   if (c->mix && !c->default_tables) return IRKGL_ERR_UNSUPPORTED;
-  const int lpt = c->mix ? 1 : (c->lpt ? c->lpt : default_lpt(c->kind, c->dim));
-  const KernelEntry* ke = lpt ? find_kernel(c->kind, c->dim, lpt, c->block, c->mix) : nullptr;
+  // the component-split tile always uses two lanes; the fixed-point stage-split
+  // tile one; otherwise the requested or default lanes per trajectory
+  const int lpt = c->layout ? 2 : c->mix ? 1 : (c->lpt ? c->lpt : default_lpt(c->kind, c->dim));
+  const KernelEntry* ke = lpt ? find_kernel(c->kind, c->dim, lpt, c->block, c->mix, c->layout) : nullptr;
   if (!ke) return IRKGL_ERR_UNSUPPORTED;
   a.counter = c->d_counter;
   a.params = c->d_params;

@@ -7,6 +7,7 @@
 
 #include <cuda_runtime.h>
 
+#include "irkgl_cs.cuh"
 #include "irkgl_device.cuh"
 
 namespace irkgl {
@@ -16,7 +17,8 @@ struct KernelEntry {
   int dim;
   int lpt;
   int block;
-  int mix;  // 0: FP64 FMA mixing, 1: fixed-point mixing on the integer pipes
+  int mix;     // 0: FP64 FMA mixing, 1: fixed-point mixing on the integer pipes
+  int layout;  // 0: stage split (irkgl_kernel), 1: component split (irkgl_kernel_cs, lpt = 2)
   const void* fn;
   void (*launch)(dim3, dim3, cudaStream_t, const KArgs&, const Coef&);
 };
@@ -24,6 +26,11 @@ struct KernelEntry {
 template <class Rhs, int LPT, int BLOCK, int MIX, int MINB>
 void launch_impl(dim3 grid, dim3 block, cudaStream_t st, const KArgs& a, const Coef& c) {
   irkgl_kernel<Rhs, LPT, BLOCK, MIX, MINB><<<grid, block, 0, st>>>(a, c);
+}
+
+template <class Rhs, int BLOCK, int MIX, int MINB>
+void launch_cs_impl(dim3 grid, dim3 block, cudaStream_t st, const KArgs& a, const Coef& c) {
+  irkgl_kernel_cs<Rhs, BLOCK, MIX, MINB><<<grid, block, 0, st>>>(a, c);
 }
 
 struct KernelTable {
@@ -38,10 +45,16 @@ KernelTable kernels_nbody();
 
 }  // namespace irkgl
 
-#define IRKGL_ENTRY_TUNED(KIND, DIM, RHS, LPT, BLOCK, MIX, MINB)                                 \
+#define IRKGL_ENTRY_TUNED(KIND, DIM, RHS, LPT, BLOCK, MIX, MINB)                                    \
+  ::irkgl::KernelEntry {                                                                            \
+    KIND, DIM, LPT, BLOCK, MIX, 0, (const void*)::irkgl::irkgl_kernel<RHS, LPT, BLOCK, MIX, MINB>,  \
+        ::irkgl::launch_impl<RHS, LPT, BLOCK, MIX, MINB>                                            \
+  }
+// component-split tile (two lanes per trajectory, one component each)
+#define IRKGL_ENTRY_CS(KIND, RHS, BLOCK, MIX, MINB)                                               \
   ::irkgl::KernelEntry {                                                                         \
-    KIND, DIM, LPT, BLOCK, MIX, (const void*)::irkgl::irkgl_kernel<RHS, LPT, BLOCK, MIX, MINB>,  \
-        ::irkgl::launch_impl<RHS, LPT, BLOCK, MIX, MINB>                                         \
+    KIND, 2, 2, BLOCK, MIX, 1, (const void*)::irkgl::irkgl_kernel_cs<RHS, BLOCK, MIX, MINB>,     \
+        ::irkgl::launch_cs_impl<RHS, BLOCK, MIX, MINB>                                           \
   }
 #define IRKGL_ENTRY_MIX(KIND, DIM, RHS, LPT, BLOCK, MIX) IRKGL_ENTRY_TUNED(KIND, DIM, RHS, LPT, BLOCK, MIX, 1)
 #define IRKGL_ENTRY(KIND, DIM, RHS, LPT, BLOCK) IRKGL_ENTRY_MIX(KIND, DIM, RHS, LPT, BLOCK, 0)

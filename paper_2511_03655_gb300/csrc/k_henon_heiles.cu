@@ -11,6 +11,7 @@ const ::irkgl::KernelEntry kEntries[] = {
     IRKGL_ENTRY(IRKGL_RHS_HENON_HEILES, 2, ::irkgl::HenonHeiles<1>, 8, 128),
     IRKGL_ENTRY(IRKGL_RHS_HENON_HEILES_FORCED, 2, ::irkgl::HenonHeilesForced<8>, 1, 128),
     IRKGL_ENTRY(IRKGL_RHS_HENON_HEILES_FORCED, 2, ::irkgl::HenonHeilesForced<4>, 2, 128),
+    IRKGL_ENTRY_CS(IRKGL_RHS_HENON_HEILES, ::irkgl::HenonHeiles<4>, 128, 0, 1),
 };
 }  // namespace
 

@@ -17,6 +17,8 @@ const ::irkgl::KernelEntry kEntries[] = {
     IRKGL_ENTRY(IRKGL_RHS_KEPLER, 2, ::irkgl::Kepler<4>, 2, 256),
     IRKGL_ENTRY(IRKGL_RHS_KEPLER, 2, ::irkgl::Kepler<2>, 4, 128),
     IRKGL_ENTRY(IRKGL_RHS_KEPLER, 2, ::irkgl::Kepler<1>, 8, 128),
+    IRKGL_ENTRY_CS(IRKGL_RHS_KEPLER, ::irkgl::Kepler<4>, 128, 0, 1),
+    IRKGL_ENTRY_CS(IRKGL_RHS_KEPLER, ::irkgl::Kepler<4>, 128, 1, 1),
 };
 }  // namespace
 

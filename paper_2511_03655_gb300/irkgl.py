@@ -28,6 +28,7 @@ OPT_LANES_PER_TRAJ, OPT_KMAX, OPT_MONITOR_EVERY, OPT_BLOCK_THREADS, OPT_GRID_BLO
 OPT_WIDE_TEAM = 6
 OPT_MONITOR_LOCAL = 7
 OPT_STAGES = 9
+OPT_TILE_LAYOUT = 10  # 0 stage split, 1 component split (d = 2 kinds)
 SPLIT_STRANG, SPLIT_SUZ90 = 1, 2
 OPT_MIX = 8
 
@@ -508,12 +509,13 @@ class Integrator:
 
     def __init__(self, kind: int, params, dim: int, h: float, coeffs: dict | None = None,
                  lanes_per_traj: int = 0, kmax: int = 100, monitor_every: int = 1,
-                 block_threads: int = 128, mix: int = 0, stages: int = 8):
+                 block_threads: int = 128, mix: int = 0, stages: int = 8, layout: int = 0):
         self.dim = dim
         self.stages = stages
         self.ctx = irkgl_create(kind, params, dim, h, coeffs)
         self.set(OPT_STAGES, stages)
         self.set(OPT_MIX, mix)
+        self.set(OPT_TILE_LAYOUT, layout)
         self.set(OPT_LANES_PER_TRAJ, lanes_per_traj)
         self.set(OPT_KMAX, kmax)
         self.set(OPT_MONITOR_EVERY, monitor_every)
