@@ -55,7 +55,8 @@ FLOPS_NBODY6 = (3882, 6456)
 # state is read once and kept in registers, so the traffic depends on the
 # batch, not on the horizon), valid only for the kernel source it was taken
 # on (sha256 prefix of irkgl_device.cuh).
-NCU_TRAFFIC_BYTES_PER_LAUNCH = {0: 4389888 + 68864, 1: 4640000 + 595968}  # by stage mixing
+NCU_TRAFFIC_BYTES_PER_LAUNCH = {(0, "stage split"): 4389888 + 68864,  # by (mixing, tile layout)
+                                (1, "stage split"): 4640000 + 595968}
 NCU_KERNEL_SHA = "f546dfbba7f613d8"
 
 
@@ -789,7 +790,7 @@ def main():
 
     flops_launch = fps * float(steps.sum()) + fpw * float(iters.sum())
     achieved = flops_launch / statistics.mean(times) / 1e12
-    traffic = (NCU_TRAFFIC_BYTES_PER_LAUNCH.get(args.mix) if NCU_KERNEL_SHA == kernel_sha()
+    traffic = (NCU_TRAFFIC_BYTES_PER_LAUNCH.get((args.mix, integ.layout)) if NCU_KERNEL_SHA == kernel_sha()
                and args.workload == "kepler" and args.batch == 65536 else None)
 
     line = {
@@ -799,7 +800,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": desc, "batch_per_gpu": args.batch,
                    "periods": args.periods if args.workload == "kepler" else None,
-                   "lanes_per_traj": integ.tile,
+                   "lanes_per_traj": integ.tile, "tile_layout": integ.layout,
                    "mixing": ("fixed-point (integer pipes)" if args.mix and args.workload == "kepler"
                               else "FP64 FMA chain"),
                    "order": "natural" if args.no_order else "similarity (e descending)",
@@ -815,7 +816,8 @@ def main():
                      "frac": achieved / peak_tflops, "traffic": traffic,
                      "peak_source": "FP64 FMA-chain probe (irkgl_probe_fp64_fma) measured live, "
                                     "2 flops per FMA",
-                     "kernel": f"irkgl_kernel<{args.workload}>", "flops_per_launch": flops_launch},
+                     "kernel": ("irkgl_kernel_cs" if integ.layout == "component split" else "irkgl_kernel")
+                               + f"<{args.workload}>", "flops_per_launch": flops_launch},
         "clocks": clk,
     }
 

@@ -152,13 +152,16 @@ enum {
                                    chain (default); 1 = exact fixed-point sums on the integer
                                    pipes, rounded once (one lane per trajectory, default tables
                                    only; IRKGL_ERR_UNSUPPORTED otherwise) */
-  IRKGL_OPT_TILE_LAYOUT = 10,   /* second-order kinds with d = 2 (Kepler, Henon-Heiles): 0 = the
-                                   stage-split tiles (default); 1 = the component-split tile: two
-                                   lanes per trajectory, each holding one component of all eight
-                                   stages, so the mixing of Eq. Qi2 uses compile-time coefficients
-                                   and no exchange; bit-identical results to the stage-split tile
-                                   with two lanes (mix 0) or one lane (mix 1).  Other kinds:
-                                   IRKGL_ERR_UNSUPPORTED at the call */
+  IRKGL_OPT_TILE_LAYOUT = 10,   /* second-order kinds: 1 = the stage-split tiles (LPT lanes per
+                                   trajectory share the stages); 2 = the component-split tile for
+                                   d = 2 (Kepler, Henon-Heiles): two lanes per trajectory, each
+                                   holding one component of all eight stages, so the mixing of
+                                   Eq. Qi2 uses compile-time coefficients and no exchange
+                                   (IRKGL_ERR_UNSUPPORTED at the call for other kinds); 0 = auto
+                                   (default): the component split with the fixed-point mixing where
+                                   compiled, else the stage split.  Results are bit-identical
+                                   between the layouts (to the two-lane stage split with mix 0, the
+                                   one-lane tile with mix 1) */
   IRKGL_OPT_STAGES = 9          /* first-order kinds: s of the s-stage IRKGL scheme, 2, 4, 6 or 8
                                    (default 8 = IRKGL16; s < 8 uses the built-in Gauss tables of
                                    that s, order 2s).  l_prev arrays are then [batch][s][D].  The
@@ -348,6 +351,11 @@ const char* irkgl_last_cuda_error(void);
 
 /* Lanes per trajectory that the context would use for its (kind, dim). */
 int irkgl_get_tile(struct irkgl_ctx* ctx);
+
+/* The tile layout a call on this context runs: 1 = stage split, 2 = component
+ * split (IRKGL_OPT_TILE_LAYOUT resolved); first-order contexts report 1.
+ * Returns IRKGL_ERR_INVALID for a NULL context. */
+int irkgl_get_layout(struct irkgl_ctx* ctx);
 
 /* Diagnostic, not part of the method: launch an FP64 fused multiply-add
  * throughput probe (a full grid of independent FMA chains) on cuda_stream

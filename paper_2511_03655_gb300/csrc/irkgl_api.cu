@@ -158,7 +158,7 @@ struct irkgl_ctx {
   int monitor_local;
   int mix;             // IRKGL_OPT_MIX
   int stages;          // IRKGL_OPT_STAGES (first-order kinds: 2, 4, 6 or 8)
-  int layout;          // IRKGL_OPT_TILE_LAYOUT: 0 stage split, 1 component split
+  int layout;          // IRKGL_OPT_TILE_LAYOUT: 0 auto, 1 stage split, 2 component split
   int default_tables;  // the context uses irkgl_default_coeffs (needed by mix = 1)
   // staging for irkgl_integrate_host
   void* d_stage;
@@ -339,7 +339,7 @@ int irkgl_set_option(irkgl_ctx* c, int option, long long value) {
       c->mix = static_cast<int>(value);
       return IRKGL_OK;
     case IRKGL_OPT_TILE_LAYOUT:
-      if (value != 0 && value != 1) return IRKGL_ERR_INVALID;
+      if (value < 0 || value > 2) return IRKGL_ERR_INVALID;
       c->layout = static_cast<int>(value);
       return IRKGL_OK;
     case IRKGL_OPT_STAGES:
@@ -360,28 +360,56 @@ int irkgl_set_option(irkgl_ctx* c, int option, long long value) {
   }
 }
 
+static void resolve_tile(const irkgl_ctx* c, int* lpt, int* layout);
+
+int irkgl_get_layout(irkgl_ctx* c) {
+  if (!c) return IRKGL_ERR_INVALID;
+  if (first_order_kind(c->kind)) return 1;
+  int lpt = 0, layout = 0;
+  resolve_tile(c, &lpt, &layout);
+  return layout ? 2 : 1;
+}
+
 int irkgl_get_tile(irkgl_ctx* c) {
   if (!c) return IRKGL_ERR_INVALID;
   if (first_order_kind(c->kind)) {
     const int lpt = c->lpt ? c->lpt : default_lpt(c->kind, c->dim, c->stages);
     return find_kernel1(c->kind, c->dim, lpt, c->block, c->stages) ? lpt : 0;
   }
-  if (c->layout) return find_kernel(c->kind, c->dim, 2, c->block, c->mix, 1) ? 2 : 0;
-  if (c->mix) return find_kernel(c->kind, c->dim, 1, c->block, 1) ? 1 : 0;
+  int lpt = 0, layout = 0;
+  if (!first_order_kind(c->kind)) {
+    resolve_tile(c, &lpt, &layout);
+    return find_kernel(c->kind, c->dim, lpt, c->block, c->mix, layout) ? lpt : 0;
+  }
   return c->lpt ? c->lpt : default_lpt(c->kind, c->dim);
 }
 
 // Right-hand sides that read t: no energy monitor (H(t) is not conserved).
 static bool time_dependent_kind(int kind) { return kind == IRKGL_RHS_HENON_HEILES_FORCED; }
 
+// The tile a second-order call runs: the component-split tile (two lanes)
+// when requested, or by default with the fixed-point mixing where it is
+// compiled (the fastest form measured on GB300: 1.31x the one-lane tile);
+// the one-lane tile for the fixed-point mixing otherwise; else the
+// requested or default lanes per trajectory of the stage-split tiles.
+static void resolve_tile(const irkgl_ctx* c, int* lpt, int* layout) {
+  const bool cs_ok = find_kernel(c->kind, c->dim, 2, c->block, c->mix, 1) != nullptr;
+  if (c->layout == 2 || (c->layout == 0 && c->mix && cs_ok)) {
+    *lpt = 2;
+    *layout = 1;
+  } else {
+    *lpt = c->mix ? 1 : (c->lpt ? c->lpt : default_lpt(c->kind, c->dim));
+    *layout = 0;
+  }
+}
+
 static int run(irkgl_ctx* c, KArgs& a, cudaStream_t st) {
   if (first_order_kind(c->kind)) return IRKGL_ERR_INVALID;  // use the irkgl_*1 calls
   if (c->stages != 8) return IRKGL_ERR_UNSUPPORTED;        // s-stage variants: first-order form only
   if (c->mix && !c->default_tables) return IRKGL_ERR_UNSUPPORTED;
-  // the component-split tile always uses two lanes; the fixed-point stage-split
-  // tile one; otherwise the requested or default lanes per trajectory
-  const int lpt = c->layout ? 2 : c->mix ? 1 : (c->lpt ? c->lpt : default_lpt(c->kind, c->dim));
-  const KernelEntry* ke = lpt ? find_kernel(c->kind, c->dim, lpt, c->block, c->mix, c->layout) : nullptr;
+  int lpt = 0, layout = 0;
+  resolve_tile(c, &lpt, &layout);
+  const KernelEntry* ke = lpt ? find_kernel(c->kind, c->dim, lpt, c->block, c->mix, layout) : nullptr;
   if (!ke) return IRKGL_ERR_UNSUPPORTED;
   a.counter = c->d_counter;
   a.params = c->d_params;

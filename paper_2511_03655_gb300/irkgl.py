@@ -28,7 +28,7 @@ OPT_LANES_PER_TRAJ, OPT_KMAX, OPT_MONITOR_EVERY, OPT_BLOCK_THREADS, OPT_GRID_BLO
 OPT_WIDE_TEAM = 6
 OPT_MONITOR_LOCAL = 7
 OPT_STAGES = 9
-OPT_TILE_LAYOUT = 10  # 0 stage split, 1 component split (d = 2 kinds)
+OPT_TILE_LAYOUT = 10  # 0 auto, 1 stage split, 2 component split (d = 2 kinds)
 SPLIT_STRANG, SPLIT_SUZ90 = 1, 2
 OPT_MIX = 8
 
@@ -109,6 +109,7 @@ def load(path: str | None = None, build_if_missing: bool = False):
     L.irkgl_last_cuda_error.argtypes = []
     L.irkgl_last_cuda_error.restype = ctypes.c_char_p
     L.irkgl_get_tile.argtypes = [_P]
+    L.irkgl_get_layout.argtypes = [_P]
     L.irkgl_probe_fp64_fma.argtypes = [_P, ctypes.POINTER(ctypes.c_longlong), _P]
     L.irkgl_advance.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int, _P, _P, _P,
                                 ctypes.c_int, _P]
@@ -527,6 +528,11 @@ class Integrator:
     @property
     def tile(self) -> int:
         return irkgl_get_tile(self.ctx)
+
+    @property
+    def layout(self) -> str:
+        """The tile layout calls run: "stage split" or "component split"."""
+        return {1: "stage split", 2: "component split"}[load().irkgl_get_layout(_P(self.ctx))]
 
     def step(self, *args, **kw):
         return irkgl_step(self.ctx, self.dim, *args, **kw)

@@ -1,4 +1,4 @@
-"""The component-split tile (IRKGL_OPT_TILE_LAYOUT = 1) performs the
+"""The component-split tile (IRKGL_OPT_TILE_LAYOUT = 2) performs the
 operation sequence of an existing tile, so its results are bit-identical:
 with FP64 mixing to the stage-split tile with two lanes per trajectory,
 with fixed-point mixing to the one-lane tile (whose parity with the oracle
@@ -39,8 +39,8 @@ def test_kepler_component_split_bitwise(torch_cuda, mix, ref_lanes):
     from paper_2511_03655_gb300 import irkgl
     torch = torch_cuda
     w = workloads.kepler_ensemble(batch=8192, periods=3)
-    a, ta = run(torch, irkgl.RHS_KEPLER, [1.0], w, mix=mix, layout=1)
-    b, tb = run(torch, irkgl.RHS_KEPLER, [1.0], w, mix=mix, lanes_per_traj=ref_lanes)
+    a, ta = run(torch, irkgl.RHS_KEPLER, [1.0], w, mix=mix, layout=2)
+    b, tb = run(torch, irkgl.RHS_KEPLER, [1.0], w, mix=mix, lanes_per_traj=ref_lanes, layout=1)
     assert ta == 2 and tb == ref_lanes
     for f in FIELDS:
         assert torch.equal(getattr(a, f), getattr(b, f)), f
@@ -52,8 +52,8 @@ def test_henon_heiles_component_split_bitwise_and_oracle(torch_cuda):
     q, v, _ = workloads.henon_heiles_ensemble(2048)
     w = {"q0": q, "v0": v, "nsteps": np.full(2048, 400, np.int64), "h": np.full(2048, 0.5),
          "e": np.zeros(2048)}
-    a, _ = run(torch, irkgl.RHS_HENON_HEILES, [1.0], w, layout=1)
-    b, _ = run(torch, irkgl.RHS_HENON_HEILES, [1.0], w, lanes_per_traj=2)
+    a, _ = run(torch, irkgl.RHS_HENON_HEILES, [1.0], w, layout=2)
+    b, _ = run(torch, irkgl.RHS_HENON_HEILES, [1.0], w, lanes_per_traj=2, layout=1)
     for f in FIELDS:
         assert torch.equal(getattr(a, f), getattr(b, f)), f
     r = cbind.run(cbind.HENON_HEILES, [1.0], q[:64], v[:64], 0.5, 400)
@@ -66,7 +66,8 @@ def test_component_split_continuation_bitwise(torch_cuda):
     from paper_2511_03655_gb300 import irkgl
     torch = torch_cuda
     w = workloads.kepler_ensemble(batch=1000, periods=1)
-    ig = irkgl.Integrator(irkgl.RHS_KEPLER, [1.0], 2, 0.01, mix=1, layout=1)
+    ig = irkgl.Integrator(irkgl.RHS_KEPLER, [1.0], 2, 0.01, mix=1)
+    assert ig.layout == "component split"  # the default with the fixed-point mixing
     d = lambda a: torch.tensor(np.ascontiguousarray(a), device="cuda")  # noqa: E731
     one = ig.integrate(d(w["q0"]), d(w["v0"]), nsteps=d(w["nsteps"]), h=d(w["h"]))
     q, v = d(w["q0"]), d(w["v0"])
@@ -91,7 +92,7 @@ def test_component_split_continuation_bitwise(torch_cuda):
 def test_component_split_unsupported_elsewhere(torch_cuda):
     from paper_2511_03655_gb300 import irkgl
     torch = torch_cuda
-    ig = irkgl.Integrator(irkgl.RHS_HARMONIC, [1.0], 3, 0.1, layout=1)
+    ig = irkgl.Integrator(irkgl.RHS_HARMONIC, [1.0], 3, 0.1, layout=2)
     x = torch.zeros((4, 3), dtype=torch.float64, device="cuda")
     with pytest.raises(irkgl.IrkglError):
         ig.integrate(x, x, nsteps_all=1)
