@@ -56,7 +56,8 @@ FLOPS_NBODY6 = (3882, 6456)
 # batch, not on the horizon), valid only for the kernel source it was taken
 # on (sha256 prefix of irkgl_device.cuh).
 NCU_TRAFFIC_BYTES_PER_LAUNCH = {(0, "stage split"): 4389888 + 68864,  # by (mixing, tile layout)
-                                (1, "stage split"): 4640000 + 595968}
+                                (1, "stage split"): 4640000 + 595968,
+                                (1, "component split"): 4217088 + 118016}
 NCU_KERNEL_SHA = "f546dfbba7f613d8"
 
 
@@ -817,7 +818,12 @@ def main():
                      "peak_source": "FP64 FMA-chain probe (irkgl_probe_fp64_fma) measured live, "
                                     "2 flops per FMA",
                      "kernel": ("irkgl_kernel_cs" if integ.layout == "component split" else "irkgl_kernel")
-                               + f"<{args.workload}>", "flops_per_launch": flops_launch},
+                               + f"<{args.workload}>", "flops_per_launch": flops_launch,
+                     "note": ("fixed-point stage mixing: the 288 mixing flops of each sweep (and the "
+                              "initial guess's) run as exact 128-bit integer multiply-adds on the "
+                              "integer pipes, so the FP64 roof understates this kernel's ceiling and "
+                              "frac can exceed 1; the FP64-pipe share measured by ncu is in profiles/")
+                             if args.mix and args.workload == "kepler" else None},
         "clocks": clk,
     }
 

@@ -52,13 +52,15 @@ def test_fixed_mix_nonfinite_propagates(lib):
     assert np.isnan(out).all()
 
 
-@pytest.mark.parametrize("block", [128, 64])
-def test_mixed_kernel_kepler_parity(lib, block):
+@pytest.mark.parametrize("block,layout,tile", [(128, 0, 2), (128, 1, 1), (64, 0, 1)])
+def test_mixed_kernel_kepler_parity(lib, block, layout, tile):
+    """Both tiles of the fixed-point mixing: the component split (the default
+    at 128 threads) and the one-lane stage split."""
     torch, irkgl = lib
     w = workloads.kepler_single()
     h = float(w["h"][0])
-    integ = irkgl.Integrator(irkgl.RHS_KEPLER, [1.0], 2, h, mix=1, block_threads=block)
-    assert integ.tile == 1
+    integ = irkgl.Integrator(irkgl.RHS_KEPLER, [1.0], 2, h, mix=1, block_threads=block, layout=layout)
+    assert integ.tile == tile
     q, v = torch.tensor(w["q0"], device="cuda"), torch.tensor(w["v0"], device="cuda")
     ql, vl = torch.zeros_like(q), torch.zeros_like(v)
     rp = torch.zeros((1, 8, 2), dtype=torch.float64, device="cuda")
