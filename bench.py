@@ -54,11 +54,11 @@ FLOPS_NBODY6 = (3882, 6456)
 # dram__bytes_write.sum of one launch of the full 65,536-orbit batch; the
 # state is read once and kept in registers, so the traffic depends on the
 # batch, not on the horizon), valid only for the kernel source it was taken
-# on (sha256 prefix of irkgl_device.cuh).
+# on (kernel_sha(): the sources of the Kepler tiles).
 NCU_TRAFFIC_BYTES_PER_LAUNCH = {(0, "stage split"): 4389888 + 68864,  # by (mixing, tile layout)
                                 (1, "stage split"): 4640000 + 595968,
                                 (1, "component split"): 4217088 + 118016}
-NCU_KERNEL_SHA = "f546dfbba7f613d8"
+NCU_KERNEL_SHA = "68265a9b374b87ca"
 
 
 def parse():
@@ -94,8 +94,11 @@ def parse():
 
 
 def kernel_sha() -> str:
-    p = os.path.join(ROOT, "paper_2511_03655_gb300", "csrc", "irkgl_device.cuh")
-    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+    """sha256 prefix of the sources the Kepler tiles are compiled from."""
+    h = hashlib.sha256()
+    for f in ("irkgl_device.cuh", "irkgl_cs.cuh", "irkgl_kernels.h", "k_kepler.cu"):
+        h.update(open(os.path.join(ROOT, "paper_2511_03655_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
 
 
 class ClockSampler:
