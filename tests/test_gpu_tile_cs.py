@@ -46,14 +46,15 @@ def test_kepler_component_split_bitwise(torch_cuda, mix, ref_lanes):
         assert torch.equal(getattr(a, f), getattr(b, f)), f
 
 
-def test_henon_heiles_component_split_bitwise_and_oracle(torch_cuda):
+@pytest.mark.parametrize("mix,ref_lanes", [(0, 2), (1, 1)])
+def test_henon_heiles_component_split_bitwise_and_oracle(torch_cuda, mix, ref_lanes):
     from paper_2511_03655_gb300 import irkgl
     torch = torch_cuda
     q, v, _ = workloads.henon_heiles_ensemble(2048)
     w = {"q0": q, "v0": v, "nsteps": np.full(2048, 400, np.int64), "h": np.full(2048, 0.5),
          "e": np.zeros(2048)}
-    a, _ = run(torch, irkgl.RHS_HENON_HEILES, [1.0], w, layout=2)
-    b, _ = run(torch, irkgl.RHS_HENON_HEILES, [1.0], w, lanes_per_traj=2, layout=1)
+    a, _ = run(torch, irkgl.RHS_HENON_HEILES, [1.0], w, mix=mix, layout=2)
+    b, _ = run(torch, irkgl.RHS_HENON_HEILES, [1.0], w, mix=mix, lanes_per_traj=ref_lanes, layout=1)
     for f in FIELDS:
         assert torch.equal(getattr(a, f), getattr(b, f)), f
     r = cbind.run(cbind.HENON_HEILES, [1.0], q[:64], v[:64], 0.5, 400)
