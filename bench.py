@@ -368,9 +368,10 @@ def run_uneven(args):
         if rank == 0 and world == 1:
             from oracle import cbind
             cores = os.cpu_count() or 1
-            # bounded sample: 128 instances evenly spaced over the plan order
-            # (all buckets), one instance per thread task, the step count
-            # sized from a 20-step pilot to about 10 s of wall time
+            # bounded sample of about 10 s: instances evenly spaced over the
+            # plan order (all buckets), one instance per thread task; a
+            # 128-instance, 20-step pilot sizes the step count (up to the
+            # full horizon) and then the instance count
             sel = plan.perm[np.linspace(0, args.ninst - 1, min(128, args.ninst)).astype(int)]
             import concurrent.futures as cf
             kinds = {2: cbind.NBODY, 3: cbind.FPUT, 5: cbind.HARMONIC}
@@ -388,6 +389,9 @@ def run_uneven(args):
                 list(ex.map(one, sel))
             pilot = time.perf_counter() - t0
             nsamp = int(max(20, min(args.traj_steps, 20 * 10.0 / max(pilot, 1e-3))))
+            more = 10.0 / max(pilot * nsamp / 20, 1e-3)
+            if more > 1.5 and args.ninst > len(sel):
+                sel = plan.perm[np.linspace(0, args.ninst - 1, min(args.ninst, int(len(sel) * more))).astype(int)]
             t0 = time.perf_counter()
             with cf.ThreadPoolExecutor(max_workers=cores) as ex:
                 list(ex.map(one, sel))
