@@ -897,13 +897,36 @@ def main():
             idx = oracle_sample(w, cores, target_s=10.0)
             dt, r = time_oracle(w, idx, cores)
             okc = (r["dH_max"] <= TOL) & (r["status"] == 0)
+            # one host thread on a 16x smaller sample (about 10 s as well)
+            idx1 = idx[::max(cores, 1)]
+            dt1, _ = time_oracle(w, idx1, 1)
             line["cpu_baseline"] = {
                 "value": float(w["nsteps"][idx][okc].sum()) / dt, "unit": "traj-steps/s",
                 "cores": cores, "kind": "oracle",
                 "value_all": float(w["nsteps"][idx].sum()) / dt,
                 "sample": f"{len(idx)} orbits evenly spaced in e, full {args.periods}-period "
                           f"horizon ({float(w['nsteps'][idx].sum()):.3g} traj-steps), "
-                          f"{dt:.1f} s wall on {cores} threads"}
+                          f"{dt:.1f} s wall on {cores} threads",
+                "single_thread": {"value_all": float(w["nsteps"][idx1].sum()) / dt1,
+                                  "sample": f"{len(idx1)} of those orbits, {dt1:.1f} s on 1 thread"}}
+
+    if not args.skip_extras and args.workload == "nbody6" and rank == 0 and world == 1:
+        # ---- CPU baseline for the 6-body ensemble: copies x steps sized from a
+        # short pilot to about 10 s on the host cores
+        from oracle import cbind
+        cores = os.cpu_count() or 1
+        ncop = min(len(w["q0"]), 4 * cores)
+        t0 = time.perf_counter()
+        cbind.run(cbind.NBODY, w["params"], w["q0"][:ncop], w["v0"][:ncop], w["h"][:ncop], 200, nthreads=cores)
+        pilot = time.perf_counter() - t0
+        nst = int(max(200, min(args.traj_steps, 200 * 10.0 / max(pilot, 1e-3))))
+        t0 = time.perf_counter()
+        r = cbind.run(cbind.NBODY, w["params"], w["q0"][:ncop], w["v0"][:ncop], w["h"][:ncop], nst,
+                      nthreads=cores)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": ncop * nst / dt, "unit": "traj-steps/s", "cores": cores,
+                                "kind": "oracle",
+                                "sample": f"{ncop} copies x {nst} steps, {dt:.1f} s wall on {cores} threads"}
 
     if not args.skip_extras and args.workload == "kepler" and args.serve_requests > 0 and world == 1:
         # ---- serving (config 5): bounded Poisson window, continuous batching vs plain
