@@ -473,7 +473,8 @@ def run_first_order(args):
     y0h = workloads.schwarzschild_ensemble(B, seed_id=pdist.shard_seed(8, rank))
     par = list(workloads.SBH_PARAMS)
     y0 = torch.tensor(y0h, device=dev)
-    integ = irkgl.Integrator(irkgl.RHS_SCHWARZSCHILD, par, 4, SBH_H, lanes_per_traj=args.lanes)
+    integ = irkgl.Integrator(irkgl.RHS_SCHWARZSCHILD, par, 4, SBH_H, lanes_per_traj=args.lanes,
+                             mix=args.mix)
     out = irkgl.Outputs1.allocate(B, 4, device=dev)
     peak = fp64_peak_tflops(irkgl, torch, stream, dev)
 
@@ -518,7 +519,8 @@ def run_first_order(args):
                                f"(Eq. Ham_SBH, E=0.995, L=4.6, beta=8.9e-4), r0~U[9.5,16), theta=pi/2, "
                                f"p_r=0, H=-1/2; t in [0, {SBH_T:g}], h={SBH_H:g} ({nsteps} steps); "
                                "one persistent launch of the first-order (mu form) kernel",
-                   "lanes_per_traj": integ.tile,
+                   "lanes_per_traj": integ.tile, "tile_layout": integ.layout,
+                   "mixing": "fixed-point (integer pipes)" if args.mix else "FP64 FMA chain",
                    "l2": "state ~10 MB < L2; L2 flushed with a 256 MiB write before every timed step",
                    "parallelism": f"dp{world} (independent shards, no collective on the data path)"},
         "value_all": args.steps * steps_all / t_max,

@@ -57,11 +57,14 @@ const KernelEntry* find_kernel(int kind, int dim, int lpt, int block, int mix = 
 
 // Built-in default tile per (kind, dim): the smallest LPT that is compiled,
 // preferring 2 for d = 2 (both components' compensated updates in one pass).
-const irkgl::KernelEntry1* find_kernel1(int kind, int dim, int lpt, int block, int nst = 8) {
+const irkgl::KernelEntry1* find_kernel1(int kind, int dim, int lpt, int block, int nst = 8, int mix = 0,
+                                        int layout = 0) {
   const irkgl::KernelTable1 t = irkgl::kernels_first_order();
   for (int i = 0; i < t.count; i++) {
     const irkgl::KernelEntry1& e = t.entries[i];
-    if (e.kind == kind && e.dim == dim && e.lpt == lpt && e.block == block && e.nst == nst) return &e;
+    if (e.kind == kind && e.dim == dim && e.lpt == lpt && e.block == block && e.nst == nst && e.mix == mix &&
+        e.layout == layout)
+      return &e;
   }
   return nullptr;
 }
@@ -362,19 +365,34 @@ int irkgl_set_option(irkgl_ctx* c, int option, long long value) {
 
 static void resolve_tile(const irkgl_ctx* c, int* lpt, int* layout);
 
+// First-order tiles: the component split (D lanes) when requested, or by
+// default with the fixed-point mixing; otherwise the stage split with the
+// requested or default lanes.
+static void resolve_tile1(const irkgl_ctx* c, int* lpt, int* layout) {
+  const bool cs_ok = find_kernel1(c->kind, c->dim, c->dim, c->block, c->stages, c->mix, 1) != nullptr;
+  if (c->layout == 2 || (c->layout == 0 && c->mix && cs_ok)) {
+    *lpt = c->dim;
+    *layout = 1;
+  } else {
+    *lpt = c->lpt ? c->lpt : default_lpt(c->kind, c->dim, c->stages);
+    *layout = 0;
+  }
+}
+
 int irkgl_get_layout(irkgl_ctx* c) {
   if (!c) return IRKGL_ERR_INVALID;
-  if (first_order_kind(c->kind)) return 1;
   int lpt = 0, layout = 0;
-  resolve_tile(c, &lpt, &layout);
+  if (first_order_kind(c->kind)) resolve_tile1(c, &lpt, &layout);
+  else resolve_tile(c, &lpt, &layout);
   return layout ? 2 : 1;
 }
 
 int irkgl_get_tile(irkgl_ctx* c) {
   if (!c) return IRKGL_ERR_INVALID;
   if (first_order_kind(c->kind)) {
-    const int lpt = c->lpt ? c->lpt : default_lpt(c->kind, c->dim, c->stages);
-    return find_kernel1(c->kind, c->dim, lpt, c->block, c->stages) ? lpt : 0;
+    int lpt = 0, layout = 0;
+    resolve_tile1(c, &lpt, &layout);
+    return find_kernel1(c->kind, c->dim, lpt, c->block, c->stages, c->mix, layout) ? lpt : 0;
   }
   int lpt = 0, layout = 0;
   if (!first_order_kind(c->kind)) {
@@ -537,9 +555,11 @@ int irkgl_advance_t(irkgl_ctx* c, double* q, double* v, double* q_lo, double* v_
 
 static int run1(irkgl_ctx* c, KArgs1& a, cudaStream_t st) {
   if (!first_order_kind(c->kind)) return IRKGL_ERR_INVALID;
-  if (c->mix) return IRKGL_ERR_UNSUPPORTED;
-  const int lpt = c->lpt ? c->lpt : default_lpt(c->kind, c->dim, c->stages);
-  const irkgl::KernelEntry1* ke = lpt ? find_kernel1(c->kind, c->dim, lpt, c->block, c->stages) : nullptr;
+  if (c->mix && !c->default_tables) return IRKGL_ERR_UNSUPPORTED;  // fixed point: built-in tables
+  int lpt = 0, layout = 0;
+  resolve_tile1(c, &lpt, &layout);
+  const irkgl::KernelEntry1* ke =
+      lpt ? find_kernel1(c->kind, c->dim, lpt, c->block, c->stages, c->mix, layout) : nullptr;
   if (!ke) return IRKGL_ERR_UNSUPPORTED;
   Coef1 small;
   if (c->stages != 8 && !small_stage_tables(c->stages, &small)) return IRKGL_ERR_UNSUPPORTED;

@@ -422,7 +422,9 @@ struct KernelEntry1 {
   int dim;
   int lpt;
   int block;
-  int nst;  // stages
+  int nst;     // stages
+  int mix;     // 0: FP64 FMA mixing, 1: fixed-point mixing (component split only)
+  int layout;  // 0: stage split (irkgl1_kernel), 1: component split (irkgl1_kernel_cs, lpt = dim)
   const void* fn;
   void (*launch)(dim3, dim3, cudaStream_t, const KArgs1&, const Coef1&);
 };
@@ -443,6 +445,12 @@ KernelTable1 kernels_first_order();
 
 #define IRKGL_ENTRY1(KIND, DIM, RHS, LPT, BLOCK, NST)                                              \
   ::irkgl::KernelEntry1 {                                                                            \
-    KIND, DIM, LPT, BLOCK, NST, (const void*)::irkgl::irkgl1_kernel<RHS, LPT, BLOCK, NST>,          \
+    KIND, DIM, LPT, BLOCK, NST, 0, 0, (const void*)::irkgl::irkgl1_kernel<RHS, LPT, BLOCK, NST>,    \
         ::irkgl::launch1_impl<RHS, LPT, BLOCK, NST>                                                  \
+  }
+// component-split tile (irkgl1_cs.cuh): DIM lanes per trajectory, 8 stages
+#define IRKGL_ENTRY1_CS(KIND, DIM, RHS, BLOCK, MIX)                                                  \
+  ::irkgl::KernelEntry1 {                                                                            \
+    KIND, DIM, DIM, BLOCK, 8, MIX, 1, (const void*)::irkgl::irkgl1_kernel_cs<RHS, BLOCK, MIX>,      \
+        ::irkgl::launch1_cs_impl<RHS, BLOCK, MIX>                                                    \
   }

@@ -1,5 +1,6 @@
 // k_first_order.cu -- compiled instantiations of the first-order IRKGL16 kernel.
 #include "irkgl.h"
+#include "irkgl1_cs.cuh"
 #include "irkgl_first_order.cuh"
 
 namespace {
@@ -21,6 +22,11 @@ const ::irkgl::KernelEntry1 kEntries[] = {
     IRKGL_ENTRY1(IRKGL_RHS_HARMONIC1, 2, ::irkgl::Harmonic1<2>, 1, 128, 2),
     IRKGL_ENTRY1(IRKGL_RHS_HARMONIC1, 2, ::irkgl::Harmonic1<4>, 1, 128, 4),
     IRKGL_ENTRY1(IRKGL_RHS_HARMONIC1, 2, ::irkgl::Harmonic1<6>, 1, 128, 6),
+    // component split (one component of all eight stages per lane)
+    IRKGL_ENTRY1_CS(IRKGL_RHS_SCHWARZSCHILD, 4, ::irkgl::Schwarzschild<2>, 128, 0),
+    IRKGL_ENTRY1_CS(IRKGL_RHS_SCHWARZSCHILD, 4, ::irkgl::Schwarzschild<2>, 128, 1),
+    IRKGL_ENTRY1_CS(IRKGL_RHS_HARMONIC1, 2, ::irkgl::Harmonic1<4>, 128, 0),
+    IRKGL_ENTRY1_CS(IRKGL_RHS_HARMONIC1, 2, ::irkgl::Harmonic1<4>, 128, 1),
 };
 }  // namespace
 

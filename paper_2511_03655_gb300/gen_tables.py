@@ -156,6 +156,8 @@ def split_tables():
 
 ETA_SHIFT = 63   # eta_ij = +-n_ij * 2^-63, n_ij exact (|eta| in [2^-11, 1))
 W_SHIFT = 50     # W_ij ~ +-w_ij * 2^-50, w_ij = round(|W_ij| 2^50) (only seeds the guess)
+MU_SHIFT = 62    # mu_ij = +-n_ij * 2^-62, n_ij exact (|mu| in [2^-8, 1.09): one bit less than eta)
+NU_SHIFT = 47    # nu_ij ~ +-n_ij * 2^-47 rounded (|nu| up to 3.7e4; only seeds the guess)
 R_BIAS = 61      # fixed-point R values are offset by 2^61 to make them non-negative
 
 
@@ -163,14 +165,16 @@ def int_tables(t):
     """Integer forms for the fixed-point mixing: magnitudes, signs and the
     per-row correction sum_j (+-n_ij) 2^R_BIAS that removes the offset."""
     out = {}
-    for name, shift, exact in (("ETA", ETA_SHIFT, True), ("W", W_SHIFT, False)):
+    for name, shift, exact in (("ETA", ETA_SHIFT, True), ("W", W_SHIFT, False),
+                               ("MU", MU_SHIFT, True), ("NU", NU_SHIFT, False)):
         mags, negs, bias = [], [], []
+        key = {"ETA": "eta", "W": "W", "MU": "mu", "NU": "nu"}[name]
         for i in range(S):
             row_sum = 0
             for j in range(S):
-                x = Fraction(t["eta" if name == "ETA" else "W"][i][j]) * (1 << shift)
+                x = Fraction(t[key][i][j]) * (1 << shift)
                 if exact:
-                    assert x.denominator == 1, "eta is not on the 2^-63 grid"
+                    assert x.denominator == 1, f"{key} is not on the 2^-{shift} grid"
                     m = abs(x.numerator)
                 else:
                     m = abs(round(x))
@@ -188,10 +192,12 @@ def _render_int(t) -> str:
     it = int_tables(t)
     lines = ["", "// Integer forms for the fixed-point mixing (see gen_tables.int_tables):",
              f"// |ETA_ij| * 2^{ETA_SHIFT} (exact), round(|W_ij| * 2^{W_SHIFT}); signs; per-row",
-             f"// corrections sum_j (+-m_ij) 2^{R_BIAS} as 128-bit two's complement words.",
+             f"// corrections sum_j (+-m_ij) 2^{R_BIAS} as 128-bit two's complement words;",
+             f"// |MU_ij| * 2^{MU_SHIFT} (exact) and round(|NU_ij| * 2^{NU_SHIFT}) for the first-order form.",
              f"#define IRKGL_ETA_SHIFT {ETA_SHIFT}", f"#define IRKGL_W_SHIFT {W_SHIFT}",
+             f"#define IRKGL_MU_SHIFT {MU_SHIFT}", f"#define IRKGL_NU_SHIFT {NU_SHIFT}",
              f"#define IRKGL_R_BIAS {R_BIAS}"]
-    for name in ("ETA", "W"):
+    for name in ("ETA", "W", "MU", "NU"):
         mags, negs, bias = it[name]
         lines.append(f"__host__ __device__ constexpr unsigned long long irkgl_{name.lower()}_mag(int k) {{")
         lines.append("  constexpr unsigned long long t[64] = {")
