@@ -921,7 +921,9 @@ def main():
         t0 = time.perf_counter()
         cbind.run(cbind.NBODY, w["params"], w["q0"][:ncop], w["v0"][:ncop], w["h"][:ncop], 200, nthreads=cores)
         pilot = time.perf_counter() - t0
-        nst = int(max(200, min(args.traj_steps, 200 * 10.0 / max(pilot, 1e-3))))
+        want = ncop * 200 * 10.0 / max(pilot, 1e-4)  # traj-steps in about 10 s
+        nst = int(max(200, min(args.traj_steps, want / ncop)))
+        ncop = int(min(len(w["q0"]), max(ncop, want / nst)))
         t0 = time.perf_counter()
         r = cbind.run(cbind.NBODY, w["params"], w["q0"][:ncop], w["v0"][:ncop], w["h"][:ncop], nst,
                       nthreads=cores)
