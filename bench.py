@@ -73,7 +73,7 @@ def parse():
     ap.add_argument("--no-order", action="store_true", help="natural order instead of similarity order")
     ap.add_argument("--skip-extras", action="store_true", help="skip e2e, plain form and CPU baseline")
     ap.add_argument("--workload", default="kepler",
-                    choices=["kepler", "nbody6", "uneven", "schwarzschild", "overhead"],
+                    choices=["kepler", "nbody6", "uneven", "schwarzschild", "overhead", "serving"],
                     help="kepler: the 65,536-orbit ensemble (default); nbody6: 16,384 perturbed "
                          "copies of a 6-body system; uneven: 4,096 ragged instances (N-body "
                          "N~U{3..64} and FPUT n~U{8..512}), autotuned vs fixed tiling; schwarzschild: "
@@ -686,6 +686,56 @@ def run_overhead(args):
     print(json.dumps(line))
     return 0
 
+
+# --------------------------------------------------------------------------
+# config 5: p50 / p99 latency over a sweep of arrival rates
+# --------------------------------------------------------------------------
+def run_serving_sweep(args):
+    """Bounded windows of 300 Poisson requests at several arrival rates,
+    served by the continuous-batching loop (arrival order, and shortest job
+    first): p50 / p99 latency, throughput, and the offered load (requested
+    trajectory-steps per second of arrival window) against the served rate,
+    below and above saturation."""
+    import copy
+
+    import torch
+
+    from paper_2511_03655_gb300 import build, irkgl, serve, workloads
+    torch.cuda.set_device(0)
+    build.build()
+    irkgl.load()
+    rows = []
+    for rate in (50.0, 200.0, 1000.0, 2000.0):
+        descs = workloads.serving_requests(n=args.serve_requests, rate=rate, batch_max=512,
+                                           horizon_max=3000, nb_max=24, n_max=256)
+        window = max(d["arrival"] for d in descs)
+        offered = sum(d["q0"].shape[0] * d["nsteps"] for d in descs) / max(window, 1e-9)
+        row = {"rate_per_s": rate, "requests": len(descs), "arrival_window_s": window,
+               "offered_traj_steps_s": offered}
+        for name, kw in (("fifo", dict(policy="fifo")), ("sjf", dict(policy="sjf", max_active=96))):
+            reqs = serve.make_requests(copy.deepcopy(descs))
+            srv = serve.Server(nstreams=16, chunk_traj_steps=2e5, **kw)
+            st = srv.run(reqs).summary()
+            srv.close()
+            row[name] = {"p50_latency_s": st["p50_latency_s"], "p99_latency_s": st["p99_latency_s"],
+                         "served_traj_steps_s": st["throughput_traj_steps_s"],
+                         "served_over_offered": st["throughput_traj_steps_s"] / offered,
+                         "makespan_s": st["makespan_s"], "gpu_launches": st["gpu_launches"]}
+        rows.append(row)
+    top = rows[-1]["sjf"]
+    line = {
+        "metric": METRIC, "value": top["served_traj_steps_s"], "unit": "traj-steps/s", "n_gpus": 1,
+        "steps": 1, "warmup": 0, "ms_per_step": 1e3 * top["makespan_s"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"serving windows of {args.serve_requests} Poisson requests per rate "
+                               "(config-1..4 families, batch logU[1,512], horizon logU[1e2,3e3], "
+                               "N-body N<=24, FPUT n<=256)"},
+        "gpu_launches": top["gpu_launches"],
+        "serving_rate_sweep": rows,
+    }
+    print(json.dumps(line))
+    return 0
+
 # --------------------------------------------------------------------------
 # GPU arm
 # --------------------------------------------------------------------------
@@ -702,6 +752,8 @@ def main():
         return run_first_order(args)
     if args.workload == "overhead":
         return run_overhead(args)
+    if args.workload == "serving":
+        return run_serving_sweep(args)
 
     import torch
     import torch.distributed as dist
