@@ -262,7 +262,7 @@ def run_uneven(args):
     plan = ragged.RaggedPlan(w, tiles=tiles)
     params = torch.tensor(w["params"], device=dev)
     q0, v0 = torch.tensor(w["q0"], device=dev), torch.tensor(w["v0"], device=dev)
-    runner = ragged.RaggedRunner(plan, params, q0, v0, device=dev)
+    runner = ragged.RaggedRunner(plan, params, q0, v0, device=dev, mix=args.mix)
     out = irkgl.RaggedOutputs.allocate(len(w["q0"]), args.ninst, device=dev)
     peak = fp64_peak_tflops(irkgl, torch, stream, dev)
 
@@ -313,6 +313,7 @@ def run_uneven(args):
                                f"(central mass + N-1 bodies), half FPUT alpha=0.25 n~U{{8..512}}, "
                                f"h from the step table, {args.traj_steps} steps each",
                    "step_table": "tuning/gb300.json" if tuned else "built-in defaults",
+                   "mixing": "fixed-point (integer pipes)" if args.mix else "FP64 FMA chain",
                    "tiling": "autotuned: one launch per size bucket on its own stream, team from "
                              "the tile table" if tiles else "bucketed, library team per bucket",
                    "buckets": [{"label": b.label, "instances": b.count, "dmax": b.dmax, "team": b.team}

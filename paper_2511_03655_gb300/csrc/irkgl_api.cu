@@ -132,15 +132,6 @@ __global__ void __launch_bounds__(256) fp64_fma_probe(double* out, double a, dou
 
 }  // namespace
 
-namespace irkgl {
-struct WideShape {
-  int team, block, slots;
-  const void* fn;
-  void (*launch)(dim3, dim3, size_t, cudaStream_t, const WideArgs&, const Coef&);
-};
-int wide_shapes(const WideShape** out);
-}  // namespace irkgl
-
 struct irkgl_ctx {
   int kind;
   int dim;
@@ -727,6 +718,7 @@ static int run_wide(irkgl_ctx* c, irkgl::WideArgs& a, int ninst, int dmax, cudaS
   static_assert(sizeof(irkgl_instance) == sizeof(irkgl::WideInstance), "instance layout");
   if (dmax < 1) return IRKGL_ERR_INVALID;
   if (dmax > 1024) return IRKGL_ERR_UNSUPPORTED;
+  if (c->mix && !c->default_tables) return IRKGL_ERR_UNSUPPORTED;  // fixed point: built-in tables
   // team shape: the requested team size, else 256-thread teams (the
   // right-hand side runs team-parallel over (stage, body or particle), and
   // the autotuner measured the 256-thread team within a few per cent of the
@@ -739,7 +731,7 @@ static int run_wide(irkgl_ctx* c, irkgl::WideArgs& a, int ninst, int dmax, cudaS
   for (int i = 0; i < ns && !ws; i++) {
     const irkgl::WideShape& x = shapes[i];
     if (x.team * x.slots < dmax) continue;
-    if (x.team == want_team) ws = &x;
+    if (x.team == want_team && x.mix == c->mix) ws = &x;
   }
   if (!ws) return IRKGL_ERR_UNSUPPORTED;
   const int teams = ws->block / ws->team;

@@ -63,6 +63,16 @@ struct WideArgs {
   int monitor_local;  // dH_max = max_n |(H_n - H_{n-1}) / H_{n-1}|
 };
 
+// Compiled team shapes (k_wide.cu): one warp per instance (small d) or the
+// whole block, SLOTS components per thread, FP64 or fixed-point mixing.
+struct WideShape {
+  int team, block, slots;
+  int mix;  // 0: FP64 FMA mixing, 1: fixed-point mixing
+  const void* fn;
+  void (*launch)(dim3, dim3, size_t, cudaStream_t, const WideArgs&, const Coef&);
+};
+int wide_shapes(const WideShape** out);
+
 // team barrier and team-wide AND / OR
 template <int TEAM>
 __device__ __forceinline__ void team_sync() {
@@ -182,7 +192,10 @@ __device__ __forceinline__ double team_energy_part(int kind, int d, const double
 }
 
 // SLOTS: owned components per thread (d <= TEAM * SLOTS).
-template <int TEAM, int BLOCK, int SLOTS>
+// MIX = 1: the stage mixing of Eq. Qi2 and the initial guess as exact
+// fixed-point sums on the integer pipes, rounded once (the register kernel's
+// fixed-point form, per owned component).
+template <int TEAM, int BLOCK, int SLOTS, int MIX = 0>
 __global__ void __launch_bounds__(BLOCK)
     irkgl_wide_kernel(const __grid_constant__ WideArgs a, const __grid_constant__ Coef cf) {
   static_assert(TEAM == 32 || TEAM == BLOCK, "a team is one warp or the whole block");
@@ -289,14 +302,28 @@ __global__ void __launch_bounds__(BLOCK)
           double Rj[S];
 #pragma unroll
           for (int j = 0; j < S; j++) Rj[j] = R[j * d + l];
+          if constexpr (MIX == 1) {
+            unsigned long long rb[S];
+            bool nf;
+            const int emax = fixed_column(Rj, rb, nf);
 #pragma unroll
-          for (int i = 0; i < S; i++) {
-            const double cvil = cf.c[i] * vh[s];
-            CV[i * d + l] = cvil;
-            double acc = cvil;
+            for (int i = 0; i < S; i++) {
+              const double cvil = cf.c[i] * vh[s];
+              CV[i * d + l] = cvil;
+              double T = fixed_row<true>(i, rb, emax);
+              if (nf) T = __longlong_as_double(0x7ff8000000000000LL);
+              Q[i * d + l] = fma(h, cvil + T, qh[s]);
+            }
+          } else {
 #pragma unroll
-            for (int j = 0; j < S; j++) acc = fma(cf.W[i * S + j], Rj[j], acc);
-            Q[i * d + l] = fma(h, acc, qh[s]);
+            for (int i = 0; i < S; i++) {
+              const double cvil = cf.c[i] * vh[s];
+              CV[i * d + l] = cvil;
+              double acc = cvil;
+#pragma unroll
+              for (int j = 0; j < S; j++) acc = fma(cf.W[i * S + j], Rj[j], acc);
+              Q[i * d + l] = fma(h, acc, qh[s]);
+            }
           }
         }
         dmin[s] = INF_BITS;
@@ -317,14 +344,28 @@ __global__ void __launch_bounds__(BLOCK)
 #pragma unroll
             for (int j = 0; j < S; j++) Rj[j] = R[j * d + l];
             unsigned long long dl = 0;
+            if constexpr (MIX == 1) {
+              unsigned long long rb[S];
+              bool nf;
+              const int emax = fixed_column(Rj, rb, nf);
 #pragma unroll
-            for (int i = 0; i < S; i++) {
-              double acc = CV[i * d + l];
+              for (int i = 0; i < S; i++) {
+                double T = fixed_row<false>(i, rb, emax);
+                if (nf) T = __longlong_as_double(0x7ff8000000000000LL);
+                const double qn = fma(h, CV[i * d + l] + T, qh[s]);
+                dl = umax64(dl, abs_bits(qn - Q[i * d + l]));
+                Q[i * d + l] = qn;
+              }
+            } else {
 #pragma unroll
-              for (int j = 0; j < S; j++) acc = fma(cf.eta[i * S + j], Rj[j], acc);
-              const double qn = fma(h, acc, qh[s]);
-              dl = umax64(dl, abs_bits(qn - Q[i * d + l]));
-              Q[i * d + l] = qn;
+              for (int i = 0; i < S; i++) {
+                double acc = CV[i * d + l];
+#pragma unroll
+                for (int j = 0; j < S; j++) acc = fma(cf.eta[i * S + j], Rj[j], acc);
+                const double qn = fma(h, acc, qh[s]);
+                dl = umax64(dl, abs_bits(qn - Q[i * d + l]));
+                Q[i * d + l] = qn;
+              }
             }
             bad = bad || (dl >= INF_BITS);
             cond = cond && ((dl == 0) || (dmin[s] <= umin64(dprev[s], dl)));

@@ -6,21 +6,18 @@
 
 namespace irkgl {
 
-// Team shapes: one warp per instance (small d), or the whole block.
-struct WideShape {
-  int team, block, slots;
-  const void* fn;
-  void (*launch)(dim3, dim3, size_t, cudaStream_t, const WideArgs&, const Coef&);
-};
-int wide_shapes(const WideShape** out);
 
-template <int TEAM, int BLOCK, int SLOTS>
+template <int TEAM, int BLOCK, int SLOTS, int MIX>
 void wide_launch(dim3 g, dim3 b, size_t smem, cudaStream_t st, const WideArgs& a, const Coef& c) {
-  irkgl_wide_kernel<TEAM, BLOCK, SLOTS><<<g, b, smem, st>>>(a, c);
+  irkgl_wide_kernel<TEAM, BLOCK, SLOTS, MIX><<<g, b, smem, st>>>(a, c);
 }
 
-#define IRKGL_WIDE(TEAM, BLOCK, SLOTS) \
-  WideShape { TEAM, BLOCK, SLOTS, (const void*)irkgl_wide_kernel<TEAM, BLOCK, SLOTS>, wide_launch<TEAM, BLOCK, SLOTS> }
+#define IRKGL_WIDE_MIX(TEAM, BLOCK, SLOTS, MIX)                                                      \
+  WideShape {                                                                                       \
+    TEAM, BLOCK, SLOTS, MIX, (const void*)irkgl_wide_kernel<TEAM, BLOCK, SLOTS, MIX>,               \
+        wide_launch<TEAM, BLOCK, SLOTS, MIX>                                                        \
+  }
+#define IRKGL_WIDE(TEAM, BLOCK, SLOTS) IRKGL_WIDE_MIX(TEAM, BLOCK, SLOTS, 0)
 
 static const WideShape kWide[] = {
     IRKGL_WIDE(32, 128, 2),    // d <= 64, 4 instances per block
@@ -29,6 +26,12 @@ static const WideShape kWide[] = {
     IRKGL_WIDE(128, 128, 4),   // d <= 512
     IRKGL_WIDE(256, 256, 2),   // d <= 512
     IRKGL_WIDE(256, 256, 4),   // d <= 1024
+    // fixed-point stage mixing (IRKGL_OPT_MIX = 1)
+    IRKGL_WIDE_MIX(32, 128, 2, 1),
+    IRKGL_WIDE_MIX(64, 64, 4, 1),
+    IRKGL_WIDE_MIX(128, 128, 4, 1),
+    IRKGL_WIDE_MIX(256, 256, 2, 1),
+    IRKGL_WIDE_MIX(256, 256, 4, 1),
 };
 
 int wide_shapes(const WideShape** out) {

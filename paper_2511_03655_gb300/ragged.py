@@ -135,8 +135,9 @@ class RaggedRunner:
     is the comparator: one launch of the whole batch with one team size
     (``team`` = 0: the library's choice for the largest dimension)."""
 
-    def __init__(self, plan: RaggedPlan, params, q0, v0, device="cuda"):
+    def __init__(self, plan: RaggedPlan, params, q0, v0, device="cuda", mix: int = 0):
         self.plan = plan
+        self.mix = mix
         wp = plan.permuted()
         self.inst = irkgl.instances_tensor(wp, device)
         self.ninst = len(wp["kind"])
@@ -148,10 +149,10 @@ class RaggedRunner:
         self.ctx = {}
         self.streams = [torch.cuda.Stream(device=device) for _ in plan.buckets]
 
-    @staticmethod
-    def _ctx(team: int) -> int:
+    def _ctx(self, team: int) -> int:
         c = irkgl.irkgl_create(irkgl.RHS_HARMONIC, [1.0], 1, 0.1)
         irkgl.irkgl_set_option(c, irkgl.OPT_WIDE_TEAM, team)
+        irkgl.irkgl_set_option(c, irkgl.OPT_MIX, self.mix)
         return c
 
     def launches(self) -> int:

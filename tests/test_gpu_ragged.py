@@ -24,10 +24,10 @@ def small_batch(ninst=24, steps=200, nmax_body=20, nmax_chain=200):
     return workloads.uneven_batch(ninst=ninst, steps=steps, nmax_body=nmax_body, nmax_chain=nmax_chain)
 
 
-def run_gpu(torch, w, team=0, order=None):
+def run_gpu(torch, w, team=0, order=None, mix=0):
     from paper_2511_03655_gb300 import irkgl
     n = len(w["kind"])
-    integ = irkgl.Integrator(irkgl.RHS_HARMONIC, [1.0], 1, 0.1)  # context for tables/options
+    integ = irkgl.Integrator(irkgl.RHS_HARMONIC, [1.0], 1, 0.1, mix=mix)  # context for tables/options
     integ.set(irkgl.OPT_WIDE_TEAM, team)
     inst = irkgl.instances_tensor(w, "cuda")
     out = irkgl.RaggedOutputs.allocate(len(w["q0"]), n)
@@ -158,3 +158,25 @@ def test_bucketed_launches_equal_single_launch_bitwise(torch_cuda):
     for f in ("iters", "status"):
         assert np.array_equal(plan.unpermute(getattr(a, f).cpu().numpy()), getattr(ref, f).cpu().numpy()), f
     runner.close()
+
+
+def test_fixed_point_mixing_ragged(torch_cuda):
+    """IRKGL_OPT_MIX = 1 on the wide kernel: every instance against the
+    oracle (tolerances as above), and team shapes bitwise equal."""
+    w = small_batch(ninst=20, steps=150)
+    out = run_gpu(torch_cuda, w, mix=1)
+    q, v = out.q.cpu().numpy(), out.v.cpu().numpy()
+    st, it = out.status.cpu().numpy(), out.iters.cpu().numpy()
+    for k in range(len(w["kind"])):
+        r = oracle_instance(w, k)
+        o, d = int(w["offset"][k]), int(w["dim"][k])
+        assert st[k] == r["status"][0] == 0, k
+        g = np.concatenate([q[o:o + d], v[o:o + d]])
+        e = np.concatenate([r["q"][0], r["v"][0]])
+        assert np.abs(g - e).max() / np.abs(e).max() <= 1e-11, (k, int(w["kind"][k]), d)
+        assert abs(it[k] - r["iters_total"][0]) <= 0.1 * r["iters_total"][0] + 2, k
+    ref = run_gpu(torch_cuda, w, team=64, mix=1)
+    for team in (128, 256):
+        other = run_gpu(torch_cuda, w, team=team, mix=1)
+        for f in ("q", "v", "q_lo", "v_lo", "r_prev", "iters", "steps", "status"):
+            assert torch_cuda.equal(getattr(ref, f), getattr(other, f)), (team, f)
