@@ -91,6 +91,26 @@ def register_kernel_available(kind: str, params, dim: int) -> bool:
         irkgl.irkgl_destroy(ctx)
 
 
+def new_context(kind: str, params, dim: int, h: float, mix: int) -> int:
+    """A context for the register kernel of (kind, dim): with the fixed-point
+    stage mixing when mix = 1 and a kernel with it is compiled, else with the
+    FP64 mixing. The choice depends only on (kind, dim, mix), so the server
+    and run_plain integrate a request with the same kernel."""
+    ctx = irkgl.irkgl_create(KIND_IDS[kind], params, dim, h)
+    if mix:
+        irkgl.irkgl_set_option(ctx, irkgl.OPT_MIX, 1)
+        if irkgl.irkgl_get_tile(ctx) <= 0:
+            irkgl.irkgl_set_option(ctx, irkgl.OPT_MIX, 0)
+    return ctx
+
+
+def new_wide_context(mix: int) -> int:
+    """A context for the wide kernel (the kinds come per instance)."""
+    ctx = irkgl.irkgl_create(irkgl.RHS_HARMONIC, [1.0], 1, 1.0)
+    irkgl.irkgl_set_option(ctx, irkgl.OPT_MIX, 1 if mix else 0)
+    return ctx
+
+
 @dataclass
 class _Active:
     req: Request
@@ -155,14 +175,16 @@ class Server:
     """policy "fifo" admits waiting requests in arrival order; "sjf" admits
     the one with the least estimated work first (shortest job first), which
     lowers the median latency when many requests wait; max_active caps how
-    many requests share the GPU at once."""
+    many requests share the GPU at once. mix = 1 runs the fixed-point stage
+    mixing wherever a kernel with it is compiled (``new_context``)."""
 
     def __init__(self, mem_budget_bytes: int = 8 << 30, nstreams: int = 16,
                  chunk_traj_steps: float = 4e5, max_active: int = 512, device=None,
-                 policy: str = "fifo"):
+                 policy: str = "fifo", mix: int = 1):
         if policy not in ("fifo", "sjf"):
             raise ValueError(policy)
         self.policy = policy
+        self.mix = 1 if mix else 0
         self.budget = int(mem_budget_bytes)
         self.device = device or torch.device("cuda")
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(nstreams)]
@@ -216,7 +238,7 @@ class Server:
             h_first = float(hb[0])
             if wide:
                 a.ckey = ("wide",)
-                a.ctx = self._take_ctx(a.ckey, lambda: irkgl.irkgl_create(irkgl.RHS_HARMONIC, [1.0], 1, 1.0))
+                a.ctx = self._take_ctx(a.ckey, lambda: new_wide_context(self.mix))
                 w = {"kind": np.full(B, KIND_IDS[req.kind], np.int32), "dim": np.full(B, d, np.int32),
                      "offset": np.arange(B, dtype=np.int64) * d, "param_offset": np.zeros(B, np.int32),
                      "nparams": np.full(B, len(req.params), np.int32), "h": hb,
@@ -227,8 +249,8 @@ class Server:
                 # the step size comes per trajectory (a.h), so contexts of the
                 # same system are interchangeable
                 a.ckey = (req.kind, tuple(float(x) for x in req.params), d)
-                a.ctx = self._take_ctx(a.ckey, lambda: irkgl.irkgl_create(KIND_IDS[req.kind], req.params, d,
-                                                                         h_first))
+                a.ctx = self._take_ctx(a.ckey, lambda: new_context(req.kind, req.params, d, h_first,
+                                                                  self.mix))
         a.remaining = req.nsteps
         a.nbytes = req.device_bytes()
         req.t_admit = now
@@ -325,7 +347,7 @@ class Server:
         return stats
 
 
-def run_plain(requests: list[Request], time_scale: float = 1.0, device=None) -> ServeStats:
+def run_plain(requests: list[Request], time_scale: float = 1.0, device=None, mix: int = 1) -> ServeStats:
     """The plain per-request GPU form: one request at a time, in arrival order,
     each integrated by one launch on the default stream."""
     device = device or torch.device("cuda")
@@ -342,15 +364,16 @@ def run_plain(requests: list[Request], time_scale: float = 1.0, device=None) -> 
         v0 = torch.tensor(req.v0, dtype=torch.float64, device=device).reshape(B, d).contiguous()
         hb = np.ascontiguousarray(np.broadcast_to(np.asarray(req.h, dtype=np.float64), (B,)))
         if register_kernel_available(req.kind, req.params, d):
-            integ = irkgl.Integrator(KIND_IDS[req.kind], req.params, d, float(hb[0]))
-            out = integ.integrate(q0, v0, nsteps_all=req.nsteps,
+            ctx = new_context(req.kind, req.params, d, float(hb[0]), mix)
+            out = irkgl.Outputs.allocate(B, d, device=device)
+            irkgl.irkgl_integrate(ctx, d, q0, v0, out, nsteps_all=req.nsteps,
                                   h=torch.tensor(hb, dtype=torch.float64, device=device))
-            integ.close()
+            irkgl.irkgl_destroy(ctx)
             req.q, req.v = out.q.cpu().numpy(), out.v.cpu().numpy()
             req.dH_max, req.iters, req.status = (out.dH_max.cpu().numpy(), out.iters.cpu().numpy(),
                                                  out.status.cpu().numpy())
         else:
-            ctx = irkgl.irkgl_create(irkgl.RHS_HARMONIC, [1.0], 1, float(hb[0]))
+            ctx = new_wide_context(mix)
             w = {"kind": np.full(B, KIND_IDS[req.kind], np.int32), "dim": np.full(B, d, np.int32),
                  "offset": np.arange(B, dtype=np.int64) * d, "param_offset": np.zeros(B, np.int32),
                  "nparams": np.full(B, len(req.params), np.int32), "h": hb,

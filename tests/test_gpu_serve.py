@@ -43,13 +43,16 @@ def test_result_same_alone_and_in_mix(server_mod):
         assert np.array_equal(r.iters, a.iters) and np.array_equal(r.dH_max, a.dH_max)
 
 
-def test_mix_matches_single_launch(server_mod):
+@pytest.mark.parametrize("stage_mix", [0, 1])
+def test_mix_matches_single_launch(server_mod, stage_mix):
+    """Served in chunks among other requests, every request gets the bits of
+    one uninterrupted launch, with either stage mixing."""
     serve = server_mod
     descs = small_requests(8)
     mix = serve.make_requests(copy.deepcopy(descs))
-    serve.Server(nstreams=4, chunk_traj_steps=1e3).run(mix)
+    serve.Server(nstreams=4, chunk_traj_steps=1e3, mix=stage_mix).run(mix)
     plain = serve.make_requests(copy.deepcopy(descs))
-    serve.run_plain(plain)
+    serve.run_plain(plain, mix=stage_mix)
     for r, p in zip(mix, plain):
         assert np.array_equal(r.q, p.q) and np.array_equal(r.v, p.v), r.kind
         assert np.array_equal(r.iters, p.iters)
@@ -74,11 +77,12 @@ def test_admission_by_memory_budget(server_mod):
         assert np.array_equal(a.q, b.q)
 
 
-def test_served_results_match_oracle(server_mod):
+@pytest.mark.parametrize("stage_mix", [0, 1])
+def test_served_results_match_oracle(server_mod, stage_mix):
     serve = server_mod
     descs = [d for d in small_requests(20) if d["kind"] in ("kepler", "fput")][:4]
     reqs = serve.make_requests(copy.deepcopy(descs))
-    serve.Server(nstreams=4, chunk_traj_steps=1e3).run(reqs)
+    serve.Server(nstreams=4, chunk_traj_steps=1e3, mix=stage_mix).run(reqs)
     for r in reqs:
         kind = cbind.KEPLER if r.kind == "kepler" else cbind.FPUT
         o = cbind.run(kind, r.params, r.q0, r.v0, r.h, r.nsteps, nthreads=8)
