@@ -715,7 +715,7 @@ def run_serving_sweep(args):
                "offered_traj_steps_s": offered}
         for name, kw in (("fifo", dict(policy="fifo")), ("sjf", dict(policy="sjf", max_active=96))):
             reqs = serve.make_requests(copy.deepcopy(descs))
-            srv = serve.Server(nstreams=16, chunk_traj_steps=2e5, **kw)
+            srv = serve.Server(nstreams=16, chunk_traj_steps=2e5, mix=args.mix, **kw)
             st = srv.run(reqs).summary()
             srv.close()
             row[name] = {"p50_latency_s": st["p50_latency_s"], "p99_latency_s": st["p99_latency_s"],
@@ -798,8 +798,8 @@ def main():
     ns = torch.tensor(w["nsteps"], device=dev)
     hh = torch.tensor(w["h"], device=dev)
     od = torch.tensor(order, device=dev)
-    integ = irkgl.Integrator(kind, w["params"], dim, float(w["h"][0]), lanes_per_traj=args.lanes,
-                             mix=args.mix if args.workload == "kepler" else 0)
+    mix = args.mix if args.workload in ("kepler", "nbody6") else 0
+    integ = irkgl.Integrator(kind, w["params"], dim, float(w["h"][0]), lanes_per_traj=args.lanes, mix=mix)
     out = irkgl.Outputs.allocate(args.batch, dim, device=dev)
 
     # ---- FP64 roof: the library's FMA-chain probe, timed on this stream
@@ -867,8 +867,7 @@ def main():
         "config": {"workload": desc, "batch_per_gpu": args.batch,
                    "periods": args.periods if args.workload == "kepler" else None,
                    "lanes_per_traj": integ.tile, "tile_layout": integ.layout,
-                   "mixing": ("fixed-point (integer pipes)" if args.mix and args.workload == "kepler"
-                              else "FP64 FMA chain"),
+                   "mixing": "fixed-point (integer pipes)" if mix else "FP64 FMA chain",
                    "order": "natural" if args.no_order else "similarity (e descending)",
                    "l2": "state ~12.6 MB < L2; L2 flushed with a 256 MiB write before every timed step",
                    "parallelism": f"dp{world} (independent shards, no collective on the data path)"},
@@ -884,11 +883,11 @@ def main():
                                     "2 flops per FMA",
                      "kernel": ("irkgl_kernel_cs" if integ.layout == "component split" else "irkgl_kernel")
                                + f"<{args.workload}>", "flops_per_launch": flops_launch,
-                     "note": ("fixed-point stage mixing: the 288 mixing flops of each sweep (and the "
+                     "note": ("fixed-point stage mixing: the mixing flops of each sweep (and the "
                               "initial guess's) run as exact 128-bit integer multiply-adds on the "
                               "integer pipes, so the FP64 roof understates this kernel's ceiling and "
                               "frac can exceed 1; the FP64-pipe share measured by ncu is in profiles/")
-                             if args.mix and args.workload == "kepler" else None},
+                             if mix else None},
         "clocks": clk,
     }
 
@@ -993,15 +992,15 @@ def main():
         descs = workloads.serving_requests(n=args.serve_requests, rate=2000.0, batch_max=512,
                                            horizon_max=3000, nb_max=24, n_max=256)
         served = serve.make_requests(copy.deepcopy(descs))
-        srv = serve.Server(nstreams=16, chunk_traj_steps=2e5)
+        srv = serve.Server(nstreams=16, chunk_traj_steps=2e5, mix=args.mix)
         s1 = srv.run(served).summary()
         srv.close()
         sjf_r = serve.make_requests(copy.deepcopy(descs))
-        srv = serve.Server(nstreams=16, chunk_traj_steps=2e5, policy="sjf", max_active=96)
+        srv = serve.Server(nstreams=16, chunk_traj_steps=2e5, policy="sjf", max_active=96, mix=args.mix)
         s3 = srv.run(sjf_r).summary()
         srv.close()
         plain_r = serve.make_requests(copy.deepcopy(descs))
-        s2 = serve.run_plain(plain_r).summary()
+        s2 = serve.run_plain(plain_r, mix=args.mix).summary()
         same = all(np.array_equal(a.q, b.q) and np.array_equal(a.q, c.q)
                    for a, b, c in zip(served, plain_r, sjf_r))
         line["serving"] = {
@@ -1011,6 +1010,8 @@ def main():
             "continuous_batching": s1, "continuous_batching_sjf": s3, "plain_per_request": s2,
             "policies": "continuous_batching: arrival order, all requests share the GPU; "
                         "continuous_batching_sjf: least estimated work first, at most 96 at once",
+            "mixing": ("fixed-point where compiled (Kepler, Henon-Heiles, wide kernel), FP64 otherwise"
+                       if args.mix else "FP64 FMA chain"),
             "results_identical_to_plain": bool(same)}
 
     if rank == 0:

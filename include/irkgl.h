@@ -372,6 +372,14 @@ int irkgl_probe_fp64_fma(double* scratch, long long* fma_count, void* cuda_strea
  * IRKGL_ERR_CUDA. */
 int irkgl_diag_fixed_mix(const double* R, double* out, int n, void* cuda_stream);
 
+/* Diagnostic, not part of the method: the same sums as irkgl_diag_fixed_mix
+ * (same arguments, layout and errors), formed the way the stage-split tiles
+ * that spread the stage rows over several lanes form them: one 128-bit
+ * accumulator per row, a negative coefficient applied to the two's
+ * complement of the operand, and a per-row constant.  The results must equal
+ * irkgl_diag_fixed_mix's bit for bit. */
+int irkgl_diag_fixed_mix_rows(const double* R, double* out, int n, void* cuda_stream);
+
 /* Integration for callers that cannot allocate device memory.  (The paper
  * has no counterpart: this is a deployment entry point.)
  *

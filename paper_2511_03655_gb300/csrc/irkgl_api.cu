@@ -93,16 +93,19 @@ bool first_order_kind(int kind) {
   return kind == IRKGL_RHS_SCHWARZSCHILD || kind == IRKGL_RHS_HARMONIC1;
 }
 
-int default_lpt(int kind, int dim, int nst = 8) {
+int default_lpt(int kind, int dim, int nst = 8, int mix = 0) {
   // measured preferences: two lanes for the second-order kinds (Kepler
   // ensemble); four for the first-order ones (Schwarzschild: 128 registers,
-  // no spills, 10 % faster than two lanes)
+  // no spills, 10 % faster than two lanes); with the fixed-point mixing the
+  // one-lane tile (compile-time coefficient rows) where it is compiled, else
+  // one stage row per lane (N-body)
   const int prefs2[] = {2, 1, 8, 4};
+  const int prefs2_mix[] = {1, 8, 4, 2};
   const int prefs1[] = {4, 2, 1, 8};
   for (int i = 0; i < 4; i++) {
-    const int p = first_order_kind(kind) ? prefs1[i] : prefs2[i];
+    const int p = first_order_kind(kind) ? prefs1[i] : (mix ? prefs2_mix[i] : prefs2[i]);
     if (first_order_kind(kind) ? find_kernel1(kind, dim, p, 128, nst) != nullptr
-                               : find_kernel(kind, dim, p, 128) != nullptr)
+                               : find_kernel(kind, dim, p, 128, mix) != nullptr)
       return p;
   }
   return 0;
@@ -399,15 +402,16 @@ static bool time_dependent_kind(int kind) { return kind == IRKGL_RHS_HENON_HEILE
 // The tile a second-order call runs: the component-split tile (two lanes)
 // when requested, or by default with the fixed-point mixing where it is
 // compiled (the fastest form measured on GB300: 1.31x the one-lane tile);
-// the one-lane tile for the fixed-point mixing otherwise; else the
-// requested or default lanes per trajectory of the stage-split tiles.
+// else the requested or default lanes per trajectory of the stage-split
+// tiles (with the fixed-point mixing: one lane where compiled, else one
+// stage row per lane).
 static void resolve_tile(const irkgl_ctx* c, int* lpt, int* layout) {
   const bool cs_ok = find_kernel(c->kind, c->dim, 2, c->block, c->mix, 1) != nullptr;
   if (c->layout == 2 || (c->layout == 0 && c->mix && cs_ok)) {
     *lpt = 2;
     *layout = 1;
   } else {
-    *lpt = c->mix ? 1 : (c->lpt ? c->lpt : default_lpt(c->kind, c->dim));
+    *lpt = c->lpt ? c->lpt : default_lpt(c->kind, c->dim, 8, c->mix);
     *layout = 0;
   }
 }

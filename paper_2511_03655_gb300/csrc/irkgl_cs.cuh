@@ -142,10 +142,10 @@ __global__ void __launch_bounds__(BLOCK, MINB)
         const int emax = fixed_column(Rc, rb, nf);
 #pragma unroll
         for (int i = 0; i < S; i++) {
-          cvc[i] = cf.c[i] * vh;
+          // c_i v + T in one rounding (fixed-point tiles: no c_i v array)
           double T = fixed_row<true>(i, rb, emax);
           if (nf) T = __longlong_as_double(0x7ff8000000000000LL);
-          Qc[i] = fma(h, cvc[i] + T, qh);
+          Qc[i] = fma(h, fma(cf.c[i], vh, T), qh);
         }
       } else {
 #pragma unroll
@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(BLOCK, MINB)
             for (int i = 0; i < S; i++) {
               double T = fixed_row<false>(i, rb, emax);
               if (nf) T = __longlong_as_double(0x7ff8000000000000LL);
-              const double qn = fma(h, cvc[i] + T, qh);
+              const double qn = fma(h, fma(cf.c[i], vh, T), qh);
               dl = umax64(dl, abs_bits(qn - Qc[i]));
               Qc[i] = qn;
             }

@@ -23,6 +23,7 @@
 #include <stdint.h>
 
 #include <type_traits>
+#include <utility>
 
 #include "irkgl_tables.h"
 
@@ -126,11 +127,19 @@ __device__ __forceinline__ bool positive_normal(double x) {
 // x^(-3/2) = y0^3 (1 - e)^(-3/2) = y0^3 (1 + 3/2 e + 15/8 e^2 + O(e^3)),
 // the binomial series (a third-order Householder correction); truncation
 // error < 2^-57, so the result is within about one ulp.  6 FP64 operations.
+// Special operands are resolved from the bit pattern (no division or square
+// root subroutine, whose call would make the compiler keep stack space for
+// the registers live across it): +-0 and positive subnormals give +Inf (the
+// exact value exceeds the FP64 range), +Inf gives 0, negative and NaN give NaN.
+__device__ __forceinline__ double rinv3_special(double x) {
+  const unsigned long long bx = static_cast<unsigned long long>(__double_as_longlong(x));
+  if ((bx << 1) == 0ull || bx < 0x0010000000000000ULL) return __longlong_as_double(0x7ff0000000000000LL);
+  if (bx == 0x7ff0000000000000ULL) return 0.0;
+  return __longlong_as_double(0x7ff8000000000000LL);
+}
+
 __device__ __forceinline__ double rinv3(double x) {
-  if (!positive_normal(x)) {
-    // zero -> +Inf, Inf -> 0, negative/NaN -> NaN (rare; native path)
-    return 1.0 / (x * sqrt(x));
-  }
+  if (!positive_normal(x)) return rinv3_special(x);
   const double y0 = rsqrt_seed(x);
   const double y02 = y0 * y0;          // exact
   const double e = fma(-x, y02, 1.0);
@@ -141,13 +150,25 @@ __device__ __forceinline__ double rinv3(double x) {
 }
 
 // x^(-1/2) for x > 0, same seed: y0 (1 + e/2 + 3/8 e^2).  5 FP64 operations.
-__device__ __forceinline__ double rinv1(double x) {
-  if (!positive_normal(x)) return 1.0 / sqrt(x);
+__device__ __forceinline__ double rinv1_normal(double x) {
   const double y0 = rsqrt_seed(x);
   const double e = fma(-x, y0 * y0, 1.0);
   const double p = fma(e, 0.375, 0.5);
   const double t = e * p;
   return fma(y0, t, y0);
+}
+
+// Special operands from the bit pattern, as for rinv3: +0 -> +Inf, -0 -> -Inf,
+// a positive subnormal is scaled by 2^54 (exactly) and the result by 2^27,
+// +Inf -> 0, negative and NaN -> NaN.
+__device__ __forceinline__ double rinv1(double x) {
+  if (positive_normal(x)) return rinv1_normal(x);
+  const unsigned long long bx = static_cast<unsigned long long>(__double_as_longlong(x));
+  if (bx == 0ull) return __longlong_as_double(0x7ff0000000000000LL);
+  if (bx == 0x8000000000000000ULL) return __longlong_as_double(static_cast<long long>(0xfff0000000000000ULL));
+  if (bx < 0x0010000000000000ULL) return rinv1_normal(x * 18014398509481984.0) * 134217728.0;
+  if (bx == 0x7ff0000000000000ULL) return 0.0;
+  return __longlong_as_double(0x7ff8000000000000LL);
 }
 
 // (hi, lo) + x: Knuth's TwoSum of hi and x, error folded into lo, Dekker's
@@ -283,6 +304,50 @@ __device__ __forceinline__ double fixed_row(int i, const unsigned long long (&rb
   else sub128(P, irkgl_eta_bias(i, 0), irkgl_eta_bias(i, 1), irkgl_eta_bias(i, 2), irkgl_eta_bias(i, 3));
   constexpr int shift = IS_W ? IRKGL_W_SHIFT : IRKGL_ETA_SHIFT;
   return s128_to_double(P, emax - 1083 - shift);
+}
+
+// Row sums for tiles that hold one or two stage rows per lane (LPT > 1), where
+// the row index, and so each coefficient's sign, is known only at run time.
+// A negative coefficient multiplies the two's complement 2^64 - r'_j of the
+// operand (r'_j lies in [1, 2^62), so that is a positive 64-bit integer) and
+// the products share one accumulator; the extra n_ij 2^64 of each negative
+// entry is part of the row constant rbias_i.  The result is the same
+// correctly rounded exact sum as fixed_row's.
+struct FixedRowTables {
+  unsigned long long mag[2][S * S];  // [0] eta, [1] W: |coef| on the 2^-SHIFT grid
+  unsigned rbias[2][S * 4];          // per-row constants, 128-bit words
+  unsigned negbits[2][S];            // bit j: coefficient (i, j) is negative
+};
+constexpr FixedRowTables make_fixed_row_tables() {
+  FixedRowTables t{};
+  for (int k = 0; k < S * S; k++) {
+    t.mag[0][k] = irkgl_eta_mag(k);
+    t.mag[1][k] = irkgl_w_mag(k);
+    t.negbits[0][k / S] |= (irkgl_eta_neg(k) ? 1u : 0u) << (k % S);
+    t.negbits[1][k / S] |= (irkgl_w_neg(k) ? 1u : 0u) << (k % S);
+  }
+  for (int k = 0; k < S * 4; k++) {
+    t.rbias[0][k] = irkgl_eta_rbias(k / 4, k % 4);
+    t.rbias[1][k] = irkgl_w_rbias(k / 4, k % 4);
+  }
+  return t;
+}
+static __constant__ FixedRowTables kFixedRows = make_fixed_row_tables();
+
+// sum_j coef_ij R_j with the row's magnitudes mags[0..7], sign bits negbits
+// and constant rbias[0..3]; R_j as offset fixed point rb[j], exponent emax.
+template <int SHIFT>
+__device__ __forceinline__ double fixed_row_rt(const unsigned long long* mags, unsigned negbits,
+                                               const unsigned* rbias, const unsigned long long (&rb)[S],
+                                               int emax) {
+  U128 P{0u, 0u, 0u, 0u};
+#pragma unroll
+  for (int j = 0; j < S; j++) {
+    const unsigned long long m = 0ull - static_cast<unsigned long long>((negbits >> j) & 1u);
+    mac64(P, mags[j], (rb[j] ^ m) - m);
+  }
+  sub128(P, rbias[0], rbias[1], rbias[2], rbias[3]);
+  return s128_to_double(P, emax - 1083 - SHIFT);
 }
 
 // Offset fixed-point form of the eight R_j of one component; returns emax and
@@ -422,47 +487,89 @@ struct Harmonic {
 template <int SPL, int NB>
 struct NBody {
   static constexpr int D = 3 * NB;
-  double G, m[NB];
+  // G and the masses stay in (L1-cached) global memory: they enter only the
+  // per-step weights and the energy, and registers are the scarce resource
+  const double* prm;  // G, m_1..m_NB
   double w[SPL][NB];  // (h b_i) G m_b
-  __device__ void load_params(const double* p) {
-    G = p[0];
-#pragma unroll
-    for (int b = 0; b < NB; b++) m[b] = p[1 + b];
-  }
+  __device__ void load_params(const double* p) { prm = p; }
+  __device__ __forceinline__ double G() const { return __ldg(prm); }
+  __device__ __forceinline__ double m(int b) const { return __ldg(prm + 1 + b); }
   __device__ void set_step(const double (&hb)[SPL]) {
+    const double G0 = G();
 #pragma unroll
     for (int t = 0; t < SPL; t++)
 #pragma unroll
-      for (int b = 0; b < NB; b++) w[t][b] = (hb[t] * G) * m[b];
+      for (int b = 0; b < NB; b++) w[t][b] = (hb[t] * G0) * m(b);
+  }
+  // Pair P of (0,1), (0,2), ..., (0,NB-1), (1,2), ...: the pairs are expanded
+  // from an index sequence, so every array index is a compile-time constant
+  // (a triangular loop nest left the arrays in local memory for NB >= 5).
+  __host__ __device__ static constexpr int pair_first(int p) {
+    int a = 0;
+    while (p >= NB - 1 - a) {
+      p -= NB - 1 - a;
+      a++;
+    }
+    return a;
+  }
+  __host__ __device__ static constexpr int pair_second(int p) {
+    int a = 0;
+    while (p >= NB - 1 - a) {
+      p -= NB - 1 - a;
+      a++;
+    }
+    return a + 1 + p;
+  }
+  template <int P>
+  __device__ __forceinline__ void pair_R(int t, const double (&x)[D], double (&R)[D]) const {
+    constexpr int a = pair_first(P), b = pair_second(P);
+    const double dx = x[3 * b] - x[3 * a];
+    const double dy = x[3 * b + 1] - x[3 * a + 1];
+    const double dz = x[3 * b + 2] - x[3 * a + 2];
+    const double z = rinv3(fma(dx, dx, fma(dy, dy, dz * dz)));
+    const double wb = w[t][b] * z, wa = w[t][a] * z;
+    R[3 * a] = fma(wb, dx, R[3 * a]);
+    R[3 * a + 1] = fma(wb, dy, R[3 * a + 1]);
+    R[3 * a + 2] = fma(wb, dz, R[3 * a + 2]);
+    R[3 * b] = fma(-wa, dx, R[3 * b]);
+    R[3 * b + 1] = fma(-wa, dy, R[3 * b + 1]);
+    R[3 * b + 2] = fma(-wa, dz, R[3 * b + 2]);
+  }
+  template <int... P>
+  __device__ __forceinline__ void pairs_R(int t, const double (&x)[D], double (&R)[D],
+                                          std::integer_sequence<int, P...>) const {
+    (pair_R<P>(t, x, R), ...);
   }
   __device__ __forceinline__ void stage_R(int t, const double (&x)[D], double (&R)[D]) const {
 #pragma unroll
     for (int l = 0; l < D; l++) R[l] = 0.0;
-#pragma unroll
-    for (int a = 0; a < NB; a++)
-#pragma unroll
-      for (int b = a + 1; b < NB; b++) {
-        const double dx = x[3 * b] - x[3 * a];
-        const double dy = x[3 * b + 1] - x[3 * a + 1];
-        const double dz = x[3 * b + 2] - x[3 * a + 2];
-        const double z = rinv3(fma(dx, dx, fma(dy, dy, dz * dz)));
-        const double wb = w[t][b] * z, wa = w[t][a] * z;
-        R[3 * a] = fma(wb, dx, R[3 * a]);
-        R[3 * a + 1] = fma(wb, dy, R[3 * a + 1]);
-        R[3 * a + 2] = fma(wb, dz, R[3 * a + 2]);
-        R[3 * b] = fma(-wa, dx, R[3 * b]);
-        R[3 * b + 1] = fma(-wa, dy, R[3 * b + 1]);
-        R[3 * b + 2] = fma(-wa, dz, R[3 * b + 2]);
-      }
+    pairs_R(t, x, R, std::make_integer_sequence<int, NB * (NB - 1) / 2>{});
   }
   // The share of H computed by lane r of a group of L lanes: pairs
   // p = r, r + L, ... (of the NB (NB-1)/2) and the kinetic energy of bodies
-  // a = r, r + L, ...; the group sums the shares.
+  // a = r, r + L, ...; the group sums the shares.  Bodies indexed at run time
+  // are picked from the register arrays by unrolled selects (no local-memory
+  // copies of q, v or m).
   static constexpr bool kSplitH = true;
-  __device__ double H_part(int r, int L, const double* q, const double* v) const {
+  __device__ static __forceinline__ void pick3(const double (&x)[D], int a, double& x0, double& x1,
+                                               double& x2) {
+    x0 = x[0];
+    x1 = x[1];
+    x2 = x[2];
+#pragma unroll
+    for (int u = 1; u < NB; u++) {
+      x0 = (a == u) ? x[3 * u] : x0;
+      x1 = (a == u) ? x[3 * u + 1] : x1;
+      x2 = (a == u) ? x[3 * u + 2] : x2;
+    }
+  }
+  __device__ double H_part(int r, int L, const double (&q)[D], const double (&v)[D]) const {
     double acc = 0.0;
-    for (int a = r; a < NB; a += L)
-      acc = fma(0.5 * m[a], fma(v[3 * a], v[3 * a], fma(v[3 * a + 1], v[3 * a + 1], v[3 * a + 2] * v[3 * a + 2])), acc);
+    for (int a = r; a < NB; a += L) {
+      double v0, v1, v2;
+      pick3(v, a, v0, v1, v2);
+      acc = fma(0.5 * m(a), fma(v0, v0, fma(v1, v1, v2 * v2)), acc);
+    }
     constexpr int NP = NB * (NB - 1) / 2;
     double pot = 0.0;
     for (int p = r; p < NP; p += L) {
@@ -472,18 +579,21 @@ struct NBody {
         a++;
       }
       b += a + 1;
-      const double dx = q[3 * b] - q[3 * a];
-      const double dy = q[3 * b + 1] - q[3 * a + 1];
-      const double dz = q[3 * b + 2] - q[3 * a + 2];
-      pot = fma(m[a] * m[b], rinv1(fma(dx, dx, fma(dy, dy, dz * dz))), pot);
+      double xa, ya, za, xb, yb, zb;
+      pick3(q, a, xa, ya, za);
+      pick3(q, b, xb, yb, zb);
+      const double dx = xb - xa;
+      const double dy = yb - ya;
+      const double dz = zb - za;
+      pot = fma(m(a) * m(b), rinv1(fma(dx, dx, fma(dy, dy, dz * dz))), pot);
     }
-    return fma(-G, pot, acc);
+    return fma(-G(), pot, acc);
   }
   __device__ double H(const double (&q)[D], const double (&v)[D]) const {
     double kin = 0.0, pot = 0.0;
 #pragma unroll
     for (int a = 0; a < NB; a++)
-      kin = fma(0.5 * m[a], fma(v[3 * a], v[3 * a], fma(v[3 * a + 1], v[3 * a + 1], v[3 * a + 2] * v[3 * a + 2])), kin);
+      kin = fma(0.5 * m(a), fma(v[3 * a], v[3 * a], fma(v[3 * a + 1], v[3 * a + 1], v[3 * a + 2] * v[3 * a + 2])), kin);
 #pragma unroll
     for (int a = 0; a < NB; a++)
 #pragma unroll
@@ -491,9 +601,9 @@ struct NBody {
         const double dx = q[3 * b] - q[3 * a];
         const double dy = q[3 * b + 1] - q[3 * a + 1];
         const double dz = q[3 * b + 2] - q[3 * a + 2];
-        pot = fma(m[a] * m[b], rinv1(fma(dx, dx, fma(dy, dy, dz * dz))), pot);
+        pot = fma(m(a) * m(b), rinv1(fma(dx, dx, fma(dy, dy, dz * dz))), pot);
       }
-    return fma(-G, pot, kin);
+    return fma(-G(), pot, kin);
   }
 };
 
@@ -565,16 +675,27 @@ __device__ __forceinline__ double select_own(const double (&arr)[D], int s, int 
 template <class Rhs, int LPT, int BLOCK, int MIX = 0, int MINB = 1>
 __global__ void __launch_bounds__(BLOCK, MINB)
     irkgl_kernel(const __grid_constant__ KArgs a, const __grid_constant__ Coef cf) {
-  static_assert(MIX == 0 || LPT == 1, "fixed-point mixing needs all stages in one lane");
   constexpr int D = Rhs::D;
   constexpr int SPL = S / LPT;
   constexpr int NS = (D + LPT - 1) / LPT;  // owned component slots per lane
   constexpr int PAD = S + 1;               // padded smem row (bank spread)
   constexpr bool TIMED = time_dependent<Rhs>::value;
+  // fixed-point mixing with the stage rows spread over the lanes: integer
+  // coefficient rows in shared memory (fixed_row_rt)
+  constexpr bool FIXED_RT = (MIX == 1) && (LPT > 1);
 
-  __shared__ double s_eta[(LPT > 1) ? S * PAD : 1];
-  __shared__ double s_W[(LPT > 1) ? S * PAD : 1];
-  if constexpr (LPT > 1) {
+  __shared__ double s_eta[(LPT > 1 && !FIXED_RT) ? S * PAD : 1];
+  __shared__ double s_W[(LPT > 1 && !FIXED_RT) ? S * PAD : 1];
+  __shared__ unsigned long long s_fmag[FIXED_RT ? 2 * S * PAD : 1];
+  __shared__ __align__(16) unsigned s_fbias[FIXED_RT ? 2 * S * 4 : 1];
+  if constexpr (FIXED_RT) {
+    for (int x = threadIdx.x; x < 2 * S * S; x += BLOCK) {
+      const int tab = x / (S * S), k = x % (S * S);
+      s_fmag[tab * S * PAD + (k / S) * PAD + (k % S)] = kFixedRows.mag[tab][k];
+    }
+    for (int x = threadIdx.x; x < 2 * S * 4; x += BLOCK) s_fbias[x] = kFixedRows.rbias[x / (S * 4)][x % (S * 4)];
+    __syncthreads();
+  } else if constexpr (LPT > 1) {
     for (int x = threadIdx.x; x < S * S; x += BLOCK) {
       s_eta[(x / S) * PAD + (x % S)] = cf.eta[x];
       s_W[(x / S) * PAD + (x % S)] = cf.W[x];
@@ -597,6 +718,12 @@ __global__ void __launch_bounds__(BLOCK, MINB)
   double cc[SPL];
 #pragma unroll
   for (int t = 0; t < SPL; t++) cc[t] = cf.c[i0 + t];
+  unsigned neg_eta[SPL], neg_W[SPL];  // sign bits of the lane's rows (FIXED_RT)
+#pragma unroll
+  for (int t = 0; t < SPL; t++) {
+    neg_eta[t] = FIXED_RT ? kFixedRows.negbits[0][i0 + t] : 0u;
+    neg_W[t] = FIXED_RT ? kFixedRows.negbits[1][i0 + t] : 0u;
+  }
 
   // Per-trajectory state.  Component l of q and v (hi and lo parts) and its
   // stopping-rule history live only on lane l % LPT of the group (slot
@@ -608,6 +735,22 @@ __global__ void __launch_bounds__(BLOCK, MINB)
   double R[SPL][D];           // own stages' R (Rprev between steps)
   double Q[SPL][D];           // own stages' values
   double cv[SPL][D];          // c_i v
+  // The eight R_j of component l in offset fixed point with their shared
+  // exponent: each lane converts its own stages after the group has agreed on
+  // the largest exponent, then gathers the others' (FIXED_RT).
+  auto gather_fixed = [&](int l, unsigned mask, unsigned long long (&rb)[S]) -> int {
+    int e = 0;
+#pragma unroll
+    for (int t = 0; t < SPL; t++) e = max(e, biased_exp(R[t][l]));
+#pragma unroll
+    for (int off = 1; off < LPT; off <<= 1) e = max(e, __shfl_xor_sync(mask, e, off));
+    unsigned long long own[SPL];
+#pragma unroll
+    for (int t = 0; t < SPL; t++) own[t] = to_fixed_offset(R[t][l], e);
+#pragma unroll
+    for (int j = 0; j < S; j++) rb[j] = __shfl_sync(mask, own[j % SPL], gbase + j / SPL);
+    return e;
+  };
   double h = 0.0, H0 = 0.0, invH0 = 0.0, dHmax = 0.0;
   double Hprev = 0.0, invHprev = 0.0;  // local-error monitor
   long long n = 0, N = 0, itot = 0;
@@ -718,7 +861,17 @@ __global__ void __launch_bounds__(BLOCK, MINB)
       for (int l = 0; l < D; l++) {
         const double vlv = owned_get<LPT, NS>(vh, l, stepmask, gbase);
         const double qlv = owned_get<LPT, NS>(qh, l, stepmask, gbase);
-        if constexpr (MIX == 1) {
+        if constexpr (FIXED_RT) {
+          unsigned long long rb[S];
+          const int emax = gather_fixed(l, stepmask, rb);
+#pragma unroll
+          for (int t = 0; t < SPL; t++) {
+            double T = fixed_row_rt<IRKGL_W_SHIFT>(&s_fmag[S * PAD + (i0 + t) * PAD], neg_W[t],
+                                                   &s_fbias[S * 4 + (i0 + t) * 4], rb, emax);
+            if (emax == 0x7ff) T = __longlong_as_double(0x7ff8000000000000LL);
+            Q[t][l] = fma(h, fma(cc[t], vlv, T), qlv);
+          }
+        } else if constexpr (MIX == 1) {
           double Rc[S];
 #pragma unroll
           for (int j = 0; j < S; j++) Rc[j] = R[j][l];
@@ -727,10 +880,9 @@ __global__ void __launch_bounds__(BLOCK, MINB)
           const int emax = fixed_column(Rc, rb, nf);
 #pragma unroll
           for (int t = 0; t < SPL; t++) {
-            cv[t][l] = cc[t] * vlv;
             double T = fixed_row<true>(t, rb, emax);
             if (nf) T = __longlong_as_double(0x7ff8000000000000LL);
-            Q[t][l] = fma(h, cv[t][l] + T, qlv);
+            Q[t][l] = fma(h, fma(cc[t], vlv, T), qlv);
           }
         } else {
           double acc[SPL];
@@ -773,7 +925,19 @@ __global__ void __launch_bounds__(BLOCK, MINB)
           for (int l = 0; l < D; l++) {
             const double qlv = owned_get<LPT, NS>(qh, l, sweepmask, gbase);
             double acc[SPL];
-            if constexpr (MIX == 1) {
+            if constexpr (FIXED_RT) {
+              // c_i v + T in one rounding (the fixed-point tiles keep no c_i v array)
+              const double vlv = owned_get<LPT, NS>(vh, l, sweepmask, gbase);
+              unsigned long long rb[S];
+              const int emax = gather_fixed(l, sweepmask, rb);
+#pragma unroll
+              for (int t = 0; t < SPL; t++) {
+                double T = fixed_row_rt<IRKGL_ETA_SHIFT>(&s_fmag[(i0 + t) * PAD], neg_eta[t],
+                                                         &s_fbias[(i0 + t) * 4], rb, emax);
+                if (emax == 0x7ff) T = __longlong_as_double(0x7ff8000000000000LL);
+                acc[t] = fma(cc[t], vlv, T);
+              }
+            } else if constexpr (MIX == 1) {
               double Rc[S];
 #pragma unroll
               for (int j = 0; j < S; j++) Rc[j] = R[j][l];
@@ -784,7 +948,7 @@ __global__ void __launch_bounds__(BLOCK, MINB)
               for (int t = 0; t < SPL; t++) {
                 double T = fixed_row<false>(t, rb, emax);
                 if (nf) T = __longlong_as_double(0x7ff8000000000000LL);
-                acc[t] = cv[t][l] + T;
+                acc[t] = fma(cc[t], owned_get<LPT, NS>(vh, l, sweepmask, gbase), T);
               }
             } else {
 #pragma unroll
@@ -845,31 +1009,60 @@ __global__ void __launch_bounds__(BLOCK, MINB)
 
       const unsigned okmask = __ballot_sync(stepmask, st == ST_OK);
       if (st == ST_OK) {
-        // update (Eq. qnvn2): sums over the stages, butterflied over the group
-        double sR[D], scR[D];
+        // update (Eq. qnvn2): sums over the stages.  Each lane sums its own
+        // stages; the group then reduce-scatters the partial sums so that
+        // each lane ends with the totals of the components it owns.  Column c
+        // of the lane's partials holds components c, c + LPT, c + 2 LPT, ...
+        // (zero past D).  At the level with offset off a lane holds the
+        // columns that agree with its rank below bit off, keeps the half
+        // whose bit off matches its own, sends the other half to lane
+        // r ^ off and adds what it receives: own + partner, in the order of a
+        // butterfly over xor offsets 1, 2, 4, so the totals are the ones every
+        // lane of a full butterfly would form, with (LPT - 1) NS additions per
+        // sum instead of D log2(LPT).
+        double sx[LPT][NS], sy[LPT][NS];
 #pragma unroll
-        for (int l = 0; l < D; l++) {
-          double x = R[0][l], y = cc[0] * R[0][l];
+        for (int c = 0; c < LPT; c++)
 #pragma unroll
-          for (int t = 1; t < SPL; t++) {
-            x = x + R[t][l];
-            y = fma(cc[t], R[t][l], y);
+          for (int s = 0; s < NS; s++) {
+            const int l = c + LPT * s;
+            if (l < D) {
+              double x = R[0][l], y = cc[0] * R[0][l];
+#pragma unroll
+              for (int t = 1; t < SPL; t++) {
+                x = x + R[t][l];
+                y = fma(cc[t], R[t][l], y);
+              }
+              sx[c][s] = x;
+              sy[c][s] = y;
+            } else {
+              sx[c][s] = 0.0;
+              sy[c][s] = 0.0;
+            }
           }
 #pragma unroll
-          for (int off = 1; off < LPT; off <<= 1) {
-            x = x + __shfl_xor_sync(okmask, x, off);
-            y = y + __shfl_xor_sync(okmask, y, off);
-          }
-          sR[l] = x;
-          scR[l] = y;
+        for (int lev = 0; (1 << lev) < LPT; lev++) {
+          const int off = 1 << lev;
+          const bool upper = (r & off) != 0;  // keep the odd member of each pair
+#pragma unroll
+          for (int u = 0; u < (LPT >> lev) / 2; u++)
+#pragma unroll
+            for (int s = 0; s < NS; s++) {
+              const double kx = upper ? sx[2 * u + 1][s] : sx[2 * u][s];
+              const double gx = upper ? sx[2 * u][s] : sx[2 * u + 1][s];
+              const double ky = upper ? sy[2 * u + 1][s] : sy[2 * u][s];
+              const double gy = upper ? sy[2 * u][s] : sy[2 * u + 1][s];
+              sx[u][s] = kx + __shfl_xor_sync(okmask, gx, off);
+              sy[u][s] = ky + __shfl_xor_sync(okmask, gy, off);
+            }
         }
         // compensated update of the owned components l = s*LPT + r
 #pragma unroll
         for (int s = 0; s < NS; s++) {
           if (s * LPT + r < D) {
-            two_sum_add(vh[s], vl[s], select_own<LPT, D>(sR, s, r));
+            two_sum_add(vh[s], vl[s], sx[0][s]);
             // dq = h v_hi + (h v_lo - h sum c_i R_i)
-            const double dq = fma(h, vh[s], fma(h, vl[s], -(h * select_own<LPT, D>(scR, s, r))));
+            const double dq = fma(h, vh[s], fma(h, vl[s], -(h * sy[0][s])));
             two_sum_add(qh[s], ql[s], dq);
           }
         }

@@ -284,6 +284,18 @@ __host__ __device__ constexpr unsigned irkgl_eta_bias(int i, int w) {
     0x00000000u, 0x00000000u, 0xd337a3adu, 0x3d88091au};
   return t[i * 4 + w];
 }
+__host__ __device__ constexpr unsigned irkgl_eta_rbias(int i, int w) {
+  constexpr unsigned t[32] = {
+    0x00000000u, 0x00000000u, 0x9aa3438du, 0x00ce5444u,
+    0x00000000u, 0x00000000u, 0x1ea37e80u, 0x02635fe0u,
+    0x00000000u, 0x00000000u, 0x22cce174u, 0x06e4effdu,
+    0x00000000u, 0x00000000u, 0xf8507540u, 0x0efa443eu,
+    0x00000000u, 0x00000000u, 0x80781a40u, 0x1a9798e7u,
+    0x00000000u, 0x00000000u, 0x8e95f8b4u, 0x27ee253au,
+    0x00000000u, 0x00000000u, 0x65fca0c0u, 0x34b521c9u,
+    0x00000000u, 0x00000000u, 0xd337a3adu, 0x3d88091au};
+  return t[i * 4 + w];
+}
 __host__ __device__ constexpr unsigned long long irkgl_w_mag(int k) {
   constexpr unsigned long long t[64] = {
     0x0000007c2d0d46caull, 0x000000aecaa86a0eull, 0x000000be44c4fb79ull, 0x000000a9df34077aull, 0x000000652b422ca6ull, 0x00000033bc93b26eull, 0x0000019f113614f5ull, 0x00000698b551c999ull,
@@ -307,6 +319,18 @@ __host__ __device__ constexpr unsigned irkgl_w_bias(int i, int w) {
     0x00000000u, 0x00000000u, 0x851780a8u, 0x00852432u,
     0x00000000u, 0x00000000u, 0x354bd4a0u, 0x013a11beu,
     0x00000000u, 0x00000000u, 0x65bb4f00u, 0x01f90f18u};
+  return t[i * 4 + w];
+}
+__host__ __device__ constexpr unsigned irkgl_w_rbias(int i, int w) {
+  constexpr unsigned t[32] = {
+    0x00000000u, 0x60000000u, 0x458f730bu, 0x000003a6u,
+    0x00000000u, 0xe0000000u, 0x061206d9u, 0x00019812u,
+    0x00000000u, 0x20000000u, 0xd907ad1eu, 0x00246176u,
+    0x00000000u, 0x40000000u, 0x5fd19f7bu, 0x01bd0efau,
+    0x00000000u, 0x00000000u, 0xc7c8ce06u, 0x0c784bbeu,
+    0x00000000u, 0x00000000u, 0x2986bd68u, 0x367fe150u,
+    0x00000000u, 0x00000000u, 0x656f91a0u, 0x94c6d34eu,
+    0x00000000u, 0x00000000u, 0xe6d60900u, 0x0263efa9u};
   return t[i * 4 + w];
 }
 __host__ __device__ constexpr unsigned long long irkgl_mu_mag(int k) {
@@ -334,6 +358,18 @@ __host__ __device__ constexpr unsigned irkgl_mu_bias(int i, int w) {
     0x00000000u, 0x00000000u, 0x59adccc0u, 0x3c77ed0au};
   return t[i * 4 + w];
 }
+__host__ __device__ constexpr unsigned irkgl_mu_rbias(int i, int w) {
+  constexpr unsigned t[32] = {
+    0x00000000u, 0x00000000u, 0x80058f40u, 0x0b7d03efu,
+    0x00000000u, 0x00000000u, 0x2fce1040u, 0x148362bdu,
+    0x00000000u, 0x00000000u, 0xe649d340u, 0x1c2e3622u,
+    0x00000000u, 0x00000000u, 0xd14a2ac0u, 0x239b2a49u,
+    0x00000000u, 0x00000000u, 0xe4530540u, 0x2b1be0fbu,
+    0x00000000u, 0x00000000u, 0x2880bcc0u, 0x31b33136u,
+    0x00000000u, 0x00000000u, 0x34e7d7c0u, 0x3908e92au,
+    0x00000000u, 0x00000000u, 0x59adccc0u, 0x3c77ed0au};
+  return t[i * 4 + w];
+}
 __host__ __device__ constexpr unsigned long long irkgl_nu_mag(int k) {
   constexpr unsigned long long t[64] = {
     0x00000304af05335dull, 0x000004cee5e85265ull, 0x000006b2263255e8ull, 0x0000093c4f7f2a07ull, 0x00000d455a464894ull, 0x000014d7d24c5f3dull, 0x000026b318d27721ull, 0x0000624cb581af54ull,
@@ -357,5 +393,17 @@ __host__ __device__ constexpr unsigned irkgl_nu_bias(int i, int w) {
     0x00000000u, 0x00000000u, 0xf46b61e0u, 0x006f7d33u,
     0x00000000u, 0x00000000u, 0xa65b6f10u, 0x00eb2347u,
     0x00000000u, 0x00000000u, 0x3aae7080u, 0x01638a34u};
+  return t[i * 4 + w];
+}
+__host__ __device__ constexpr unsigned irkgl_nu_rbias(int i, int w) {
+  constexpr unsigned t[32] = {
+    0x00000000u, 0x60000000u, 0x56ecf13au, 0x0000469fu,
+    0x00000000u, 0xc0000000u, 0x03d2aaeeu, 0x00064ae0u,
+    0x00000000u, 0xc0000000u, 0xf3268617u, 0x00510235u,
+    0x00000000u, 0x40000000u, 0xad204e44u, 0x02aba028u,
+    0x00000000u, 0x00000000u, 0x9598d6f2u, 0x0ec42df8u,
+    0x00000000u, 0x00000000u, 0xe46bb260u, 0x35ae0bdcu,
+    0x00000000u, 0x00000000u, 0x16bf5690u, 0x81ba078fu,
+    0x00000000u, 0x00000000u, 0x72e23680u, 0xd2e7fd33u};
   return t[i * 4 + w];
 }

@@ -19,6 +19,10 @@ const ::irkgl::KernelEntry kEntries[] = {
     IRKGL_ENTRY(IRKGL_RHS_KEPLER, 2, ::irkgl::Kepler<1>, 8, 128),
     IRKGL_ENTRY_CS(IRKGL_RHS_KEPLER, ::irkgl::Kepler<4>, 128, 0, 1),
     IRKGL_ENTRY_CS(IRKGL_RHS_KEPLER, ::irkgl::Kepler<4>, 128, 1, 1),
+    // fixed-point mixing with the stage rows spread over 2 and 8 lanes (the
+    // N-body tiles' form; here for bitwise checks against the one-lane tile)
+    IRKGL_ENTRY_MIX(IRKGL_RHS_KEPLER, 2, ::irkgl::Kepler<4>, 2, 128, 1),
+    IRKGL_ENTRY_MIX(IRKGL_RHS_KEPLER, 2, ::irkgl::Kepler<1>, 8, 128, 1),
 };
 }  // namespace
 

@@ -13,6 +13,11 @@ const ::irkgl::KernelEntry kEntries[] = {
     IRKGL_ENTRY(IRKGL_RHS_NBODY, 12, NB4, 8, 128),
     IRKGL_ENTRY(IRKGL_RHS_NBODY, 15, NB5, 8, 128),
     IRKGL_ENTRY(IRKGL_RHS_NBODY, 18, NB6, 8, 128),
+    // fixed-point stage mixing, one stage row per lane
+    IRKGL_ENTRY_MIX(IRKGL_RHS_NBODY, 9, NB3, 8, 128, 1),
+    IRKGL_ENTRY_MIX(IRKGL_RHS_NBODY, 12, NB4, 8, 128, 1),
+    IRKGL_ENTRY_MIX(IRKGL_RHS_NBODY, 15, NB5, 8, 128, 1),
+    IRKGL_ENTRY_MIX(IRKGL_RHS_NBODY, 18, NB6, 8, 128, 1),
 };
 }  // namespace
 

@@ -163,14 +163,21 @@ R_BIAS = 61      # fixed-point R values are offset by 2^61 to make them non-nega
 
 def int_tables(t):
     """Integer forms for the fixed-point mixing: magnitudes, signs and the
-    per-row correction sum_j (+-n_ij) 2^R_BIAS that removes the offset."""
+    per-row correction sum_j (+-n_ij) 2^R_BIAS that removes the offset.
+
+    rbias is the correction for rows whose signs are only known at run time
+    (one stage row per lane): there a negative coefficient multiplies the
+    two's complement 2^64 - r'_j of the operand instead of going to a second
+    accumulator, which adds n_ij 2^64 per negative entry; rbias_i =
+    bias_i + 2^64 sum_{j: eta_ij < 0} n_ij, taken mod 2^128."""
     out = {}
     for name, shift, exact in (("ETA", ETA_SHIFT, True), ("W", W_SHIFT, False),
                                ("MU", MU_SHIFT, True), ("NU", NU_SHIFT, False)):
-        mags, negs, bias = [], [], []
+        mags, negs, bias, rbias = [], [], [], []
         key = {"ETA": "eta", "W": "W", "MU": "mu", "NU": "nu"}[name]
         for i in range(S):
             row_sum = 0
+            neg_sum = 0
             for j in range(S):
                 x = Fraction(t[key][i][j]) * (1 << shift)
                 if exact:
@@ -183,8 +190,10 @@ def int_tables(t):
                 mags.append(m)
                 negs.append(1 if neg else 0)
                 row_sum += -m if neg else m
+                neg_sum += m if neg else 0
             bias.append(row_sum * (1 << R_BIAS))
-        out[name] = (mags, negs, bias)
+            rbias.append(row_sum * (1 << R_BIAS) + (neg_sum << 64))
+        out[name] = (mags, negs, bias, rbias)
     return out
 
 
@@ -198,21 +207,22 @@ def _render_int(t) -> str:
              f"#define IRKGL_MU_SHIFT {MU_SHIFT}", f"#define IRKGL_NU_SHIFT {NU_SHIFT}",
              f"#define IRKGL_R_BIAS {R_BIAS}"]
     for name in ("ETA", "W", "MU", "NU"):
-        mags, negs, bias = it[name]
+        mags, negs, bias, rbias = it[name]
         lines.append(f"__host__ __device__ constexpr unsigned long long irkgl_{name.lower()}_mag(int k) {{")
         lines.append("  constexpr unsigned long long t[64] = {")
         lines.append("    " + ",\n    ".join(", ".join(f"0x{m:016x}ull" for m in mags[r * 8:(r + 1) * 8]) for r in range(8)).replace("\\n", "\n") + "};")
         lines.append("  return t[k];\n}")
         negmask = sum(1 << k for k, v in enumerate(negs) if v)
         lines.append(f"__host__ __device__ constexpr bool irkgl_{name.lower()}_neg(int k) {{ return (0x{negmask:016x}ull >> k) & 1ull; }}")
-        words = []
-        for b in bias:
-            v = b % (1 << 128)
-            words.append([(v >> (32 * w)) & 0xffffffff for w in range(4)])
-        lines.append(f"__host__ __device__ constexpr unsigned irkgl_{name.lower()}_bias(int i, int w) {{")
-        lines.append("  constexpr unsigned t[32] = {")
-        lines.append("    " + ",\n    ".join(", ".join(f"0x{x:08x}u" for x in ws) for ws in words).replace("\\n", "\n") + "};")
-        lines.append("  return t[i * 4 + w];\n}")
+        for fn, rows in (("bias", bias), ("rbias", rbias)):
+            words = []
+            for b in rows:
+                v = b % (1 << 128)
+                words.append([(v >> (32 * w)) & 0xffffffff for w in range(4)])
+            lines.append(f"__host__ __device__ constexpr unsigned irkgl_{name.lower()}_{fn}(int i, int w) {{")
+            lines.append("  constexpr unsigned t[32] = {")
+            lines.append("    " + ",\n    ".join(", ".join(f"0x{x:08x}u" for x in ws) for ws in words).replace("\\n", "\n") + "};")
+            lines.append("  return t[i * 4 + w];\n}")
     return "\n".join(lines) + "\n"
 
 

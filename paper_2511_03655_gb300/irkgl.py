@@ -36,7 +36,8 @@ EXPORTS = ("irkgl_default_coeffs", "irkgl_create", "irkgl_set_option", "irkgl_st
            "irkgl_integrate", "irkgl_integrate_host", "irkgl_destroy", "irkgl_strerror",
            "irkgl_last_cuda_error", "irkgl_get_tile", "irkgl_probe_fp64_fma",
            "irkgl_integrate_noalloc", "irkgl_integrate_ragged", "irkgl_advance",
-           "irkgl_advance_ragged", "irkgl_diag_fixed_mix")
+           "irkgl_advance_ragged", "irkgl_diag_fixed_mix",
+           "irkgl_diag_fixed_mix_rows")
 NOALLOC_MAX_PARAMS = 63
 
 _P = ctypes.c_void_p
@@ -115,6 +116,7 @@ def load(path: str | None = None, build_if_missing: bool = False):
                                 ctypes.c_int, _P]
     L.irkgl_advance_t.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int, _P]
     L.irkgl_diag_fixed_mix.argtypes = [_P, _P, ctypes.c_int, _P]
+    L.irkgl_diag_fixed_mix_rows.argtypes = [_P, _P, ctypes.c_int, _P]
     L.irkgl_advance_ragged.argtypes = [_P, _P, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P, _P,
                                        _P, _P, ctypes.c_int, _P, _P, _P, _P]
     L.irkgl_integrate_ragged.argtypes = [_P, _P, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P,
@@ -125,7 +127,8 @@ def load(path: str | None = None, build_if_missing: bool = False):
     for name in ("irkgl_default_coeffs", "irkgl_create", "irkgl_set_option", "irkgl_step",
                  "irkgl_integrate", "irkgl_integrate_host", "irkgl_get_tile",
                  "irkgl_probe_fp64_fma", "irkgl_integrate_noalloc", "irkgl_integrate_ragged",
-                 "irkgl_advance", "irkgl_advance_ragged", "irkgl_diag_fixed_mix"):
+                 "irkgl_advance", "irkgl_advance_ragged", "irkgl_diag_fixed_mix",
+                 "irkgl_diag_fixed_mix_rows"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -217,6 +220,15 @@ def irkgl_diag_fixed_mix(R: torch.Tensor, stream=None) -> torch.Tensor:
     out = torch.empty((n, 8, 2), dtype=torch.float64, device=R.device)
     _check(load().irkgl_diag_fixed_mix(_ptr(R, torch.float64, (n, 8), "R"),
                                        _ptr(out, torch.float64, (n, 8, 2), "out"), n, _stream(stream)))
+    return out
+
+
+def irkgl_diag_fixed_mix_rows(R: torch.Tensor, stream=None) -> torch.Tensor:
+    """The same sums by the runtime-row form (rows spread over lanes)."""
+    n = R.shape[0]
+    out = torch.empty((n, 8, 2), dtype=torch.float64, device=R.device)
+    _check(load().irkgl_diag_fixed_mix_rows(_ptr(R, torch.float64, (n, 8), "R"),
+                                            _ptr(out, torch.float64, (n, 8, 2), "out"), n, _stream(stream)))
     return out
 
 

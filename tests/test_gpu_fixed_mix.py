@@ -110,3 +110,55 @@ def test_mixed_kernel_ensemble(lib):
     ig = out.iters.cpu().numpy()
     assert (np.abs(ig - r["iters_total"]) <= 0.1 * r["iters_total"] + 2).all()
     integ.close()
+
+
+def test_fixed_mix_rows_form_bitwise(lib):
+    """The runtime-row form (one accumulator, signs on the operands, row
+    constants) gives the bits of the two-accumulator form for every column,
+    inside the exact regime and outside it (spreads beyond 2^8, where both
+    truncate the small R_j the same way), for zeros and non-finite values."""
+    torch, irkgl = lib
+    rng = np.random.default_rng(12)
+    n = 4096
+    scale = 10.0 ** rng.uniform(-30, 30, size=(n, 1))
+    sign = np.where(rng.uniform(size=(n, 8)) < 0.5, -1.0, 1.0)
+    R = sign * scale * (1.0 + rng.uniform(size=(n, 8))) * 2.0 ** rng.integers(-40, 40, size=(n, 8))
+    R[0] = 0.0
+    R[1, :5] = 0.0
+    R[2, 3] = np.inf
+    R[3, 6] = np.nan
+    R[4] = 5e-324 * np.arange(1, 9)          # subnormals
+    R[5] = np.array([1.0, -1.0] * 4) * 2.0 ** 60
+    Rt = torch.tensor(R, device="cuda")
+    a = irkgl.irkgl_diag_fixed_mix(Rt).cpu().numpy()
+    b = irkgl.irkgl_diag_fixed_mix_rows(Rt).cpu().numpy()
+    assert np.array_equal(np.isnan(a), np.isnan(b))
+    assert np.array_equal(a.view(np.int64)[~np.isnan(a)], b.view(np.int64)[~np.isnan(b)])
+
+
+@pytest.mark.parametrize("lanes", [2, 8])
+def test_rows_spread_over_lanes_one_step_bitwise(lib, lanes):
+    """With the stage rows spread over 2 or 8 lanes, the group agrees on each
+    component's exponent, converts its own stages and gathers the rest: the
+    sweeps then form the same Q and R as the one-lane tile, so after one step
+    R (kept as R_prev) and the sweep counts are bit-identical; q and v differ
+    only by the order of the update's stage sums."""
+    torch, irkgl = lib
+    w = workloads.kepler_ensemble(batch=1024, periods=1)
+    d = lambda a: torch.tensor(np.ascontiguousarray(a), device="cuda")  # noqa: E731
+    res = {}
+    for lpt in (1, lanes):
+        integ = irkgl.Integrator(irkgl.RHS_KEPLER, [1.0], 2, 0.01, mix=1, layout=1, lanes_per_traj=lpt)
+        assert integ.tile == lpt
+        q, v = d(w["q0"]), d(w["v0"])
+        ql, vl = torch.zeros_like(q), torch.zeros_like(v)
+        rp = torch.zeros((q.shape[0], 8, 2), dtype=torch.float64, device="cuda")
+        it = torch.zeros((q.shape[0], 1), dtype=torch.int32, device="cuda")
+        integ.step(q, v, ql, vl, rp, h=d(w["h"]), nsteps=1, iters=it)
+        torch.cuda.synchronize()
+        res[lpt] = (q.cpu().numpy(), v.cpu().numpy(), rp.cpu().numpy(), it.cpu().numpy())
+        integ.close()
+    a, b = res[1], res[lanes]
+    assert np.array_equal(a[2], b[2]) and np.array_equal(a[3], b[3])
+    for x, y in ((a[0], b[0]), (a[1], b[1])):
+        assert (np.abs(x - y).max(axis=1) / np.abs(x).max(axis=1)).max() <= 4e-16

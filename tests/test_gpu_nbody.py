@@ -6,6 +6,9 @@
     max of max_n |dH/H| agree with the oracle's within a factor of 2, and are
     <= 1e-13 where the oracle's are;
   * chunked stepping == one persistent launch, bitwise; N = 3..5 variants.
+
+Every test runs with the FP64 stage mixing and with the fixed-point mixing
+(exact 128-bit sums, one stage row per lane).
 """
 import numpy as np
 import pytest
@@ -35,12 +38,13 @@ def rel(qg, vg, qo, vo):
     return np.abs(g - o).max(axis=-1) / np.abs(o).max(axis=-1)
 
 
-def test_nbody_first_steps_and_iterations(torch_cuda):
+@pytest.mark.parametrize("mix", [0, 1])
+def test_nbody_first_steps_and_iterations(torch_cuda, mix):
     from paper_2511_03655_gb300 import irkgl
     torch = torch_cuda
     w = workloads.nbody_ensemble(copies=8, steps=1000)
     d, h = w["dim"], float(w["h"][0])
-    integ = irkgl.Integrator(irkgl.RHS_NBODY, w["params"], d, h)
+    integ = irkgl.Integrator(irkgl.RHS_NBODY, w["params"], d, h, mix=mix)
     assert integ.tile == 8
     q, v = dev(torch, w["q0"]), dev(torch, w["v0"])
     ql, vl = torch.zeros_like(q), torch.zeros_like(v)
@@ -67,12 +71,13 @@ def test_nbody_first_steps_and_iterations(torch_cuda):
     integ.close()
 
 
-def test_nbody_energy_statistics_chaotic_criterion(torch_cuda):
+@pytest.mark.parametrize("mix", [0, 1])
+def test_nbody_energy_statistics_chaotic_criterion(torch_cuda, mix):
     from paper_2511_03655_gb300 import irkgl
     torch = torch_cuda
     w = workloads.nbody_ensemble(copies=64, steps=10000)
     d, h = w["dim"], float(w["h"][0])
-    integ = irkgl.Integrator(irkgl.RHS_NBODY, w["params"], d, h)
+    integ = irkgl.Integrator(irkgl.RHS_NBODY, w["params"], d, h, mix=mix)
     out = integ.integrate(dev(torch, w["q0"]), dev(torch, w["v0"]), nsteps_all=10000)
     torch.cuda.synchronize()
     r = cbind.run(cbind.NBODY, w["params"], w["q0"], w["v0"], h, 10000, nthreads=8)
@@ -90,12 +95,13 @@ def test_nbody_energy_statistics_chaotic_criterion(torch_cuda):
     integ.close()
 
 
-def test_nbody_chunked_equals_single_launch(torch_cuda):
+@pytest.mark.parametrize("mix", [0, 1])
+def test_nbody_chunked_equals_single_launch(torch_cuda, mix):
     from paper_2511_03655_gb300 import irkgl
     torch = torch_cuda
     w = workloads.nbody_ensemble(copies=40, steps=300)
     d, h = w["dim"], float(w["h"][0])
-    integ = irkgl.Integrator(irkgl.RHS_NBODY, w["params"], d, h)
+    integ = irkgl.Integrator(irkgl.RHS_NBODY, w["params"], d, h, mix=mix)
     a = integ.integrate(dev(torch, w["q0"]), dev(torch, w["v0"]), nsteps_all=300)
     q, v = dev(torch, w["q0"]), dev(torch, w["v0"])
     ql, vl = torch.zeros_like(q), torch.zeros_like(v)
@@ -108,13 +114,14 @@ def test_nbody_chunked_equals_single_launch(torch_cuda):
     integ.close()
 
 
+@pytest.mark.parametrize("mix", [0, 1])
 @pytest.mark.parametrize("nb", [3, 4, 5])
-def test_nbody_smaller_systems(torch_cuda, nb):
+def test_nbody_smaller_systems(torch_cuda, nb, mix):
     from paper_2511_03655_gb300 import irkgl
     torch = torch_cuda
     w = workloads.nbody_ensemble(copies=16, nbodies=nb, steps=500, seed_id=10 + nb)
     d, h = w["dim"], float(w["h"][0])
-    integ = irkgl.Integrator(irkgl.RHS_NBODY, w["params"], d, h)
+    integ = irkgl.Integrator(irkgl.RHS_NBODY, w["params"], d, h, mix=mix)
     out = integ.integrate(dev(torch, w["q0"]), dev(torch, w["v0"]), nsteps_all=500)
     torch.cuda.synchronize()
     r = cbind.run(cbind.NBODY, w["params"], w["q0"], w["v0"], h, 500, nthreads=8)

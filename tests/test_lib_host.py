@@ -100,3 +100,34 @@ def test_workload_generator_is_deterministic():
     # splitmix64 reference values (seed 0): first outputs of the published generator
     assert int(workloads.splitmix64(0, 1)[0]) == 0xE220A8397B1DCDAF
     assert np.all(a["nsteps"] == 100 * np.rint(200 + 100 * a["e"]).astype(np.int64))
+
+
+def test_runtime_row_constants():
+    """The row constants of the runtime-row fixed-point form: with a negative
+    coefficient applied to the two's complement 2^64 - r' of the operand,
+    sum_j n_ij q_j - rbias_i equals sum_j (+-n_ij) r_j mod 2^128, the exact
+    scaled sum (and the two-accumulator form's P - N - bias_i), for random
+    operands r_j in (-2^61, 2^61), offset r' = r + 2^61."""
+    import random
+
+    from paper_2511_03655_gb300 import gen_tables
+    it = gen_tables.int_tables(gen_tables.tables())
+    M = 1 << 128
+    rnd = random.Random(5)
+    for name in ("ETA", "W", "MU", "NU"):
+        mags, negs, bias, rbias = it[name]
+        for _ in range(200):
+            r = [rnd.randrange(-(1 << 61) + 1, 1 << 61) for _ in range(8)]
+            if _ == 0:
+                r = [(1 << 61) - 1, -(1 << 61) + 1] * 4   # extremes
+            rp = [x + (1 << gen_tables.R_BIAS) for x in r]
+            for i in range(8):
+                n = mags[i * 8:(i + 1) * 8]
+                s = negs[i * 8:(i + 1) * 8]
+                exact = sum((-m if ng else m) * x for m, ng, x in zip(n, s, r))
+                assert abs(exact) < (1 << 127)
+                acc = sum(m * ((1 << 64) - x if ng else x) for m, ng, x in zip(n, s, rp)) % M
+                assert (acc - rbias[i]) % M == exact % M, (name, i)
+                pos = sum(m * x for m, ng, x in zip(n, s, rp) if not ng)
+                neg = sum(m * x for m, ng, x in zip(n, s, rp) if ng)
+                assert (pos - neg - bias[i]) % M == exact % M
