@@ -85,9 +85,10 @@ def parse():
     ap.add_argument("--ninst", type=int, default=4096, help="instances for the uneven workload")
     ap.add_argument("--stage-sweep", action="store_true",
                     help="schwarzschild: also the work-precision sweep of the s = 2, 4, 6, 8 schemes")
-    ap.add_argument("--mix", type=int, default=1, choices=[0, 1],
-                    help="stage mixing of the Kepler line: 1 fixed-point sums on the integer pipes "
-                         "(default, the faster), 0 FP64 FMA chain")
+    ap.add_argument("--mix", type=int, default=None, choices=[0, 1],
+                    help="stage mixing: 1 fixed-point sums on the integer pipes, 0 FP64 FMA chain; "
+                         "default: the faster measured on GB300 (fixed point everywhere except the "
+                         "6-body register tile, where the integer chains cost occupancy)")
     ap.add_argument("--serve-requests", type=int, default=300,
                     help="requests in the bounded serving window (0 = skip the serving measurement)")
     return ap.parse_args()
@@ -745,6 +746,8 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
 
+    if args.mix is None:
+        args.mix = 0 if args.workload == "nbody6" else 1
     if args.traj_steps is None:
         args.traj_steps = {"nbody6": 10000, "uneven": 1000}.get(args.workload, 10000)
     if args.workload == "uneven":

@@ -91,13 +91,20 @@ def register_kernel_available(kind: str, params, dim: int) -> bool:
         irkgl.irkgl_destroy(ctx)
 
 
+# Register tiles whose fixed-point form is slower on GB300: the N-body tile
+# spreads the stage rows over eight lanes, and the integer chains then cost
+# occupancy (measured 3.9e7 vs 4.9e7 trajectory-steps/s on the 6-body ensemble).
+FP64_MIX_FASTER = {"nbody"}
+
+
 def new_context(kind: str, params, dim: int, h: float, mix: int) -> int:
     """A context for the register kernel of (kind, dim): with the fixed-point
-    stage mixing when mix = 1 and a kernel with it is compiled, else with the
-    FP64 mixing. The choice depends only on (kind, dim, mix), so the server
-    and run_plain integrate a request with the same kernel."""
+    stage mixing when mix = 1, a kernel with it is compiled and it is the
+    faster form, else with the FP64 mixing. The choice depends only on
+    (kind, dim, mix), so the server and run_plain integrate a request with
+    the same kernel."""
     ctx = irkgl.irkgl_create(KIND_IDS[kind], params, dim, h)
-    if mix:
+    if mix and kind not in FP64_MIX_FASTER:
         irkgl.irkgl_set_option(ctx, irkgl.OPT_MIX, 1)
         if irkgl.irkgl_get_tile(ctx) <= 0:
             irkgl.irkgl_set_option(ctx, irkgl.OPT_MIX, 0)
