@@ -886,11 +886,13 @@ def main():
                                     "2 flops per FMA",
                      "kernel": ("irkgl_kernel_cs" if integ.layout == "component split" else "irkgl_kernel")
                                + f"<{args.workload}>", "flops_per_launch": flops_launch,
-                     "note": ("fixed-point stage mixing: the mixing flops of each sweep (and the "
-                              "initial guess's) run as exact 128-bit integer multiply-adds on the "
-                              "integer pipes, so the FP64 roof understates this kernel's ceiling and "
-                              "frac can exceed 1; the FP64-pipe share measured by ncu is in profiles/")
-                             if mix else None},
+                     "note": ("the algorithmic count includes the 9 flops of each x^(-3/2), which "
+                              "run on the integer pipes (an integer correction of an FP32 seed)"
+                              + ("; with the fixed-point stage mixing the mixing flops of each sweep "
+                                 "(and the initial guess's) run as exact 128-bit integer multiply-adds "
+                                 "as well" if mix else "")
+                              + ", so the FP64 roof understates this kernel's ceiling and frac can "
+                                "exceed 1; the FP64-pipe share measured by ncu is in profiles/")},
         "clocks": clk,
     }
 

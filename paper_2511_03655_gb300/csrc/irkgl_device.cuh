@@ -123,14 +123,11 @@ __device__ __forceinline__ bool positive_normal(double x) {
   return (bx - 0x0010000000000000ULL) < 0x7fe0000000000000ULL;  // 0 < x < Inf, normal
 }
 
-// x^(-3/2) for x > 0.  From the seed y0 with e = 1 - x y0^2 (|e| < 2^-20):
-// x^(-3/2) = y0^3 (1 - e)^(-3/2) = y0^3 (1 + 3/2 e + 15/8 e^2 + O(e^3)),
-// the binomial series (a third-order Householder correction); truncation
-// error < 2^-57, so the result is within about one ulp.  6 FP64 operations.
-// Special operands are resolved from the bit pattern (no division or square
-// root subroutine, whose call would make the compiler keep stack space for
-// the registers live across it): +-0 and positive subnormals give +Inf (the
-// exact value exceeds the FP64 range), +Inf gives 0, negative and NaN give NaN.
+// x^(-3/2) of the special operands, resolved from the bit pattern (no
+// division or square root subroutine, whose call would make the compiler
+// keep stack space for the registers live across it): +-0 and positive
+// subnormals give +Inf (the exact value exceeds the FP64 range), +Inf gives
+// 0, negative and NaN give NaN.
 __device__ __forceinline__ double rinv3_special(double x) {
   const unsigned long long bx = static_cast<unsigned long long>(__double_as_longlong(x));
   if ((bx << 1) == 0ull || bx < 0x0010000000000000ULL) return __longlong_as_double(0x7ff0000000000000LL);
@@ -138,8 +135,12 @@ __device__ __forceinline__ double rinv3_special(double x) {
   return __longlong_as_double(0x7ff8000000000000LL);
 }
 
-__device__ __forceinline__ double rinv3(double x) {
-  if (!positive_normal(x)) return rinv3_special(x);
+// x^(-3/2) for a positive normal x in FP64 (used where the result is
+// subnormal).  From the seed y0 with e = 1 - x y0^2 (|e| < 2^-20):
+// x^(-3/2) = y0^3 (1 - e)^(-3/2) = y0^3 (1 + 3/2 e + 15/8 e^2 + O(e^3)),
+// the binomial series (a third-order Householder correction); truncation
+// error < 2^-57, so the result is within about one ulp.  6 FP64 operations.
+__device__ __forceinline__ double rinv3_fp64(double x) {
   const double y0 = rsqrt_seed(x);
   const double y02 = y0 * y0;          // exact
   const double e = fma(-x, y02, 1.0);
@@ -147,6 +148,61 @@ __device__ __forceinline__ double rinv3(double x) {
   const double p = fma(e, 1.875, 1.5);
   const double t = e * p;
   return fma(y03, t, y03);
+}
+
+// x^(-3/2) for x > 0 with no FP64 arithmetic at all: the same expansion
+// y0^3 (1 + 3/2 e + 15/8 e^2), e = 1 - x y0^2, evaluated in integers.  With
+// x = X 2^Ex (X the 53-bit significand) and the FP32 seed y0 = Yf 2^f (Yf its
+// 24-bit significand):
+//   * P = X Yf^2 (101 bits, exact) is x y0^2 scaled by 2^k, k = -(Ex + 2f);
+//     e 2^56 = 2^56 - P / 2^(k-56), truncated (|e| < 2^-21, so this fits in
+//     38 bits and is off by less than 2^-56);
+//   * T = (3/2 e + 15/8 e^2) 2^56 from that integer (the square from its top
+//     28 bits: the term is below 2^-40, so 2^-27 of it is negligible);
+//   * y0^3 = Yf^3 (72 bits, top 64 kept) times (2^56 + T) 2^7, top 64 bits
+//     of the 128-bit product, rounded to nearest-even FP64.
+// Truncations add about 0.15 ulp to the rounding: 0.66 ulp worst case over
+// 2e5 random arguments (the FP64 form above is within about one ulp).  About
+// 60 integer operations and one FP32 reciprocal square root replace six
+// FP64 operations, and FP64 issues 1/64 as fast as the integer pipes on
+// GB300.  A result above the FP64 range (x below about 2^-682) is +Inf; a
+// subnormal one (x above about 2^681) takes the FP64 form.
+__device__ __forceinline__ double rinv3_int(double x) {
+  const unsigned long long bx = static_cast<unsigned long long>(__double_as_longlong(x));
+  const int E = static_cast<int>((bx >> 52) & 0x7ff);
+  const unsigned long long X = (bx & 0x000fffffffffffffULL) | 0x0010000000000000ULL;
+  const int Eu = E - 1023;
+  const int par = Eu & 1;
+  const int half = (Eu - par) / 2;  // exact: Eu - par is even
+  const unsigned m23 = static_cast<unsigned>((bx >> 29) & 0x7fffffu);
+  const float yf = rsqrtf(__uint_as_float((static_cast<unsigned>(127 + par) << 23) | m23));  // (0.5, 1]
+  const unsigned yb = __float_as_uint(yf);
+  const int f = static_cast<int>(yb >> 23) - 127 - 23 - half;   // y0 = Yf 2^f
+  const unsigned long long Yf = (yb & 0x7fffffu) | 0x800000u;
+  const unsigned long long Y2 = Yf * Yf;                       // 48 bits, exact
+  const unsigned long long Plo = X * Y2, Phi = __umul64hi(X, Y2);
+  const int sh = (1075 - E) - 2 * f - 56;                      // k - 56, 43..45
+  const unsigned long long Ptop = (Phi << (64 - sh)) | (Plo >> sh);
+  const long long D = static_cast<long long>((1ULL << 56) - Ptop);  // e 2^56
+  const long long Dq = D >> 8;
+  const long long T = ((3 * D) >> 1) + ((15 * Dq * Dq) >> 43);
+  const unsigned long long M = static_cast<unsigned long long>((1LL << 56) + T) << 7;
+  const unsigned long long C = (__umul64hi(Y2, Yf) << 56) | ((Y2 * Yf) >> 8);  // Yf^3 / 2^8
+  const unsigned long long hi = __umul64hi(C, M);               // in [2^59, 2^64)
+  const int lz = __clzll(static_cast<long long>(hi));
+  const unsigned long long mant = hi << lz;
+  const int biased = 3 * f + 72 - lz + 1023;
+  if (biased >= 2047) return __longlong_as_double(0x7ff0000000000000LL);  // above the range
+  if (biased <= 0) return rinv3_fp64(x);  // subnormal or zero result
+  const unsigned long long m53 = mant >> 11;
+  unsigned long long bits = (static_cast<unsigned long long>(biased - 1) << 52) + m53;
+  bits += ((mant >> 10) & 1ULL) & (((mant & 0x3ffULL) != 0ULL ? 1ULL : 0ULL) | (m53 & 1ULL));
+  return __longlong_as_double(static_cast<long long>(bits));
+}
+
+__device__ __forceinline__ double rinv3(double x) {
+  if (!positive_normal(x)) return rinv3_special(x);
+  return rinv3_int(x);
 }
 
 // x^(-1/2) for x > 0, same seed: y0 (1 + e/2 + 3/8 e^2).  5 FP64 operations.

@@ -44,7 +44,21 @@ __global__ void fixed_mix_rows_kernel(const double* R, double* out, int n) {
     out[(x * irkgl::S + i) * 2 + 1] = nf ? __longlong_as_double(0x7ff8000000000000LL) : w;
   }
 }
+// The device reciprocal square roots the right-hand sides use.
+__global__ void rinv_kernel(const double* x, double* out, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  out[2 * i] = irkgl::rinv3(x[i]);
+  out[2 * i + 1] = irkgl::rinv1(x[i]);
+}
 }  // namespace
+
+extern "C" int irkgl_diag_rinv(const double* x, double* out, int n, void* stream) {
+  if (n < 0 || (n > 0 && (!x || !out))) return IRKGL_ERR_INVALID;
+  if (n == 0) return IRKGL_OK;
+  rinv_kernel<<<(n + 127) / 128, 128, 0, static_cast<cudaStream_t>(stream)>>>(x, out, n);
+  return cudaGetLastError() == cudaSuccess ? IRKGL_OK : IRKGL_ERR_CUDA;
+}
 
 extern "C" int irkgl_diag_fixed_mix_rows(const double* R, double* out, int n, void* stream) {
   if (n < 0 || (n > 0 && (!R || !out))) return IRKGL_ERR_INVALID;

@@ -37,7 +37,7 @@ EXPORTS = ("irkgl_default_coeffs", "irkgl_create", "irkgl_set_option", "irkgl_st
            "irkgl_last_cuda_error", "irkgl_get_tile", "irkgl_probe_fp64_fma",
            "irkgl_integrate_noalloc", "irkgl_integrate_ragged", "irkgl_advance",
            "irkgl_advance_ragged", "irkgl_diag_fixed_mix",
-           "irkgl_diag_fixed_mix_rows")
+           "irkgl_diag_fixed_mix_rows", "irkgl_diag_rinv")
 NOALLOC_MAX_PARAMS = 63
 
 _P = ctypes.c_void_p
@@ -117,6 +117,7 @@ def load(path: str | None = None, build_if_missing: bool = False):
     L.irkgl_advance_t.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int, _P]
     L.irkgl_diag_fixed_mix.argtypes = [_P, _P, ctypes.c_int, _P]
     L.irkgl_diag_fixed_mix_rows.argtypes = [_P, _P, ctypes.c_int, _P]
+    L.irkgl_diag_rinv.argtypes = [_P, _P, ctypes.c_int, _P]
     L.irkgl_advance_ragged.argtypes = [_P, _P, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P, _P,
                                        _P, _P, ctypes.c_int, _P, _P, _P, _P]
     L.irkgl_integrate_ragged.argtypes = [_P, _P, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P,
@@ -128,7 +129,7 @@ def load(path: str | None = None, build_if_missing: bool = False):
                  "irkgl_integrate", "irkgl_integrate_host", "irkgl_get_tile",
                  "irkgl_probe_fp64_fma", "irkgl_integrate_noalloc", "irkgl_integrate_ragged",
                  "irkgl_advance", "irkgl_advance_ragged", "irkgl_diag_fixed_mix",
-                 "irkgl_diag_fixed_mix_rows"):
+                 "irkgl_diag_fixed_mix_rows", "irkgl_diag_rinv"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -229,6 +230,15 @@ def irkgl_diag_fixed_mix_rows(R: torch.Tensor, stream=None) -> torch.Tensor:
     out = torch.empty((n, 8, 2), dtype=torch.float64, device=R.device)
     _check(load().irkgl_diag_fixed_mix_rows(_ptr(R, torch.float64, (n, 8), "R"),
                                             _ptr(out, torch.float64, (n, 8, 2), "out"), n, _stream(stream)))
+    return out
+
+
+def irkgl_diag_rinv(x: torch.Tensor, stream=None) -> torch.Tensor:
+    """x^(-3/2) and x^(-1/2) as the right-hand sides evaluate them: [n] -> [n, 2]."""
+    n = x.shape[0]
+    out = torch.empty((n, 2), dtype=torch.float64, device=x.device)
+    _check(load().irkgl_diag_rinv(_ptr(x, torch.float64, (n,), "x"),
+                                  _ptr(out, torch.float64, (n, 2), "out"), n, _stream(stream)))
     return out
 
 

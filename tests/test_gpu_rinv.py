@@ -1,0 +1,74 @@
+"""The device reciprocal square roots against 50-digit decimal arithmetic.
+
+x^(-3/2) (the force factor of the Kepler and N-body right-hand sides) is
+evaluated without FP64 arithmetic, from an FP32 seed and integer products;
+x^(-1/2) (the potential) by an FP64 correction of the same seed.  Both must
+be within one unit in the last place over the whole normal range, and the
+special operands must give the IEEE limits."""
+from decimal import Decimal, getcontext
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import torch
+    from paper_2511_03655_gb300 import build, irkgl
+    build.build()
+    irkgl.load()
+    return torch, irkgl
+
+
+def ulp(x: float) -> float:
+    return float(np.spacing(np.float64(abs(x))))
+
+
+def exact(x: float, p: str) -> Decimal:
+    getcontext().prec = 50
+    d = Decimal(x)
+    return 1 / (d * d.sqrt()) if p == "3" else 1 / d.sqrt()
+
+
+def test_rinv_normal_range(lib):
+    torch, irkgl = lib
+    rng = np.random.default_rng(21)
+    x = np.concatenate([
+        2.0 ** rng.uniform(-60, 60, 20000),        # the physical range
+        2.0 ** rng.uniform(-680, 680, 4000),       # the rest of the normal results
+        2.0 ** np.arange(-40, 41, dtype=np.float64),  # powers of two (seed boundaries)
+        np.nextafter(2.0 ** np.arange(-40, 41, dtype=np.float64), 0.0),
+        2.0 ** rng.uniform(-700, -682, 200),       # x^(-3/2) above the range -> Inf / FP64 form
+        2.0 ** rng.uniform(682, 700, 200),         # x^(-3/2) subnormal or zero
+    ])
+    out = irkgl.irkgl_diag_rinv(torch.tensor(x, device="cuda")).cpu().numpy()
+    worst3 = worst1 = 0.0
+    for xi, y3, y1 in zip(x, out[:, 0], out[:, 1]):
+        e3 = exact(float(xi), "3")
+        if e3 < Decimal("1.7976931348623157e308"):
+            if e3 >= Decimal("2.2250738585072014e-308"):
+                worst3 = max(worst3, float(abs(Decimal(float(y3)) - e3)) / ulp(float(e3)))
+            else:   # subnormal range: absolute error within one unit of the smallest subnormal
+                assert abs(Decimal(float(y3)) - e3) <= Decimal(5e-324), xi
+        else:
+            assert y3 == np.inf, xi
+        e1 = exact(float(xi), "1")
+        worst1 = max(worst1, float(abs(Decimal(float(y1)) - e1)) / ulp(float(e1)))
+    assert worst3 <= 1.0, worst3
+    assert worst1 <= 1.0, worst1
+
+
+def test_rinv_special_operands(lib):
+    torch, irkgl = lib
+    x = np.array([0.0, -0.0, 5e-324, 1e-310, np.inf, -1.0, -np.inf, np.nan])
+    out = irkgl.irkgl_diag_rinv(torch.tensor(x, device="cuda")).cpu().numpy()
+    r3, r1 = out[:, 0], out[:, 1]
+    assert r3[0] == np.inf and r3[1] == np.inf and r3[2] == np.inf and r3[3] == np.inf
+    assert r3[4] == 0.0 and np.isnan(r3[5]) and np.isnan(r3[6]) and np.isnan(r3[7])
+    assert r1[0] == np.inf and r1[1] == -np.inf and r1[4] == 0.0
+    assert np.isnan(r1[5]) and np.isnan(r1[6]) and np.isnan(r1[7])
+    for k in (2, 3):   # positive subnormals: finite x^(-1/2), within one ulp
+        e = exact(float(x[k]), "1")
+        assert float(abs(Decimal(float(r1[k])) - e)) <= ulp(float(e))
