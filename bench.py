@@ -54,11 +54,12 @@ FLOPS_NBODY6 = (3882, 6456)
 # dram__bytes_write.sum of one launch of the full 65,536-orbit batch; the
 # state is read once and kept in registers, so the traffic depends on the
 # batch, not on the horizon), valid only for the kernel source it was taken
-# on (kernel_sha(): the sources of the Kepler tiles).
-NCU_TRAFFIC_BYTES_PER_LAUNCH = {(0, "stage split"): 4389888 + 68864,  # by (mixing, tile layout)
-                                (1, "stage split"): 4640000 + 595968,
-                                (1, "component split"): 4217088 + 118016}
-NCU_KERNEL_SHA = "68265a9b374b87ca"
+# on (kernel_sha(): the sources of the Kepler tiles), recorded per entry.
+NCU_TRAFFIC_BYTES_PER_LAUNCH = {  # (mixing, tile layout): (bytes per launch, kernel_sha at capture)
+    (0, "stage split"): (4389888 + 68864, "68265a9b374b87ca"),
+    (1, "stage split"): (4640000 + 595968, "68265a9b374b87ca"),
+    (1, "component split"): (4225792 + 105216, "8e568b2904e1d1f1"),
+}
 
 
 def parse():
@@ -859,8 +860,9 @@ def main():
 
     flops_launch = fps * float(steps.sum()) + fpw * float(iters.sum())
     achieved = flops_launch / statistics.mean(times) / 1e12
-    traffic = (NCU_TRAFFIC_BYTES_PER_LAUNCH.get((args.mix, integ.layout)) if NCU_KERNEL_SHA == kernel_sha()
-               and args.workload == "kepler" and args.batch == 65536 else None)
+    cap = NCU_TRAFFIC_BYTES_PER_LAUNCH.get((args.mix, integ.layout))
+    traffic = (cap[0] if cap and cap[1] == kernel_sha() and args.workload == "kepler"
+               and args.batch == 65536 else None)
 
     line = {
         "metric": METRIC, "value": value, "unit": "traj-steps/s", "n_gpus": world,
