@@ -380,10 +380,11 @@ int irkgl_diag_fixed_mix(const double* R, double* out, int n, void* cuda_stream)
  * irkgl_diag_fixed_mix's bit for bit. */
 int irkgl_diag_fixed_mix_rows(const double* R, double* out, int n, void* cuda_stream);
 
-/* Diagnostic, not part of the method: the reciprocal square roots the
- * right-hand sides evaluate, for n arguments x[n] (device): out[n][2]
- * (device) receives x^(-3/2) (the gravitational force factor) and x^(-1/2)
- * (the potential).  Errors: IRKGL_ERR_INVALID, IRKGL_ERR_CUDA. */
+/* Diagnostic, not part of the method: the reciprocal roots the right-hand
+ * sides evaluate, for n arguments x[n] (device): out[n][3] (device)
+ * receives x^(-3/2) (the gravitational force factor), x^(-1/2) (the
+ * potential) and 1/x (the Schwarzschild terms).  Errors: IRKGL_ERR_INVALID,
+ * IRKGL_ERR_CUDA. */
 int irkgl_diag_rinv(const double* x, double* out, int n, void* cuda_stream);
 
 /* Integration for callers that cannot allocate device memory.  (The paper

@@ -205,6 +205,45 @@ __device__ __forceinline__ double rinv3(double x) {
   return rinv3_int(x);
 }
 
+// 1/x with no FP64 arithmetic, the same construction: an FP32 seed
+// y0 = Yf 2^f of the reciprocal of x's leading 24 bits (rcp.approx, within
+// an FP32 ulp), e = 1 - x y0 from the exact integer product X Yf (77 bits)
+// as e 2^56, then 1/x = y0 (1 + e + e^2) (|e| < 2^-21, the e^3 term is
+// below 2^-63) as Yf (2^56 + T) 2^7 with the top 64 bits of the product
+// rounded to nearest-even.  0.61 ulp worst case over 2e5 random arguments of
+// both signs across the exponent range (a Python model of the integer steps
+// against 60-digit decimals).  Zero, subnormal, infinite and NaN arguments
+// and subnormal results (|x| > 2^1022) take the FP64 division.
+__device__ __forceinline__ double rcp_int(double x) {
+  const unsigned long long bx = static_cast<unsigned long long>(__double_as_longlong(x));
+  const int E = static_cast<int>((bx >> 52) & 0x7ff);
+  if (E == 0 || E >= 0x7fe) return 1.0 / x;
+  const unsigned long long X = (bx & 0x000fffffffffffffULL) | 0x0010000000000000ULL;
+  const unsigned m23 = static_cast<unsigned>((bx >> 29) & 0x7fffffu);
+  float yf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(__uint_as_float((127u << 23) | m23)));  // (0.5, 1]
+  const unsigned yb = __float_as_uint(yf);
+  const int f = static_cast<int>(yb >> 23) - 127 - 23 - (E - 1023);  // y0 = Yf 2^f
+  const unsigned long long Yf = (yb & 0x7fffffu) | 0x800000u;
+  const unsigned long long P = X * Yf;                  // 77 bits: the low 64 ...
+  const unsigned long long Ph = __umul64hi(X, Yf);      // ... and the high ones
+  const int sh = (1075 - E) - f - 56;                   // k - 56, about 19..20
+  const unsigned long long Ptop = (Ph << (64 - sh)) | (P >> sh);
+  const long long D = static_cast<long long>((1ULL << 56) - Ptop);  // e 2^56
+  const long long Dq = D >> 8;
+  const long long T = D + ((Dq * Dq) >> 40);            // (e + e^2) 2^56
+  const unsigned long long M = static_cast<unsigned long long>((1LL << 56) + T) << 7;
+  const unsigned long long hi = __umul64hi(Yf << 40, M);
+  const int lz = __clzll(static_cast<long long>(hi));
+  const unsigned long long mant = hi << lz;
+  const int biased = f + 24 - lz + 1023;
+  if (biased <= 0) return 1.0 / x;
+  const unsigned long long m53 = mant >> 11;
+  unsigned long long bits = (static_cast<unsigned long long>(biased - 1) << 52) + m53;
+  bits += ((mant >> 10) & 1ULL) & (((mant & 0x3ffULL) != 0ULL ? 1ULL : 0ULL) | (m53 & 1ULL));
+  return __longlong_as_double(static_cast<long long>(bits | (bx & 0x8000000000000000ULL)));
+}
+
 // x^(-1/2) for x > 0, same seed: y0 (1 + e/2 + 3/8 e^2).  5 FP64 operations.
 __device__ __forceinline__ double rinv1_normal(double x) {
   const double y0 = rsqrt_seed(x);

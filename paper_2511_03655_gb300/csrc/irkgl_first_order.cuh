@@ -86,10 +86,10 @@ struct Schwarzschild {
     double sn, cs;
     sincos(y[1], &sn, &cs);
     const double s = sn * sn;
-    const double ri = 1.0 / r;
+    const double ri = rcp_int(r);
     const double u = fma(-2.0, ri, 1.0);
-    const double ui = 1.0 / u;
-    const double si = 1.0 / s;
+    const double ui = rcp_int(u);
+    const double si = rcp_int(s);
     const double r2i = ri * ri;
     const double r3i = r2i * ri;
     // dH/dr

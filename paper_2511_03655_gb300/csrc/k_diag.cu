@@ -48,8 +48,9 @@ __global__ void fixed_mix_rows_kernel(const double* R, double* out, int n) {
 __global__ void rinv_kernel(const double* x, double* out, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  out[2 * i] = irkgl::rinv3(x[i]);
-  out[2 * i + 1] = irkgl::rinv1(x[i]);
+  out[3 * i] = irkgl::rinv3(x[i]);
+  out[3 * i + 1] = irkgl::rinv1(x[i]);
+  out[3 * i + 2] = irkgl::rcp_int(x[i]);
 }
 }  // namespace
 

@@ -234,11 +234,11 @@ def irkgl_diag_fixed_mix_rows(R: torch.Tensor, stream=None) -> torch.Tensor:
 
 
 def irkgl_diag_rinv(x: torch.Tensor, stream=None) -> torch.Tensor:
-    """x^(-3/2) and x^(-1/2) as the right-hand sides evaluate them: [n] -> [n, 2]."""
+    """x^(-3/2), x^(-1/2) and 1/x as the right-hand sides evaluate them: [n] -> [n, 3]."""
     n = x.shape[0]
-    out = torch.empty((n, 2), dtype=torch.float64, device=x.device)
+    out = torch.empty((n, 3), dtype=torch.float64, device=x.device)
     _check(load().irkgl_diag_rinv(_ptr(x, torch.float64, (n,), "x"),
-                                  _ptr(out, torch.float64, (n, 2), "out"), n, _stream(stream)))
+                                  _ptr(out, torch.float64, (n, 3), "out"), n, _stream(stream)))
     return out
 
 

@@ -1,10 +1,11 @@
-"""The device reciprocal square roots against 50-digit decimal arithmetic.
+"""The device reciprocal roots against 50-digit decimal arithmetic.
 
-x^(-3/2) (the force factor of the Kepler and N-body right-hand sides) is
-evaluated without FP64 arithmetic, from an FP32 seed and integer products;
-x^(-1/2) (the potential) by an FP64 correction of the same seed.  Both must
-be within one unit in the last place over the whole normal range, and the
-special operands must give the IEEE limits."""
+x^(-3/2) (the force factor of the Kepler and N-body right-hand sides) and
+1/x (the Schwarzschild terms) are evaluated without FP64 arithmetic, from an
+FP32 seed and integer products; x^(-1/2) (the potential) by an FP64
+correction of the same seed.  All must be within one unit in the last place
+over the whole normal range, and the special operands must give the IEEE
+limits."""
 from decimal import Decimal, getcontext
 
 import numpy as np
@@ -43,7 +44,7 @@ def test_rinv_normal_range(lib):
         2.0 ** rng.uniform(-700, -682, 200),       # x^(-3/2) above the range -> Inf / FP64 form
         2.0 ** rng.uniform(682, 700, 200),         # x^(-3/2) subnormal or zero
     ])
-    out = irkgl.irkgl_diag_rinv(torch.tensor(x, device="cuda")).cpu().numpy()
+    out = irkgl.irkgl_diag_rinv(torch.tensor(x, device="cuda")).cpu().numpy()[:, :2]
     worst3 = worst1 = 0.0
     for xi, y3, y1 in zip(x, out[:, 0], out[:, 1]):
         e3 = exact(float(xi), "3")
@@ -58,6 +59,30 @@ def test_rinv_normal_range(lib):
         worst1 = max(worst1, float(abs(Decimal(float(y1)) - e1)) / ulp(float(e1)))
     assert worst3 <= 1.0, worst3
     assert worst1 <= 1.0, worst1
+
+
+def test_reciprocal(lib):
+    torch, irkgl = lib
+    rng = np.random.default_rng(22)
+    mag = np.concatenate([2.0 ** rng.uniform(-60, 60, 20000), 2.0 ** rng.uniform(-1021, 1021, 4000),
+                          2.0 ** np.arange(-40, 41, dtype=np.float64),
+                          np.nextafter(2.0 ** np.arange(-40, 41, dtype=np.float64), 0.0),
+                          2.0 ** rng.uniform(1022, 1023.9, 100)])   # subnormal results
+    x = mag * np.where(rng.uniform(size=mag.size) < 0.5, -1.0, 1.0)
+    out = irkgl.irkgl_diag_rinv(torch.tensor(x, device="cuda")).cpu().numpy()[:, 2]
+    getcontext().prec = 50
+    worst = 0.0
+    for xi, y in zip(x, out):
+        e = 1 / Decimal(float(xi))
+        if abs(e) >= Decimal("2.2250738585072014e-308"):
+            worst = max(worst, float(abs(Decimal(float(y)) - e)) / ulp(float(e)))
+        else:
+            assert abs(Decimal(float(y)) - e) <= Decimal(5e-324), xi
+    assert worst <= 1.0, worst
+    sp = np.array([0.0, -0.0, np.inf, -np.inf, np.nan, 5e-324, -1e-310])
+    r = irkgl.irkgl_diag_rinv(torch.tensor(sp, device="cuda")).cpu().numpy()[:, 2]
+    assert r[0] == np.inf and r[1] == -np.inf and r[2] == 0.0 and r[3] == 0.0 and np.isnan(r[4])
+    assert r[5] == np.inf and r[6] == -np.inf   # 1/x overflows for these subnormals
 
 
 def test_rinv_special_operands(lib):
