@@ -387,6 +387,11 @@ int irkgl_diag_fixed_mix_rows(const double* R, double* out, int n, void* cuda_st
  * IRKGL_ERR_CUDA. */
 int irkgl_diag_rinv(const double* x, double* out, int n, void* cuda_stream);
 
+/* Diagnostic, not part of the method: sin x and cos x as the Schwarzschild
+ * right-hand side evaluates them, for n arguments x[n] (device): out[n][2]
+ * (device) receives (sin, cos).  Errors: IRKGL_ERR_INVALID, IRKGL_ERR_CUDA. */
+int irkgl_diag_sincos(const double* x, double* out, int n, void* cuda_stream);
+
 /* Integration for callers that cannot allocate device memory.  (The paper
  * has no counterpart: this is a deployment entry point.)
  *

@@ -407,3 +407,40 @@ __host__ __device__ constexpr unsigned irkgl_nu_rbias(int i, int w) {
     0x00000000u, 0x00000000u, 0x72e23680u, 0xd2e7fd33u};
   return t[i * 4 + w];
 }
+
+// Fixed-point sine and cosine (see gen_tables.sincos_tables): 2/pi * 2^128 as
+// two 64-bit words; Taylor coefficients of sin(pi/2 f)/f and cos(pi/2 f) in z = f^2,
+// scaled by 2^62, constant term first.
+#define IRKGL_SINCOS_TERMS 11
+#define IRKGL_TWO_OVER_PI_HI 0xa2f9836e4e441529ULL
+#define IRKGL_TWO_OVER_PI_LO 0xfc2757d1f534ddc1ULL
+__host__ __device__ constexpr long long irkgl_sin_coef(int k) {
+  constexpr long long t[11] = {
+    7244019458077122842LL,
+    -2978983596875621757LL,
+    367517370231208053LL,
+    -21590780087563799LL,
+    739904368663792LL,
+    -16596735030340LL,
+    262505142787LL,
+    -3084311801LL,
+    27978803LL,
+    -201857LL,
+    1186LL};
+  return t[k];
+}
+__host__ __device__ constexpr long long irkgl_cos_coef(int k) {
+  constexpr long long t[11] = {
+    4611686018427387904LL,
+    -5689439577989151081LL,
+    1169844122888618931LL,
+    -96215822532083616LL,
+    4239339756772701LL,
+    -116223906447658LL,
+    2172507535204LL,
+    -29453008147LL,
+    302801603LL,
+    -2441611LL,
+    15854LL};
+  return t[k];
+}

@@ -52,7 +52,23 @@ __global__ void rinv_kernel(const double* x, double* out, int n) {
   out[3 * i + 1] = irkgl::rinv1(x[i]);
   out[3 * i + 2] = irkgl::rcp_int(x[i]);
 }
+// The fixed-point sine and cosine of the Schwarzschild right-hand side.
+__global__ void sincos_kernel(const double* x, double* out, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s, c;
+  irkgl::sincos_fx(x[i], s, c);
+  out[2 * i] = s;
+  out[2 * i + 1] = c;
+}
 }  // namespace
+
+extern "C" int irkgl_diag_sincos(const double* x, double* out, int n, void* stream) {
+  if (n < 0 || (n > 0 && (!x || !out))) return IRKGL_ERR_INVALID;
+  if (n == 0) return IRKGL_OK;
+  sincos_kernel<<<(n + 127) / 128, 128, 0, static_cast<cudaStream_t>(stream)>>>(x, out, n);
+  return cudaGetLastError() == cudaSuccess ? IRKGL_OK : IRKGL_ERR_CUDA;
+}
 
 extern "C" int irkgl_diag_rinv(const double* x, double* out, int n, void* stream) {
   if (n < 0 || (n > 0 && (!x || !out))) return IRKGL_ERR_INVALID;

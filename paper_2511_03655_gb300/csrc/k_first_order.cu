@@ -5,6 +5,11 @@
 
 namespace {
 
+// The fixed-point component-split tile takes the FP64 sincos (its mixing
+// already fills the integer pipes); every other Schwarzschild tile the
+// fixed-point one.
+using SchwarzschildFp64Trig = ::irkgl::Schwarzschild<2, false>;
+
 // Functor template argument = stages per lane (NST / LPT).
 const ::irkgl::KernelEntry1 kEntries[] = {
     IRKGL_ENTRY1(IRKGL_RHS_SCHWARZSCHILD, 4, ::irkgl::Schwarzschild<8>, 1, 128, 8),
@@ -24,7 +29,7 @@ const ::irkgl::KernelEntry1 kEntries[] = {
     IRKGL_ENTRY1(IRKGL_RHS_HARMONIC1, 2, ::irkgl::Harmonic1<6>, 1, 128, 6),
     // component split (one component of all eight stages per lane)
     IRKGL_ENTRY1_CS(IRKGL_RHS_SCHWARZSCHILD, 4, ::irkgl::Schwarzschild<2>, 128, 0),
-    IRKGL_ENTRY1_CS(IRKGL_RHS_SCHWARZSCHILD, 4, ::irkgl::Schwarzschild<2>, 128, 1),
+    IRKGL_ENTRY1_CS(IRKGL_RHS_SCHWARZSCHILD, 4, SchwarzschildFp64Trig, 128, 1),
     IRKGL_ENTRY1_CS(IRKGL_RHS_HARMONIC1, 2, ::irkgl::Harmonic1<4>, 128, 0),
     IRKGL_ENTRY1_CS(IRKGL_RHS_HARMONIC1, 2, ::irkgl::Harmonic1<4>, 128, 1),
 };

@@ -197,6 +197,68 @@ def int_tables(t):
     return out
 
 
+SINCOS_TERMS = 11   # Taylor terms of sin and cos on a quarter period (last term below 2^-62)
+SINCOS_SHIFT = 62   # coefficient scale
+
+
+def dec_pi() -> Decimal:
+    """pi by Machin's formula, pi = 16 atan(1/5) - 4 atan(1/239), to PREC digits."""
+    with localcontext() as ctx:
+        ctx.prec = PREC + 10
+
+        def atan_inv(k):
+            x = Decimal(k)
+            term = 1 / x
+            total, n, sign = term, 1, -1
+            while True:
+                term /= x * x
+                t = term / (2 * n + 1)
+                if t < Decimal(10) ** (-(PREC + 5)):
+                    return total
+                total += sign * t
+                sign, n = -sign, n + 1
+
+        return +(16 * atan_inv(5) - 4 * atan_inv(239))
+
+
+def sincos_tables():
+    """Integer constants of the fixed-point sine and cosine: 2/pi rounded to
+    128 bits, and the Taylor coefficients of sin(pi/2 f) / f and cos(pi/2 f)
+    in powers of z = f^2, (-1)^k (pi/2)^(2k+1)/(2k+1)! and (-1)^k
+    (pi/2)^(2k)/(2k)!, rounded to 2^-62 (|f| <= 1/2, so z <= 1/4 and the
+    twelfth term is below 2^-62)."""
+    from math import factorial
+    with localcontext() as ctx:
+        ctx.prec = PREC
+        pi = dec_pi()
+        two_over_pi = int(((2 / pi) * (Decimal(2) ** 128)).to_integral_value())
+        hp = pi / 2
+        scale = Decimal(2) ** SINCOS_SHIFT
+        sin_c = [int((((-1) ** k) * hp ** (2 * k + 1) / factorial(2 * k + 1) * scale).to_integral_value())
+                 for k in range(SINCOS_TERMS)]
+        cos_c = [int((((-1) ** k) * hp ** (2 * k) / factorial(2 * k) * scale).to_integral_value())
+                 for k in range(SINCOS_TERMS)]
+    return two_over_pi, sin_c, cos_c
+
+
+def _render_sincos() -> str:
+    two_over_pi, sin_c, cos_c = sincos_tables()
+    m64 = (1 << 64) - 1
+    lines = ["", "// Fixed-point sine and cosine (see gen_tables.sincos_tables): 2/pi * 2^128 as",
+             "// two 64-bit words; Taylor coefficients of sin(pi/2 f)/f and cos(pi/2 f) in z = f^2,",
+             f"// scaled by 2^{SINCOS_SHIFT}, constant term first.",
+             f"#define IRKGL_SINCOS_TERMS {SINCOS_TERMS}",
+             f"#define IRKGL_TWO_OVER_PI_HI 0x{two_over_pi >> 64:016x}ULL",
+             f"#define IRKGL_TWO_OVER_PI_LO 0x{two_over_pi & m64:016x}ULL"]
+    for name, co in (("SIN", sin_c), ("COS", cos_c)):
+        lines.append(f"__host__ __device__ constexpr long long irkgl_{name.lower()}_coef(int k) {{")
+        lines.append(f"  constexpr long long t[{SINCOS_TERMS}] = {{")
+        lines.append("    " + ",\n    ".join(f"{x}LL" if x != -(1 << 63) else "(-9223372036854775807LL - 1)"
+                                           for x in co).replace("\\n", "\n") + "};")
+        lines.append("  return t[k];\n}")
+    return "\n".join(lines) + "\n"
+
+
 def _render_int(t) -> str:
     it = int_tables(t)
     lines = ["", "// Integer forms for the fixed-point mixing (see gen_tables.int_tables):",
@@ -261,7 +323,7 @@ def render(t) -> str:
     for name, (a, b) in split_tables().items():
         out.append(arrn(f"IRKGL_SPLIT_{name}_A", a))
         out.append(arrn(f"IRKGL_SPLIT_{name}_B", b))
-    return "\n".join(out) + _render_int(t)
+    return "\n".join(out) + _render_int(t) + _render_sincos()
 
 
 def main(argv=None):

@@ -37,7 +37,7 @@ EXPORTS = ("irkgl_default_coeffs", "irkgl_create", "irkgl_set_option", "irkgl_st
            "irkgl_last_cuda_error", "irkgl_get_tile", "irkgl_probe_fp64_fma",
            "irkgl_integrate_noalloc", "irkgl_integrate_ragged", "irkgl_advance",
            "irkgl_advance_ragged", "irkgl_diag_fixed_mix",
-           "irkgl_diag_fixed_mix_rows", "irkgl_diag_rinv")
+           "irkgl_diag_fixed_mix_rows", "irkgl_diag_rinv", "irkgl_diag_sincos")
 NOALLOC_MAX_PARAMS = 63
 
 _P = ctypes.c_void_p
@@ -118,6 +118,7 @@ def load(path: str | None = None, build_if_missing: bool = False):
     L.irkgl_diag_fixed_mix.argtypes = [_P, _P, ctypes.c_int, _P]
     L.irkgl_diag_fixed_mix_rows.argtypes = [_P, _P, ctypes.c_int, _P]
     L.irkgl_diag_rinv.argtypes = [_P, _P, ctypes.c_int, _P]
+    L.irkgl_diag_sincos.argtypes = [_P, _P, ctypes.c_int, _P]
     L.irkgl_advance_ragged.argtypes = [_P, _P, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P, _P,
                                        _P, _P, ctypes.c_int, _P, _P, _P, _P]
     L.irkgl_integrate_ragged.argtypes = [_P, _P, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P,
@@ -129,7 +130,7 @@ def load(path: str | None = None, build_if_missing: bool = False):
                  "irkgl_integrate", "irkgl_integrate_host", "irkgl_get_tile",
                  "irkgl_probe_fp64_fma", "irkgl_integrate_noalloc", "irkgl_integrate_ragged",
                  "irkgl_advance", "irkgl_advance_ragged", "irkgl_diag_fixed_mix",
-                 "irkgl_diag_fixed_mix_rows", "irkgl_diag_rinv"):
+                 "irkgl_diag_fixed_mix_rows", "irkgl_diag_rinv", "irkgl_diag_sincos"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -239,6 +240,15 @@ def irkgl_diag_rinv(x: torch.Tensor, stream=None) -> torch.Tensor:
     out = torch.empty((n, 3), dtype=torch.float64, device=x.device)
     _check(load().irkgl_diag_rinv(_ptr(x, torch.float64, (n,), "x"),
                                   _ptr(out, torch.float64, (n, 3), "out"), n, _stream(stream)))
+    return out
+
+
+def irkgl_diag_sincos(x: torch.Tensor, stream=None) -> torch.Tensor:
+    """(sin x, cos x) as the Schwarzschild right-hand side evaluates them: [n] -> [n, 2]."""
+    n = x.shape[0]
+    out = torch.empty((n, 2), dtype=torch.float64, device=x.device)
+    _check(load().irkgl_diag_sincos(_ptr(x, torch.float64, (n,), "x"),
+                                    _ptr(out, torch.float64, (n, 2), "out"), n, _stream(stream)))
     return out
 
 

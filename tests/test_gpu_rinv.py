@@ -1,11 +1,11 @@
 """The device reciprocal roots against 50-digit decimal arithmetic.
 
-x^(-3/2) (the force factor of the Kepler and N-body right-hand sides) and
-1/x (the Schwarzschild terms) are evaluated without FP64 arithmetic, from an
-FP32 seed and integer products; x^(-1/2) (the potential) by an FP64
-correction of the same seed.  All must be within one unit in the last place
-over the whole normal range, and the special operands must give the IEEE
-limits."""
+x^(-3/2) (the force factor of the Kepler and N-body right-hand sides),
+x^(-1/2) (the potential) and 1/x (the Schwarzschild terms) are evaluated
+without FP64 arithmetic, from an FP32 seed and integer products; sin and cos
+of the Schwarzschild right-hand side in fixed point.  All must be within one
+unit in the last place over the whole normal range, and the special
+operands must give the IEEE limits."""
 from decimal import Decimal, getcontext
 
 import numpy as np
@@ -97,3 +97,64 @@ def test_rinv_special_operands(lib):
     for k in (2, 3):   # positive subnormals: finite x^(-1/2), within one ulp
         e = exact(float(x[k]), "1")
         assert float(abs(Decimal(float(r1[k])) - e)) <= ulp(float(e))
+
+
+def _dec_sin_cos(x: float):
+    """sin and cos by Taylor series in 60-digit decimals after reduction by
+    2 pi (pi from Machin's formula, computed here)."""
+    getcontext().prec = 70
+
+    def atan_inv(k):
+        t = Decimal(1) / k
+        tot, n, sg = t, 1, -1
+        while True:
+            t /= k * k
+            u = t / (2 * n + 1)
+            if u < Decimal(10) ** -68:
+                return tot
+            tot += sg * u
+            sg, n = -sg, n + 1
+
+    pi = 16 * atan_inv(5) - 4 * atan_inv(239)
+    d = Decimal(x)
+    d -= (d / (2 * pi)).to_integral_value() * 2 * pi
+    s = c = Decimal(0)
+    term, n = d, 1
+    while abs(term) > Decimal(10) ** -66:
+        s += term
+        term = -term * d * d / ((n + 1) * (n + 2))
+        n += 2
+    term, n = Decimal(1), 0
+    while abs(term) > Decimal(10) ** -66:
+        c += term
+        term = -term * d * d / ((n + 1) * (n + 2))
+        n += 2
+    return s, c
+
+
+def test_fixed_point_sincos(lib):
+    """sin and cos of the Schwarzschild right-hand side (fixed-point for
+    2^-30 <= |x| < 64, the FP64 sincos elsewhere) within one ulp of the
+    60-digit values, including arguments next to multiples of pi/2."""
+    torch, irkgl = lib
+    rng = np.random.default_rng(23)
+    hp = np.pi / 2
+    x = np.concatenate([
+        rng.uniform(-64, 64, 6000),
+        2.0 ** rng.uniform(-30, 6, 2000) * np.where(rng.uniform(size=2000) < 0.5, -1.0, 1.0),
+        np.array([k * hp for k in range(1, 40)]),                    # the FP64 multiples of pi/2
+        np.nextafter(np.array([k * hp for k in range(1, 40)]), 0.0),
+        np.array([1e-12, 3e-10, 100.0, -1e3, 0.0, -0.0]),           # outside: the FP64 sincos
+    ])
+    out = irkgl.irkgl_diag_sincos(torch.tensor(x, device="cuda")).cpu().numpy()
+    worst = 0.0
+    for xi, (s, c) in zip(x, out):
+        es, ec = _dec_sin_cos(float(xi))
+        for got, ex in ((s, es), (c, ec)):
+            if ex == 0:
+                assert got == 0.0
+                continue
+            worst = max(worst, float(abs(Decimal(float(got)) - ex)) / ulp(float(ex)))
+    assert worst <= 1.0, worst
+    sp = irkgl.irkgl_diag_sincos(torch.tensor([np.inf, np.nan], dtype=torch.float64, device="cuda")).cpu().numpy()
+    assert np.isnan(sp).all()

@@ -131,3 +131,24 @@ def test_runtime_row_constants():
                 pos = sum(m * x for m, ng, x in zip(n, s, rp) if not ng)
                 neg = sum(m * x for m, ng, x in zip(n, s, rp) if ng)
                 assert (pos - neg - bias[i]) % M == exact % M
+
+
+def test_sincos_constants():
+    """The generated fixed-point sine/cosine constants against the math
+    library: 2/pi to 128 bits, and the Taylor polynomials of sin(pi/2 f)/f
+    and cos(pi/2 f) in z = f^2 on the quarter period."""
+    import math
+    from fractions import Fraction
+
+    from paper_2511_03655_gb300 import gen_tables
+    two_over_pi, sin_c, cos_c = gen_tables.sincos_tables()
+    assert abs(Fraction(two_over_pi, 1 << 128) - Fraction(2 / math.pi)) < Fraction(1, 1 << 52)
+    scale = Fraction(1, 1 << gen_tables.SINCOS_SHIFT)
+    for f in (0.5, 0.37, -0.21, 1e-3, 2.0 ** -20):
+        z = Fraction(f) ** 2
+        S = sum(Fraction(c) * scale * z ** k for k, c in enumerate(sin_c))
+        C = sum(Fraction(c) * scale * z ** k for k, c in enumerate(cos_c))
+        # the library's argument pi/2 f is rounded, hence a few units of 1e-16
+        s_ref, c_ref = math.sin(math.pi / 2 * f), math.cos(math.pi / 2 * f)
+        assert abs(float(Fraction(f) * S) - s_ref) <= 4e-16 * abs(s_ref)
+        assert abs(float(C) - c_ref) <= 4e-16
