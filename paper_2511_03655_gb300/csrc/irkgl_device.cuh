@@ -181,7 +181,7 @@ __device__ __forceinline__ double rinv3_int(double x) {
   const unsigned long long Yf = (yb & 0x7fffffu) | 0x800000u;
   const unsigned long long Y2 = Yf * Yf;                       // 48 bits, exact
   const unsigned long long Plo = X * Y2, Phi = __umul64hi(X, Y2);
-  const int sh = (1075 - E) - 2 * f - 56;                      // k - 56, 43..45
+  const int sh = (1075 - E) - 2 * f - 56;                      // k - 56 = 42 - par - 2 ef: 41..44
   const unsigned long long Ptop = (Phi << (64 - sh)) | (Plo >> sh);
   const long long D = static_cast<long long>((1ULL << 56) - Ptop);  // e 2^56
   const long long Dq = D >> 8;
@@ -353,7 +353,7 @@ __device__ __forceinline__ double rinv1_int(double x) {
   const unsigned long long Yf = (yb & 0x7fffffu) | 0x800000u;
   const unsigned long long Y2 = Yf * Yf;
   const unsigned long long Plo = X * Y2, Phi = __umul64hi(X, Y2);
-  const int sh = (1075 - E) - 2 * f - 56;
+  const int sh = (1075 - E) - 2 * f - 56;  // 41..44, as in rinv3_int
   const unsigned long long Ptop = (Phi << (64 - sh)) | (Plo >> sh);
   const long long D = static_cast<long long>((1ULL << 56) - Ptop);  // e 2^56
   const long long Dq = D >> 8;
