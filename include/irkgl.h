@@ -150,8 +150,10 @@ enum {
                                    carried across irkgl_advance calls) */
   IRKGL_OPT_MIX = 8,            /* stage mixing of Eq. Qi2 and the initial guess: 0 = FP64 FMA
                                    chain (default); 1 = exact fixed-point sums on the integer
-                                   pipes, rounded once (one lane per trajectory, default tables
-                                   only; IRKGL_ERR_UNSUPPORTED otherwise) */
+                                   pipes, rounded once (the one-lane and component-split tiles,
+                                   the tiles with the stage rows spread over lanes, the wide
+                                   kernel); needs the default tables.  A call with no compiled
+                                   kernel for the choice returns IRKGL_ERR_UNSUPPORTED */
   IRKGL_OPT_TILE_LAYOUT = 10,   /* second-order kinds: 1 = the stage-split tiles (LPT lanes per
                                    trajectory share the stages); 2 = the component-split tile for
                                    d = 2 (Kepler, Henon-Heiles): two lanes per trajectory, each
