@@ -58,7 +58,7 @@ FLOPS_NBODY6 = (3882, 6456)
 NCU_TRAFFIC_BYTES_PER_LAUNCH = {  # (mixing, tile layout): (bytes per launch, kernel_sha at capture)
     (0, "stage split"): (4389888 + 68864, "68265a9b374b87ca"),
     (1, "stage split"): (4640000 + 595968, "68265a9b374b87ca"),
-    (1, "component split"): (4115456 + 140288, "078754e3379d7718"),  # sources differ from the capture in comments only
+    (1, "component split"): (4179456 + 81920, "a3d0963eec2c4a34"),
 }
 
 

@@ -29,18 +29,18 @@ namespace irkgl {
 // exact) or nu (rounded).
 template <bool IS_NU>
 __device__ __forceinline__ double fixed_row1(int i, const unsigned long long (&rb)[S], int emax) {
-  U128 P{0u, 0u, 0u, 0u}, N{0u, 0u, 0u, 0u};
+  // one accumulator: a negative coefficient takes the two's complement of
+  // the operand, and the row constant rbias absorbs the n_ij 2^64 that adds
+  U128 P{0u, 0u, 0u, 0u};
 #pragma unroll
   for (int j = 0; j < S; j++) {
     const int k = i * S + j;
     const unsigned long long m = IS_NU ? irkgl_nu_mag(k) : irkgl_mu_mag(k);
     const bool neg = IS_NU ? irkgl_nu_neg(k) : irkgl_mu_neg(k);
-    if (neg) mac64(N, m, rb[j]);
-    else mac64(P, m, rb[j]);
+    mac64(P, m, neg ? (0ull - rb[j]) : rb[j]);
   }
-  sub128(P, N.x0, N.x1, N.x2, N.x3);
-  if (IS_NU) sub128(P, irkgl_nu_bias(i, 0), irkgl_nu_bias(i, 1), irkgl_nu_bias(i, 2), irkgl_nu_bias(i, 3));
-  else sub128(P, irkgl_mu_bias(i, 0), irkgl_mu_bias(i, 1), irkgl_mu_bias(i, 2), irkgl_mu_bias(i, 3));
+  if (IS_NU) sub128(P, irkgl_nu_rbias(i, 0), irkgl_nu_rbias(i, 1), irkgl_nu_rbias(i, 2), irkgl_nu_rbias(i, 3));
+  else sub128(P, irkgl_mu_rbias(i, 0), irkgl_mu_rbias(i, 1), irkgl_mu_rbias(i, 2), irkgl_mu_rbias(i, 3));
   constexpr int shift = IS_NU ? IRKGL_NU_SHIFT : IRKGL_MU_SHIFT;
   return s128_to_double(P, emax - 1083 - shift);
 }

@@ -407,9 +407,10 @@ __device__ __forceinline__ void two_sum_add(double& hi, double& lo, double x) {
 //   * eta_ij = +-n_ij 2^-63 with n_ij an exact integer (every eta is on that
 //     grid); W_ik = +-w_ik 2^-50 rounded (W only seeds the initial guess);
 //   * products n r' (64 x 64 -> 128 bits, eight 32-bit multiply-adds with
-//     carry) go to a positive or a negative accumulator by the coefficient's
-//     sign, known at compile time; the difference minus the row constant
-//     sum_j (+-n_ij) 2^61 is the exact sum, rounded to nearest-even FP64.
+//     carry) go to one accumulator, a negative coefficient multiplying the
+//     two's complement 2^64 - r' of the operand; minus the row constant
+//     rbias_i = sum_j (+-n_ij) 2^61 + 2^64 sum_{negative j} n_ij (mod 2^128)
+//     that is the exact sum, rounded to nearest-even FP64.
 // The result is the correctly rounded value of the (exact) sum, one rounding
 // instead of the FMA chain's eight.
 // ------------------------------------------------------------------------
@@ -500,18 +501,19 @@ __device__ __forceinline__ unsigned long long to_fixed_offset(double x, int emax
 // offset fixed point rb[j] with shared exponent emax.  IS_W selects W.
 template <bool IS_W>
 __device__ __forceinline__ double fixed_row(int i, const unsigned long long (&rb)[S], int emax) {
-  U128 P{0u, 0u, 0u, 0u}, N{0u, 0u, 0u, 0u};
+  // one accumulator: a negative coefficient takes the two's complement of
+  // the operand (computed once per column, shared by the rows), and the row
+  // constant rbias absorbs the n_ij 2^64 that adds (see fixed_row_rt)
+  U128 P{0u, 0u, 0u, 0u};
 #pragma unroll
   for (int j = 0; j < S; j++) {
     const int k = i * S + j;
     const unsigned long long m = IS_W ? irkgl_w_mag(k) : irkgl_eta_mag(k);
     const bool neg = IS_W ? irkgl_w_neg(k) : irkgl_eta_neg(k);
-    if (neg) mac64(N, m, rb[j]);
-    else mac64(P, m, rb[j]);
+    mac64(P, m, neg ? (0ull - rb[j]) : rb[j]);
   }
-  sub128(P, N.x0, N.x1, N.x2, N.x3);
-  if (IS_W) sub128(P, irkgl_w_bias(i, 0), irkgl_w_bias(i, 1), irkgl_w_bias(i, 2), irkgl_w_bias(i, 3));
-  else sub128(P, irkgl_eta_bias(i, 0), irkgl_eta_bias(i, 1), irkgl_eta_bias(i, 2), irkgl_eta_bias(i, 3));
+  if (IS_W) sub128(P, irkgl_w_rbias(i, 0), irkgl_w_rbias(i, 1), irkgl_w_rbias(i, 2), irkgl_w_rbias(i, 3));
+  else sub128(P, irkgl_eta_rbias(i, 0), irkgl_eta_rbias(i, 1), irkgl_eta_rbias(i, 2), irkgl_eta_rbias(i, 3));
   constexpr int shift = IS_W ? IRKGL_W_SHIFT : IRKGL_ETA_SHIFT;
   return s128_to_double(P, emax - 1083 - shift);
 }
