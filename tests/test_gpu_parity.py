@@ -296,8 +296,10 @@ def test_ragged_batches(torch_cuda, batch):
     torch = torch_cuda
     w = workloads.kepler_ensemble(batch=batch, periods=1)
     n = np.minimum(w["nsteps"], 50 + np.arange(batch))
-    for lpt in (1, 2, 8):
-        integ = irkgl.Integrator(irkgl.RHS_KEPLER, [1.0], 2, 0.01, lanes_per_traj=lpt)
+    # the stage-split tiles with the FP64 mixing, and the default tile (the
+    # component split with the fixed-point mixing)
+    for kw in (dict(lanes_per_traj=1), dict(lanes_per_traj=2), dict(lanes_per_traj=8), dict(mix=1)):
+        integ = irkgl.Integrator(irkgl.RHS_KEPLER, [1.0], 2, 0.01, **kw)
         out = integ.integrate(dev(torch, w["q0"]), dev(torch, w["v0"]), nsteps=dev(torch, n),
                               h=dev(torch, w["h"]))
         torch.cuda.synchronize()
@@ -307,10 +309,11 @@ def test_ragged_batches(torch_cuda, batch):
         integ.close()
 
 
-def test_empty_and_zero_steps(torch_cuda):
+@pytest.mark.parametrize("mix", [0, 1])
+def test_empty_and_zero_steps(torch_cuda, mix):
     from paper_2511_03655_gb300 import irkgl
     torch = torch_cuda
-    integ = irkgl.Integrator(irkgl.RHS_KEPLER, [1.0], 2, 0.01)
+    integ = irkgl.Integrator(irkgl.RHS_KEPLER, [1.0], 2, 0.01, mix=mix)
     e = torch.zeros((0, 2), dtype=torch.float64, device="cuda")
     out = integ.integrate(e, e, nsteps_all=10)
     assert out.q.shape == (0, 2)
@@ -328,14 +331,16 @@ def test_empty_and_zero_steps(torch_cuda):
     integ.close()
 
 
-def test_status_codes(torch_cuda):
+@pytest.mark.parametrize("mix", [0, 1])
+def test_status_codes(torch_cuda, mix):
     """Iteration cap and non-finite stage values stop a trajectory at the
-    start of the failing step, leaving the other trajectories untouched."""
+    start of the failing step, leaving the other trajectories untouched
+    (the default FP64 tile and the fixed-point component-split tile)."""
     from paper_2511_03655_gb300 import irkgl
     torch = torch_cuda
     q0 = np.array([[0.5, 0.0], [0.0, 0.0], [0.5, 0.0]])
     v0 = np.array([[0.0, math.sqrt(3.0)], [0.0, 0.0], [0.0, math.sqrt(3.0)]])
-    integ = irkgl.Integrator(irkgl.RHS_KEPLER, [1.0], 2, 0.05)
+    integ = irkgl.Integrator(irkgl.RHS_KEPLER, [1.0], 2, 0.05, mix=mix)
     out = integ.integrate(dev(torch, q0), dev(torch, v0), nsteps_all=5)
     torch.cuda.synchronize()
     assert out.status.cpu().tolist() == [0, irkgl.STATUS_NONFINITE, 0]
