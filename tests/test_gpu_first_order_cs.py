@@ -99,3 +99,35 @@ def test_harmonic1_cs(torch_cuda, mix):
     r = cbind.run1(cbind.HARMONIC1, [1.3], y0, 0.4, 500)
     assert rel(out.y.cpu().numpy(), r["y"]).max() <= 1e-11
     ig.close()
+
+
+@pytest.mark.parametrize("batch", [1, 3, 33])
+def test_default_tile_ragged_empty_and_status(torch_cuda, batch):
+    """The default first-order tile (component split, fixed-point mixing) on
+    batch sizes that leave partly filled warps, per-orbit step counts
+    (including zero), an empty batch, and an orbit on the polar axis
+    (sin theta = 0: the 1/sin^2 terms are infinite, so that orbit stops with
+    the non-finite status and leaves the others untouched)."""
+    from paper_2511_03655_gb300 import irkgl
+    torch = torch_cuda
+    y0 = workloads.schwarzschild_ensemble(batch, seed_id=53)
+    n = (20 + 7 * np.arange(batch)).astype(np.int64)
+    n[0] = 0
+    ig = integ(1, 0)
+    out = ig.integrate1(torch.tensor(y0, device="cuda"), nsteps=torch.tensor(n, device="cuda"))
+    torch.cuda.synchronize()
+    r = cbind.run1(cbind.SCHWARZSCHILD, PAR, y0, 4.0, n)
+    assert (out.steps.cpu().numpy() == n).all() and (out.status.cpu().numpy() == 0).all()
+    assert np.array_equal(out.y.cpu().numpy()[0], y0[0])
+    if batch > 1:
+        assert rel(out.y.cpu().numpy()[1:], r["y"][1:]).max() <= 1e-12
+    e = torch.zeros((0, 4), dtype=torch.float64, device="cuda")
+    assert ig.integrate1(e, nsteps_all=10).y.shape == (0, 4)
+    bad = y0.copy()
+    bad[0, 1] = 0.0  # theta = 0
+    out = ig.integrate1(torch.tensor(bad, device="cuda"), nsteps_all=5)
+    torch.cuda.synchronize()
+    st = out.status.cpu().numpy()
+    assert st[0] == irkgl.STATUS_NONFINITE and (st[1:] == 0).all()
+    assert out.steps.cpu().numpy()[0] == 0
+    ig.close()
