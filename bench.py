@@ -39,7 +39,8 @@ METRIC = "IRKGL16 trajectory-steps/s at |ΔH/H|≤1e-13 vs plain GPU form; p50/p
 TOL = 1e-13
 
 # Algorithmic FP64 floating-point operations (an FMA counts 2) per unit for
-# the Kepler right-hand side, d = 2 (derivation in DESIGN.md, "Roofline"):
+# the Kepler right-hand side, d = 2 (counted from the kernel's operation list:
+# 8 stages x d components, 8-term mixing rows, one x^(-3/2) per stage):
 #   per completed step:  init 304 + compensated update 90 + energy monitor 19
 #   per fixed-point sweep (8 stages): g and R 120 + mixing 288 + Delta 16
 FLOPS_PER_STEP = 413

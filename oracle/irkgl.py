@@ -28,7 +28,7 @@ One step n (s = 8 stages, d position components):
       v_n = v + sum_i R_i
       q_n = q + h v_n - h sum_i c_i R_i
 
-Readings where the paper is silent (also listed in the design doc):
+Readings where the paper is silent:
   * first step: Rprev = 0;
   * min over an empty set is +inf, so for k <= 2 only Delta == 0 stops;
   * iteration cap kmax = 100 -> status MAXITER; a non-finite Qn -> status
@@ -264,7 +264,12 @@ class Harmonic:
 
 class NBody:
     """Newtonian N-body problem in 3-D (Eq. Ham2 with G = 1 by default);
-    positions q[3a + x]; g_a = G sum_{b != a} m_b (q_b - q_a)/|q_b - q_a|^3."""
+    positions q[3a + x]; g_a = G sum_{b != a} m_b (q_b - q_a)/|q_b - q_a|^3.
+
+    Pinned (tests/test_oracle_rhs.py): g = -grad H / m by 60-digit central
+    differences; two unequal bodies follow the closed-form Kepler orbit with
+    mu = G (m_1 + m_2); Lagrange's equilateral triangle of unequal masses
+    rotates rigidly with omega^2 = G M / L^3; total momentum is conserved."""
 
     def __init__(self, masses, G=1.0):
         self.m = list(masses)
@@ -306,7 +311,12 @@ class FPUT:
     """Fermi-Pasta-Ulam-Tsingou alpha chain with fixed ends q_0 = q_{n+1} = 0:
     H = sum_j v_j^2/2 + sum_{j=0}^{n} V(q_{j+1} - q_j),
     V(r) = r^2/2 + alpha r^3/3, so g_j = V'(r_j) - V'(r_{j-1}),
-    r_j = q_{j+1} - q_j, V'(r) = r + alpha r^2."""
+    r_j = q_{j+1} - q_j, V'(r) = r + alpha r^2.
+
+    Pinned (tests/test_oracle_rhs.py): g = -grad H by 60-digit central
+    differences; g equals the Fermi-Pasta-Ulam equation of motion in its
+    second-difference form; for alpha = 0 the run follows the chain's
+    closed-form normal modes; the energy of a mode-1 run stays bounded."""
 
     def __init__(self, n, alpha=0.25):
         self.d = n

@@ -6,8 +6,9 @@
  * identical operation sequence: sequential sums j = 1..8, every operation
  * rounded separately.  Build with -O2 -ffp-contract=off (no fast-math, no
  * FMA contraction) so that its results are bit-identical to the Python form;
- * tests/test_oracle_c.py checks that.  Used by the tests for large cases and
- * by bench.py as the timed CPU baseline; never by the CUDA product path.
+ * tests/test_oracle_step.py::test_c_equals_python_bitwise checks that.  Used
+ * by the tests for large cases and by bench.py as the timed CPU baseline;
+ * never by the CUDA product path.
  *
  * Readings where the paper is silent are those stated in oracle/irkgl.py:
  * Rprev = 0 on the first step, kmax = 100 (status 1), a non-finite stage
