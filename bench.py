@@ -75,13 +75,16 @@ def parse():
     ap.add_argument("--no-order", action="store_true", help="natural order instead of similarity order")
     ap.add_argument("--skip-extras", action="store_true", help="skip e2e, plain form and CPU baseline")
     ap.add_argument("--workload", default="kepler",
-                    choices=["kepler", "nbody6", "uneven", "schwarzschild", "overhead", "serving"],
+                    choices=["kepler", "nbody6", "uneven", "schwarzschild", "overhead", "serving",
+                             "sweeps"],
                     help="kepler: the 65,536-orbit ensemble (default); nbody6: 16,384 perturbed "
                          "copies of a 6-body system; uneven: 4,096 ragged instances (N-body "
                          "N~U{3..64} and FPUT n~U{8..512}), autotuned vs fixed tiling; schwarzschild: "
                          "65,536 first-order black-hole orbits (Eq. Ham_SBH), t in [0, 1e5], h = 16; "
                          "overhead: GPU time per g-evaluation of IRKGL16 over that of the explicit "
-                         "splitting methods (Henon-Heiles and 6-body ensembles)")
+                         "splitting methods (Henon-Heiles and 6-body ensembles); serving: config-5 "
+                         "windows at --serve-rates; sweeps: per-step sweep counts against the "
+                         "oracle's from the identical state (Kepler ensemble, Henon-Heiles)")
     ap.add_argument("--traj-steps", type=int, default=None,
                     help="steps per trajectory/instance (nbody6: 10000, uneven: 1000 by default)")
     ap.add_argument("--ninst", type=int, default=4096, help="instances for the uneven workload")
@@ -91,9 +94,180 @@ def parse():
                     help="stage mixing: 1 fixed-point sums on the integer pipes, 0 FP64 FMA chain; "
                          "default: the faster measured on GB300 (fixed point everywhere except the "
                          "6-body register tile, where the integer chains cost occupancy)")
-    ap.add_argument("--serve-requests", type=int, default=300,
+    ap.add_argument("--serve-requests", type=int, default=16,
                     help="requests in the bounded serving window (0 = skip the serving measurement)")
+    ap.add_argument("--serve-rates", default="2000",
+                    help="--workload serving: comma-separated Poisson arrival rates per second")
+    ap.add_argument("--no-sublines", action="store_true",
+                    help="skip the compact lines of the other configurations in the default run")
     return ap.parse_args()
+
+
+# --------------------------------------------------------------------------
+# compact lines of the other configurations (each its own bench.py run)
+# --------------------------------------------------------------------------
+SUBLINES = {
+    "nbody6": ["--workload", "nbody6", "--batch", "16384", "--traj-steps", "1000", "--steps", "2",
+               "--warmup", "1", "--skip-extras"],
+    "uneven": ["--workload", "uneven", "--ninst", "1024", "--traj-steps", "1000", "--steps", "2",
+               "--warmup", "1", "--skip-extras"],
+    "schwarzschild": ["--workload", "schwarzschild", "--batch", "16384", "--steps", "2", "--warmup",
+                      "1", "--skip-extras"],
+}
+
+
+def sublines() -> dict:
+    """Run each other configuration at a reduced size in its own process and
+    keep the figures of its JSON line (value, CUDA-event time per step,
+    roofline fraction, accuracy), so that the default run reports them."""
+    out = {}
+    for name, extra in SUBLINES.items():
+        cmd = [sys.executable, os.path.abspath(__file__)] + extra
+        t0 = time.perf_counter()
+        try:
+            r = subprocess.run(cmd, capture_output=True, text=True, timeout=900)
+            js = json.loads([x for x in r.stdout.splitlines() if x.startswith("{")][-1])
+        except Exception as e:  # noqa: BLE001 - reported in the line, the main figure stands
+            out[name] = {"command": "python bench.py " + " ".join(extra), "error": repr(e)[:300]}
+            continue
+        rf = js.get("roofline", {})
+        out[name] = {
+            "command": "python bench.py " + " ".join(extra), "workload": js["config"]["workload"],
+            "value": js["value"], "value_all": js.get("value_all"), "unit": js["unit"],
+            "ms_per_step": js["ms_per_step"], "steps": js["steps"],
+            "roofline": {k: rf.get(k) for k in ("bound", "achieved", "peak", "unit", "frac")},
+            "accuracy": js.get("accuracy"), "sweeps_per_step": js.get("sweeps_per_step"),
+            "gpu_launches": js.get("gpu_launches"), "clocks": js.get("clocks"),
+            "wall_s": time.perf_counter() - t0}
+    return out
+
+
+# --------------------------------------------------------------------------
+# sweep counts against the oracle, step by step from the identical state
+# --------------------------------------------------------------------------
+def sweep_histogram(torch, irkgl, kind_g, kind_o, params, q0, v0, h, nsteps, cores, **integ_kw):
+    """Histogram of k_gpu - k_oracle per step, where before every step the
+    GPU's state (hi and lo parts, R_prev) is handed to the oracle, so the two
+    differ only by the arithmetic of that one step (Eqs. IRK_init2, IRK_FP2,
+    Delta_n, stopping).  Also the histogram of k itself on both sides."""
+    from oracle import cbind
+    B, d = q0.shape
+    f = dict(dtype=torch.float64, device="cuda")
+    q, v = torch.tensor(q0, **f), torch.tensor(v0, **f)
+    ql, vl = torch.zeros_like(q), torch.zeros_like(v)
+    rp = torch.zeros((B, 8, d), **f)
+    hh = torch.tensor(np.broadcast_to(np.asarray(h, dtype=np.float64), (B,)).copy(), **f)
+    it = torch.zeros((B, 1), dtype=torch.int32, device="cuda")
+    integ = irkgl.Integrator(kind_g, params, d, float(np.asarray(h).reshape(-1)[0]), **integ_kw)
+    pin = {k: torch.empty(t.shape, dtype=t.dtype, pin_memory=True)
+           for k, t in (("q", q), ("v", v), ("ql", ql), ("vl", vl), ("rp", rp))}
+    hs = np.broadcast_to(np.asarray(h, dtype=np.float64), (B,)).copy()
+    diff, kg_hist, ko_hist = {}, {}, {}
+    worst = []  # (step, trajectory, k_gpu, k_oracle) of |diff| >= 2, first few
+    for n in range(nsteps):
+        for k, t in (("q", q), ("v", v), ("ql", ql), ("vl", vl), ("rp", rp)):
+            pin[k].copy_(t)
+        integ.step(q, v, ql, vl, rp, h=hh, nsteps=1, iters=it)
+        r = cbind.run(kind_o, params, pin["q"].numpy(), pin["v"].numpy(), hs, 1, q_lo=pin["ql"].numpy(),
+                      v_lo=pin["vl"].numpy(), r_prev=pin["rp"].numpy(), iters_len=1, nthreads=cores)
+        kg = it.cpu().numpy()[:, 0].astype(np.int64)
+        ko = r["iters"][:, 0].astype(np.int64)
+        dd = kg - ko
+        for hist, vals in ((diff, dd), (kg_hist, kg), (ko_hist, ko)):
+            u, c = np.unique(vals, return_counts=True)
+            for a, b in zip(u.tolist(), c.tolist()):
+                hist[a] = hist.get(a, 0) + b
+        if len(worst) < 8:
+            for b in np.flatnonzero(np.abs(dd) >= 2)[:8 - len(worst)]:
+                worst.append((n, int(b), int(kg[b]), int(ko[b])))
+    integ.close()
+    total = B * nsteps
+    beyond = sum(c for a, c in diff.items() if abs(a) >= 2)
+    return {"traj_steps": total, "diff_hist": {str(a): diff[a] for a in sorted(diff)},
+            "k_gpu_hist": {str(a): kg_hist[a] for a in sorted(kg_hist)},
+            "k_oracle_hist": {str(a): ko_hist[a] for a in sorted(ko_hist)},
+            "rate_beyond_1": beyond / total, "max_abs_diff": max(abs(a) for a in diff),
+            "rate_equal": diff.get(0, 0) / total, "first_beyond_1": worst}
+
+
+def run_sweeps(args):
+    """Sweep-count parity, step by step from the identical state: the
+    65,536-orbit Kepler ensemble (both stage mixings) over 1,000 steps, the
+    Henon-Heiles orbit of Sec. 5.1 over 2 pi 1e4 at h = 1.0, and a
+    4,096-orbit Henon-Heiles ensemble over 1,000 steps at h = 0.7."""
+    import torch
+
+    from paper_2511_03655_gb300 import build, irkgl, workloads
+    from oracle import cbind
+    torch.cuda.set_device(0)
+    build.build()
+    irkgl.load()
+    cores = os.cpu_count() or 1
+    n = args.traj_steps or 1000
+    kw = workloads.kepler_ensemble(batch=args.batch, periods=1)
+    rows = {}
+    for mix in (1, 0):
+        t0 = time.perf_counter()
+        rows[f"kepler_ensemble_mix{mix}"] = sweep_histogram(
+            torch, irkgl, irkgl.RHS_KEPLER, cbind.KEPLER, [1.0], kw["q0"], kw["v0"], kw["h"], n, cores,
+            mix=mix)
+        rows[f"kepler_ensemble_mix{mix}"]["seconds"] = time.perf_counter() - t0
+    q0, v0 = workloads.henon_heiles_ic()
+    nhh = int(round(2 * math.pi * 1e4 / 1.0))
+    for mix in (1, 0):
+        rows[f"henon_heiles_orbit_mix{mix}"] = sweep_histogram(
+            torch, irkgl, irkgl.RHS_HENON_HEILES, cbind.HENON_HEILES, [1.0], q0, v0, 1.0, nhh, cores,
+            mix=mix)
+        hq, hv, _ = workloads.henon_heiles_ensemble(4096)
+        rows[f"henon_heiles_ensemble_mix{mix}"] = sweep_histogram(
+            torch, irkgl, irkgl.RHS_HENON_HEILES, cbind.HENON_HEILES, [1.0], hq, hv, 0.7, n, cores,
+            mix=mix)
+    line = {"metric": "sweep-count parity (k_gpu - k_oracle per step, identical state before each step)",
+            "config": {"workload": f"Kepler ensemble B={args.batch} e~U[0,0.9) h=2pi/round(200+100e) "
+                                   f"x {n} steps; Henon-Heiles orbit (Sec. 5.1, H = 1/12) h = 1.0 x "
+                                   f"{nhh} steps; Henon-Heiles ensemble B=4096 h = 0.7 x {n} steps"},
+            "cases": rows}
+    print(json.dumps(line))
+    return 0
+
+
+# --------------------------------------------------------------------------
+# config 5: serving window
+# --------------------------------------------------------------------------
+SERVE_DIST = ("config-5 distribution: families Kepler ensemble, 6-body ensemble, N-body N in "
+              "{3..64}, FPUT n in {8..1536} (D = 2d from 4 to 3072); batch logU[1,4096], horizon "
+              "logU[1e2,1e5] steps")
+
+
+def serving_window(serve, workloads, n, rate, mix, peak_tflops, plain=True):
+    """The first `n` Poisson arrivals at `rate` per second from the config-5
+    distribution, served to completion by the continuous-batching loop (and
+    by the plain per-request form): p50 / p99 latency, served and offered
+    trajectory-steps/s, the algorithmic FP64 rate against the roof, the
+    fraction of the makespan with a kernel running, and launches per tick."""
+    import copy
+    descs = workloads.serving_requests(n=n, rate=rate)
+    window = max(d["arrival"] for d in descs) - min(d["arrival"] for d in descs)
+    offered = sum(d["q0"].shape[0] * d["nsteps"] for d in descs) / max(window, 1e-9)
+    reqs = serve.make_requests(copy.deepcopy(descs))
+    srv = serve.Server(mix=mix)
+    st = srv.run(reqs).summary()
+    srv.close()
+    out = {"requests": n, "rate_per_s": rate, "arrival_window_s": window,
+           "offered_traj_steps_s": offered,
+           "traj_steps": int(sum(r.traj_steps for r in reqs)),
+           "continuous_batching": st,
+           "served_over_offered": st["throughput_traj_steps_s"] / offered,
+           "fp64_roof_frac": st["flops_per_s"] / (peak_tflops * 1e12),
+           "status_nonzero": int(sum(int((r.status != 0).sum()) for r in reqs))}
+    if plain:
+        pr = serve.make_requests(copy.deepcopy(descs))
+        sp = serve.run_plain(pr, mix=mix).summary()
+        out["plain_per_request"] = sp
+        out["results_identical_to_plain"] = bool(all(
+            np.array_equal(a.q, b.q) and np.array_equal(a.v, b.v) and np.array_equal(a.iters, b.iters)
+            for a, b in zip(reqs, pr)))
+    return out
 
 
 def kernel_sha() -> str:
@@ -695,45 +869,30 @@ def run_overhead(args):
 # config 5: p50 / p99 latency over a sweep of arrival rates
 # --------------------------------------------------------------------------
 def run_serving_sweep(args):
-    """Bounded windows of 300 Poisson requests at several arrival rates,
-    served by the continuous-batching loop (arrival order, and shortest job
-    first): p50 / p99 latency, throughput, and the offered load (requested
-    trajectory-steps per second of arrival window) against the served rate,
-    below and above saturation."""
-    import copy
-
+    """Serving windows of --serve-requests Poisson requests from the config-5
+    distribution at each rate of --serve-rates, served to completion by the
+    continuous-batching loop: p50 / p99 latency, served against offered
+    trajectory-steps/s, the GPU-busy fraction and the FP64 roof fraction of
+    the served work, below and above saturation."""
     import torch
 
     from paper_2511_03655_gb300 import build, irkgl, serve, workloads
     torch.cuda.set_device(0)
     build.build()
     irkgl.load()
+    dev = torch.device("cuda", 0)
+    peak = fp64_peak_tflops(irkgl, torch, torch.cuda.current_stream(), dev)
     rows = []
-    for rate in (50.0, 200.0, 1000.0, 2000.0):
-        descs = workloads.serving_requests(n=args.serve_requests, rate=rate, batch_max=512,
-                                           horizon_max=3000, nb_max=24, n_max=256)
-        window = max(d["arrival"] for d in descs)
-        offered = sum(d["q0"].shape[0] * d["nsteps"] for d in descs) / max(window, 1e-9)
-        row = {"rate_per_s": rate, "requests": len(descs), "arrival_window_s": window,
-               "offered_traj_steps_s": offered}
-        for name, kw in (("fifo", dict(policy="fifo")), ("sjf", dict(policy="sjf", max_active=96))):
-            reqs = serve.make_requests(copy.deepcopy(descs))
-            srv = serve.Server(nstreams=16, chunk_traj_steps=2e5, mix=args.mix, **kw)
-            st = srv.run(reqs).summary()
-            srv.close()
-            row[name] = {"p50_latency_s": st["p50_latency_s"], "p99_latency_s": st["p99_latency_s"],
-                         "served_traj_steps_s": st["throughput_traj_steps_s"],
-                         "served_over_offered": st["throughput_traj_steps_s"] / offered,
-                         "makespan_s": st["makespan_s"], "gpu_launches": st["gpu_launches"]}
-        rows.append(row)
-    top = rows[-1]["sjf"]
+    for rate in (float(x) for x in args.serve_rates.split(",")):
+        rows.append(serving_window(serve, workloads, args.serve_requests, rate, args.mix, peak,
+                                   plain=False))
+    top = rows[-1]["continuous_batching"]
     line = {
-        "metric": METRIC, "value": top["served_traj_steps_s"], "unit": "traj-steps/s", "n_gpus": 1,
+        "metric": METRIC, "value": top["throughput_traj_steps_s"], "unit": "traj-steps/s", "n_gpus": 1,
         "steps": 1, "warmup": 0, "ms_per_step": 1e3 * top["makespan_s"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"serving windows of {args.serve_requests} Poisson requests per rate "
-                               "(config-1..4 families, batch logU[1,512], horizon logU[1e2,3e3], "
-                               "N-body N<=24, FPUT n<=256)"},
+        "config": {"workload": f"serving windows of {args.serve_requests} Poisson requests per rate, "
+                               + SERVE_DIST},
         "gpu_launches": top["gpu_launches"],
         "serving_rate_sweep": rows,
     }
@@ -760,6 +919,8 @@ def main():
         return run_overhead(args)
     if args.workload == "serving":
         return run_serving_sweep(args)
+    if args.workload == "sweeps":
+        return run_sweeps(args)
 
     import torch
     import torch.distributed as dist
@@ -993,34 +1154,22 @@ def main():
                                 "sample": f"{ncop} copies x {nst} steps, {dt:.1f} s wall on {cores} threads"}
 
     if not args.skip_extras and args.workload == "kepler" and args.serve_requests > 0 and world == 1:
-        # ---- serving (config 5): bounded Poisson window, continuous batching vs plain
-        import copy
-
+        # ---- serving (config 5): a bounded window of the stated arrival
+        # process and distribution, drained; continuous batching vs plain
         from paper_2511_03655_gb300 import serve
-        descs = workloads.serving_requests(n=args.serve_requests, rate=2000.0, batch_max=512,
-                                           horizon_max=3000, nb_max=24, n_max=256)
-        served = serve.make_requests(copy.deepcopy(descs))
-        srv = serve.Server(nstreams=16, chunk_traj_steps=2e5, mix=args.mix)
-        s1 = srv.run(served).summary()
-        srv.close()
-        sjf_r = serve.make_requests(copy.deepcopy(descs))
-        srv = serve.Server(nstreams=16, chunk_traj_steps=2e5, policy="sjf", max_active=96, mix=args.mix)
-        s3 = srv.run(sjf_r).summary()
-        srv.close()
-        plain_r = serve.make_requests(copy.deepcopy(descs))
-        s2 = serve.run_plain(plain_r, mix=args.mix).summary()
-        same = all(np.array_equal(a.q, b.q) and np.array_equal(a.q, c.q)
-                   for a, b, c in zip(served, plain_r, sjf_r))
-        line["serving"] = {
-            "window": f"{args.serve_requests} Poisson requests at 2000/s from the config-1..4 families, "
-                      "batch logU[1,512], horizon logU[1e2,3e3], N-body N<=24, FPUT n<=256 "
-                      "(the full config-5 ranges offer ~100x the GPU's capacity)",
-            "continuous_batching": s1, "continuous_batching_sjf": s3, "plain_per_request": s2,
-            "policies": "continuous_batching: arrival order, all requests share the GPU; "
-                        "continuous_batching_sjf: least estimated work first, at most 96 at once",
-            "mixing": ("fixed-point where compiled (Kepler, Henon-Heiles, wide kernel), FP64 otherwise"
-                       if args.mix else "FP64 FMA chain"),
-            "results_identical_to_plain": bool(same)}
+        sv = serving_window(serve, workloads, args.serve_requests, 2000.0, args.mix, peak_tflops)
+        sv["window"] = (f"the first {args.serve_requests} Poisson arrivals at 2000/s from the "
+                        + SERVE_DIST + ", served to completion (the full process offers about "
+                        "6000x the GPU's capacity: see the rate sweep of --workload serving)")
+        sv["policy"] = ("continuous batching: one pool of shared device state per kernel class "
+                        "(register kernel per (kind, d), wide kernel per size bucket), one launch "
+                        "per busy pool per tick advancing every admitted request")
+        sv["mixing"] = ("fixed-point where compiled (Kepler, wide kernel), FP64 on the N-body "
+                        "register tiles" if args.mix else "FP64 FMA chain")
+        line["serving"] = sv
+
+    if not args.skip_extras and args.workload == "kepler" and world == 1 and not args.no_sublines:
+        line["other_configs"] = sublines()
 
     if rank == 0:
         print(json.dumps(line))

@@ -216,7 +216,9 @@ int irkgl_step(struct irkgl_ctx* ctx, double* q, double* v, double* q_lo, double
  *   nsteps   steps to take in this call (0 = leave the trajectory alone)
  *   H0       in/out reference energy (required when dH_max is given)
  *   h0_init  1 on the first call of a run: H0 is computed at the first step
- *            and written; 0 afterwards: H0 is read
+ *            and written; 0 afterwards: H0 is read, except that an entry
+ *            holding NaN is computed at that trajectory's first step in this
+ *            call (when it takes one) and written
  *   dH_max, iters   in/out running maxima / totals (NULL = not tracked)
  *   status   out: IRKGL_STATUS_* of this call (NULL = not wanted)
  * Errors: IRKGL_ERR_INVALID, IRKGL_ERR_UNSUPPORTED, IRKGL_ERR_CUDA. */
@@ -224,6 +226,36 @@ int irkgl_advance(struct irkgl_ctx* ctx, double* q, double* v, double* q_lo, dou
                   double* r_prev, const double* h, const long long* nsteps, double* H0,
                   int h0_init, double* dH_max, long long* iters, int* status, int batch,
                   void* cuda_stream);
+
+/* irkgl_advance for a batch that mixes many requests of one right-hand-side
+ * kind and dimension (the serving loop's shared state arrays, Sec. 3's
+ * driver loop run for many problems at once): every trajectory may carry its
+ * own parameters, trajectories join the batch between calls, and idle slots
+ * of the arrays are skipped without being touched.
+ *   params        [batch][param_stride] device parameters: trajectory b uses
+ *                 params[b * param_stride ...] (param_stride >= the kind's
+ *                 parameter count, as given to irkgl_create); NULL with
+ *                 param_stride = 0 uses the context's parameters for all
+ *   order         [batch] device list of the slots to advance, -1 for a slot
+ *                 to skip (its arrays are neither read nor written), or NULL
+ *                 for 0..batch-1
+ *   H0            in/out [batch]: an entry holding NaN (a trajectory that
+ *                 joins the batch) is computed at its first step in this call
+ *                 and written; the others are read
+ *   status        in/out [batch] (NULL = not tracked): zero before a
+ *                 trajectory's first call; an entry that is nonzero on entry
+ *                 (IRKGL_STATUS_MAXITER / NONFINITE of an earlier call) marks a
+ *                 trajectory that stopped, which is not advanced again and
+ *                 keeps its status, as in one uninterrupted run
+ *   q .. r_prev, h, nsteps, dH_max, iters as in irkgl_advance.
+ * A trajectory's bits do not depend on what else is in the batch or on how
+ * its steps are split over calls.  Errors: IRKGL_ERR_INVALID (also for
+ * param_stride below the kind's count), IRKGL_ERR_UNSUPPORTED, IRKGL_ERR_CUDA. */
+int irkgl_advance_multi(struct irkgl_ctx* ctx, double* q, double* v, double* q_lo, double* v_lo,
+                        double* r_prev, const double* h, const long long* nsteps,
+                        const double* params, int param_stride, const int* order, double* H0,
+                        double* dH_max, long long* iters, int* status, int batch,
+                        void* cuda_stream);
 
 /* irkgl_advance for a right-hand side that depends on t (IRKGL_RHS_HENON_HEILES_FORCED),
  * with the time carried alongside the state.  Each trajectory starts at
@@ -318,7 +350,9 @@ int irkgl_integrate_host(struct irkgl_ctx* ctx, const double* q0, const double* 
  * in shared memory.  The step is the same as irkgl_integrate's (Eqs.
  * IRK_init2, IRK_FP2, stopping, qnvn2 with compensated sums), starting from
  * R_prev = 0 and lo = 0.
- *   dmax     the largest inst[k].dim (host value; sizes shared memory), 1..1024
+ *   dmax     the largest inst[k].dim (host value; sizes shared memory), 1..1536
+ *            (above 1024 only with 256-thread teams); N-body instances may have
+ *            at most 128 bodies (larger ones get IRKGL_STATUS_BAD_INSTANCE)
  *   params   packed parameters (device)
  *   q0, v0   packed initial states (device)
  *   order    processing order (device permutation of 0..ninst-1) or NULL;
@@ -336,11 +370,19 @@ int irkgl_integrate_ragged(struct irkgl_ctx* ctx, const irkgl_instance* inst, in
  * irkgl_advance): instance k takes nsteps[k] steps (device int64 [ninst];
  * inst[k].nsteps is ignored) from the packed state q, v, q_lo, v_lo, r_prev
  * (all required, in/out), with H0 / h0_init / dH_max / iters as in
- * irkgl_advance (per instance).  Errors as irkgl_integrate_ragged. */
+ * irkgl_advance (per instance; with h0_init = 0 a NaN entry of H0 is computed
+ * at that instance's first step in the call).  status is in/out as in
+ * irkgl_advance_multi: zero it before an instance's first call; an instance
+ * whose entry is nonzero on entry stopped in an earlier call and is not
+ * advanced again.  order (device, [ninst], or NULL for 0..ninst-1) lists the
+ * instances to advance; an entry of -1 is skipped without touching that
+ * instance's memory, so a serving loop can keep idle descriptors in its
+ * arrays.  Errors as irkgl_integrate_ragged. */
 int irkgl_advance_ragged(struct irkgl_ctx* ctx, const irkgl_instance* inst, int ninst, int dmax,
                          const double* params, double* q, double* v, double* q_lo, double* v_lo,
                          double* r_prev, const long long* nsteps, double* H0, int h0_init,
-                         double* dH_max, long long* iters, int* status, void* cuda_stream);
+                         double* dH_max, long long* iters, int* status, const int* order,
+                         void* cuda_stream);
 
 /* Release the context and its device workspace (NULL is ignored). */
 void irkgl_destroy(struct irkgl_ctx* ctx);
@@ -414,11 +456,16 @@ int irkgl_diag_sincos(const double* x, double* out, int n, void* cuda_stream);
  * counter and rewrites the parameters before launching, so calls that
  * overlap on the GPU race on it; serialise them (one stream, or ordering
  * between streams).  The first call on a device looks up the array's device
- * address for that device (cudaGetSymbolAddress); make that first call
- * before any stream capture on that device.
+ * address for that device (cudaGetSymbolAddress) and keeps it for the life
+ * of the process; make that first call before any stream capture on that
+ * device.  The kept address does not survive cudaDeviceReset: do not call
+ * this entry point on a device after resetting it.  As with irkgl_integrate,
+ * the energy monitor is off for the time-dependent kind
+ * IRKGL_RHS_HENON_HEILES_FORCED (dH_max is left at 0).
  *
  * Errors: IRKGL_ERR_INVALID for the same argument errors as irkgl_create /
- * irkgl_integrate, and when f.nparams > IRKGL_NOALLOC_MAX_PARAMS (the
+ * irkgl_integrate (including the first-order kinds, which take the
+ * irkgl_*1 calls), and when f.nparams > IRKGL_NOALLOC_MAX_PARAMS (the
  * parameters must fit the fixed scratch); IRKGL_ERR_UNSUPPORTED;
  * IRKGL_ERR_CUDA. */
 #define IRKGL_NOALLOC_MAX_PARAMS 63

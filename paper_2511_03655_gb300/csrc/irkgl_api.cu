@@ -425,7 +425,7 @@ static int run(irkgl_ctx* c, KArgs& a, cudaStream_t st) {
   const KernelEntry* ke = lpt ? find_kernel(c->kind, c->dim, lpt, c->block, c->mix, layout) : nullptr;
   if (!ke) return IRKGL_ERR_UNSUPPORTED;
   a.counter = c->d_counter;
-  a.params = c->d_params;
+  if (!a.params) a.params = c->d_params;  // else per-trajectory (irkgl_advance_multi)
   a.kmax = c->kmax;
   a.monitor = time_dependent_kind(c->kind) ? 0 : c->monitor;
   a.monitor_local = c->monitor_local;
@@ -508,6 +508,48 @@ int irkgl_advance(irkgl_ctx* c, double* q, double* v, double* q_lo, double* v_lo
   a.H0_io = H0;
   a.h0_init = h0_init ? 1 : 0;
   a.accumulate = 1;
+  const int saved_monitor = c->monitor;
+  if (!dH_max) c->monitor = 0;
+  const int rc = run(c, a, static_cast<cudaStream_t>(stream));
+  c->monitor = saved_monitor;
+  return rc;
+}
+
+int irkgl_advance_multi(irkgl_ctx* c, double* q, double* v, double* q_lo, double* v_lo,
+                        double* r_prev, const double* h, const long long* nsteps,
+                        const double* params, int param_stride, const int* order, double* H0,
+                        double* dH_max, long long* iters, int* status, int batch, void* stream) {
+  if (!c || batch < 0 || param_stride < 0) return IRKGL_ERR_INVALID;
+  if (batch == 0) return IRKGL_OK;
+  if (!q || !v || !q_lo || !v_lo || !r_prev || !nsteps) return IRKGL_ERR_INVALID;
+  if (dH_max && !H0) return IRKGL_ERR_INVALID;
+  if (params ? param_stride < c->nparams : param_stride != 0) return IRKGL_ERR_INVALID;
+  KArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.batch = batch;
+  a.q_in = q;
+  a.v_in = v;
+  a.qlo_in = q_lo;
+  a.vlo_in = v_lo;
+  a.rp_in = r_prev;
+  a.q_out = q;
+  a.v_out = v;
+  a.qlo_out = q_lo;
+  a.vlo_out = v_lo;
+  a.rp_out = r_prev;
+  a.nsteps = nsteps;
+  a.h = h;
+  a.h_all = c->h;
+  a.order = order;
+  a.iters_total = iters;
+  a.dH_max = dH_max;
+  a.status = status;
+  a.H0_io = H0;
+  a.h0_init = 0;  // per trajectory: a NaN entry of H0 is computed at its first step
+  a.accumulate = 1;
+  a.params = params;
+  a.param_stride = params ? param_stride : 0;
+  a.sticky_status = 1;
   const int saved_monitor = c->monitor;
   if (!dH_max) c->monitor = 0;
   const int rc = run(c, a, static_cast<cudaStream_t>(stream));
@@ -721,26 +763,29 @@ int irkgl_integrate(irkgl_ctx* c, const double* q0, const double* v0, int batch,
 static int run_wide(irkgl_ctx* c, irkgl::WideArgs& a, int ninst, int dmax, cudaStream_t st) {
   static_assert(sizeof(irkgl_instance) == sizeof(irkgl::WideInstance), "instance layout");
   if (dmax < 1) return IRKGL_ERR_INVALID;
-  if (dmax > 1024) return IRKGL_ERR_UNSUPPORTED;
+  if (dmax > 1536) return IRKGL_ERR_UNSUPPORTED;
   if (c->mix && !c->default_tables) return IRKGL_ERR_UNSUPPORTED;  // fixed point: built-in tables
   // team shape: the requested team size, else 256-thread teams (the
   // right-hand side runs team-parallel over (stage, body or particle), and
   // the autotuner measured the 256-thread team within a few per cent of the
   // best for every size bucket on GB300); the first shape of that team size
-  // whose threads x slots cover dmax
+  // whose threads x slots cover dmax and whose shared memory fits
   const irkgl::WideShape* shapes = nullptr;
   const int ns = irkgl::wide_shapes(&shapes);
   const irkgl::WideShape* ws = nullptr;
   const int want_team = c->wide_team ? c->wide_team : 256;
+  size_t smem = 0;
   for (int i = 0; i < ns && !ws; i++) {
     const irkgl::WideShape& x = shapes[i];
     if (x.team * x.slots < dmax) continue;
-    if (x.team == want_team && x.mix == c->mix) ws = &x;
+    if (x.team != want_team || x.mix != c->mix) continue;
+    const size_t need_smem = irkgl::wide_smem_bytes(x.block / x.team, dmax, x.cvs);
+    if (need_smem > 227 * 1024) continue;
+    ws = &x;
+    smem = need_smem;
   }
   if (!ws) return IRKGL_ERR_UNSUPPORTED;
   const int teams = ws->block / ws->team;
-  const size_t smem = irkgl::wide_smem_bytes(teams, dmax);
-  if (smem > 227 * 1024) return IRKGL_ERR_UNSUPPORTED;
   IRKGL_CUDA(cudaFuncSetAttribute(ws->fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   static_cast<int>(smem)));
   int per_sm = 0;
@@ -789,7 +834,8 @@ int irkgl_integrate_ragged(irkgl_ctx* c, const irkgl_instance* inst, int ninst, 
 int irkgl_advance_ragged(irkgl_ctx* c, const irkgl_instance* inst, int ninst, int dmax,
                          const double* params, double* q, double* v, double* q_lo, double* v_lo,
                          double* r_prev, const long long* nsteps, double* H0, int h0_init,
-                         double* dH_max, long long* iters, int* status, void* stream) {
+                         double* dH_max, long long* iters, int* status, const int* order,
+                         void* stream) {
   if (!c || ninst < 0) return IRKGL_ERR_INVALID;
   if (ninst == 0) return IRKGL_OK;
   if (!inst || !params || !q || !v || !q_lo || !v_lo || !r_prev || !nsteps) return IRKGL_ERR_INVALID;
@@ -816,6 +862,8 @@ int irkgl_advance_ragged(irkgl_ctx* c, const irkgl_instance* inst, int ninst, in
   a.dH_max = dH_max;
   a.iters_total = iters;
   a.status = status;
+  a.sticky_status = 1;
+  a.order = order;
   return run_wide(c, a, ninst, dmax, static_cast<cudaStream_t>(stream));
 }
 
@@ -917,7 +965,11 @@ std::mutex g_noalloc_mu;
 double* g_noalloc_ptr[kNoallocMaxDevices] = {nullptr};
 
 // Device address of the scratch array on the current device, looked up once
-// per device (host code sees only a host-side stand-in for the symbol).
+// per device (host code sees only a host-side stand-in for the symbol).  The
+// cached address belongs to the device's current context: after
+// cudaDeviceReset (or any other teardown of the primary context) the module
+// is loaded again and the array may move, so a process that resets a device
+// must not call irkgl_integrate_noalloc on it afterwards.
 int noalloc_scratch(double** out) {
   int dev = 0;
   IRKGL_CUDA(cudaGetDevice(&dev));
@@ -943,11 +995,12 @@ extern "C" int irkgl_integrate_noalloc(irkgl_rhs f, int dim, double h, const dou
   if (!std::isfinite(h) || h == 0.0) return IRKGL_ERR_INVALID;
   int rc = check_rhs(f, dim);
   if (rc != IRKGL_OK) return rc;
+  if (first_order_kind(f.kind)) return IRKGL_ERR_INVALID;  // the second-order form only
   if (f.nparams > IRKGL_NOALLOC_MAX_PARAMS) return IRKGL_ERR_INVALID;  // beyond the scratch capacity
   if (batch == 0) return IRKGL_OK;
   if (!q0 || !v0 || !out->q || !out->v) return IRKGL_ERR_INVALID;
   if (!nsteps && nsteps_all < 0) return IRKGL_ERR_INVALID;
-  const int lpt = default_lpt(f.kind, dim);
+  const int lpt = default_lpt(f.kind, dim, /*nst=*/8, /*mix=*/0);
   const int block = 128;
   const KernelEntry* ke = lpt ? find_kernel(f.kind, dim, lpt, block) : nullptr;
   if (!ke) return IRKGL_ERR_UNSUPPORTED;
@@ -974,7 +1027,7 @@ extern "C" int irkgl_integrate_noalloc(irkgl_rhs f, int dim, double h, const dou
   std::memset(&a, 0, sizeof(a));
   a.batch = batch;
   a.kmax = 100;
-  a.monitor = 1;
+  a.monitor = time_dependent_kind(f.kind) ? 0 : 1;  // H(t) is not conserved
   a.q_in = q0;
   a.v_in = v0;
   a.q_out = out->q;

@@ -89,6 +89,13 @@ __global__ void __launch_bounds__(BLOCK, MINB)
             itot = 0;
             dHmax = 0.0;
             N = a.nsteps ? a.nsteps[t] : a.nsteps_all;
+            if (a.sticky_status && a.status) {
+              const int s0 = a.status[t];
+              if (s0 != ST_OK) {  // a failure is final: keep the status, take no step
+                st = s0;
+                N = 0;
+              }
+            }
             h = a.h ? a.h[t] : a.h_all;
             if (a.accumulate) {
               if (a.dH_max) dHmax = a.dH_max[t];
@@ -100,6 +107,7 @@ __global__ void __launch_bounds__(BLOCK, MINB)
               Hprev = H0;
               invHprev = invH0;
             }
+            if (a.param_stride) rhs.load_params(a.params + static_cast<size_t>(t) * a.param_stride);
             const size_t off = static_cast<size_t>(t) * 2 + r;
             qh = a.q_in[off];
             vh = a.v_in[off];
@@ -120,7 +128,7 @@ __global__ void __launch_bounds__(BLOCK, MINB)
 
     // ---------------- H_0 before the first step (exact ballot of the lanes)
     {
-      const bool want = active && n == 0 && a.monitor > 0 && (!a.H0_io || a.h0_init);
+      const bool want = active && n == 0 && a.monitor > 0 && (!a.H0_io || a.h0_init || (H0 != H0 && N > 0));
       const unsigned h0mask = __ballot_sync(FULL, want);
       if (want) {
         H0 = energy(h0mask);

@@ -70,8 +70,14 @@ struct KArgs {
   long long* steps_done;    // [batch] or null
   unsigned int* counter;    // work counter, zero at launch
   const double* params;     // right-hand-side parameters (device)
-  double* H0_io;            // [batch] reference energy: read, or written when h0_init
+  double* H0_io;            // [batch] reference energy: read, or written when h0_init; an
+                            // entry that is NaN is computed at the trajectory's first step
+                            // of the call and written (a trajectory joining a running batch)
   int h0_init;              // 1: compute H0 at the first step and store it in H0_io
+  int param_stride;         // 0: params serve every trajectory; else trajectory t reads its
+                            // own at params + t * param_stride
+  int sticky_status;        // 1: status is in/out; a trajectory whose entry is nonzero on
+                            // entry stopped in an earlier call and is not advanced again
   int accumulate;           // 1: dH_max / iters_total start from the values in the arrays
   int monitor_local;        // 1: dH_max = max_n |(H_n - H_{n-1}) / H_{n-1}| (Eq. DHlocmax)
   // time t_n as a compensated pair, read only by time-dependent right-hand
@@ -1001,6 +1007,13 @@ __global__ void __launch_bounds__(BLOCK, MINB)
             itot = 0;
             dHmax = 0.0;
             N = a.nsteps ? a.nsteps[t] : a.nsteps_all;
+            if (a.sticky_status && a.status) {
+              const int s0 = a.status[t];
+              if (s0 != ST_OK) {  // a failure is final: keep the status, take no step
+                st = s0;
+                N = 0;
+              }
+            }
             h = a.h ? a.h[t] : a.h_all;
             if (a.accumulate) {
               if (a.dH_max) dHmax = a.dH_max[t];
@@ -1012,6 +1025,7 @@ __global__ void __launch_bounds__(BLOCK, MINB)
               Hprev = H0;
               invHprev = invH0;
             }
+            if (a.param_stride) rhs.load_params(a.params + static_cast<size_t>(t) * a.param_stride);
             const size_t off = static_cast<size_t>(t) * D;
 #pragma unroll
             for (int s = 0; s < NS; s++) {
@@ -1046,7 +1060,7 @@ __global__ void __launch_bounds__(BLOCK, MINB)
     // step.  The groups that need it differ from warp iteration to iteration,
     // so the shuffles inside run under the ballot of exactly those lanes.
     {
-      const bool want = active && n == 0 && a.monitor > 0 && (!a.H0_io || a.h0_init);
+      const bool want = active && n == 0 && a.monitor > 0 && (!a.H0_io || a.h0_init || (H0 != H0 && N > 0));
       const unsigned h0mask = __ballot_sync(FULL, want);
       if (want) {
         H0 = group_energy<Rhs, LPT, NS>(rhs, qh, vh, h0mask, gbase, r);

@@ -21,6 +21,13 @@
 
 namespace irkgl {
 
+// Largest N-body instance the wide kernel takes (its per-stage body weights
+// are staged in shared memory); a larger one gets IRKGL_STATUS_BAD_INSTANCE.
+constexpr int kWideMaxBodies = 128;
+__host__ __device__ constexpr int wide_nbmax(int dmax) {
+  return (dmax / 3 < kWideMaxBodies ? dmax / 3 : kWideMaxBodies) + 1;
+}
+
 // One instance of a ragged batch (mirrors irkgl_instance in irkgl.h).
 struct WideInstance {
   int kind;
@@ -57,17 +64,20 @@ struct WideArgs {
   const double* vlo_in;
   const double* rp_in;
   const long long* nsteps_call;  // [ninst] steps for this call, overrides inst.nsteps
-  double* H0_io;
+  double* H0_io;  // an entry that is NaN is computed at this call's first step
   int h0_init;
   int accumulate;
   int monitor_local;  // dH_max = max_n |(H_n - H_{n-1}) / H_{n-1}|
+  int sticky_status;  // status in/out: an instance with a nonzero entry is not advanced
 };
 
 // Compiled team shapes (k_wide.cu): one warp per instance (small d) or the
-// whole block, SLOTS components per thread, FP64 or fixed-point mixing.
+// whole block, SLOTS components per thread, FP64 or fixed-point mixing,
+// c_i v kept in shared memory or formed again where it is used.
 struct WideShape {
   int team, block, slots;
   int mix;  // 0: FP64 FMA mixing, 1: fixed-point mixing
+  int cvs;  // 1: c_i v in shared memory; 0: recomputed (same bits, less shared memory)
   const void* fn;
   void (*launch)(dim3, dim3, size_t, cudaStream_t, const WideArgs&, const Coef&);
 };
@@ -195,7 +205,11 @@ __device__ __forceinline__ double team_energy_part(int kind, int d, const double
 // MIX = 1: the stage mixing of Eq. Qi2 and the initial guess as exact
 // fixed-point sums on the integer pipes, rounded once (the register kernel's
 // fixed-point form, per owned component).
-template <int TEAM, int BLOCK, int SLOTS, int MIX = 0>
+// CVS = 1: c_i v of the owned components is stored once per step in shared
+// memory; CVS = 0 forms the same product again at each use (one FP64
+// multiply, identical bits), which frees 8 d doubles of shared memory per
+// team so that chains up to d = 1536 fit one block.
+template <int TEAM, int BLOCK, int SLOTS, int MIX = 0, int CVS = 1>
 __global__ void __launch_bounds__(BLOCK)
     irkgl_wide_kernel(const __grid_constant__ WideArgs a, const __grid_constant__ Coef cf) {
   static_assert(TEAM == 32 || TEAM == BLOCK, "a team is one warp or the whole block");
@@ -204,13 +218,13 @@ __global__ void __launch_bounds__(BLOCK)
   const int team = threadIdx.x / TEAM;
   const int tid = threadIdx.x - team * TEAM;
   const int dmax = a.dmax;
-  // per team: Q, R, cv [8][dmax]; w8 [8 + 8 * nb]; qs, vs [dmax]; red [32]
-  const int nbmax = dmax / 3 + 1;
-  const int per_team = 3 * S * dmax + (S + S * nbmax) + 2 * dmax + 32;
+  // per team: Q, R [, cv] [8][dmax]; w8 [8 + 8 * nb]; qs, vs [dmax]; red [32]
+  const int nbmax = wide_nbmax(dmax);
+  const int per_team = (CVS ? 3 : 2) * S * dmax + (S + S * nbmax) + 2 * dmax + 32;
   double* Q = smem + team * per_team;
   double* R = Q + S * dmax;
-  double* CV = R + S * dmax;
-  double* w8 = CV + S * dmax;
+  double* CV = R + S * dmax;  // used only when CVS
+  double* w8 = CV + (CVS ? S * dmax : 0);
   double* qs = w8 + S + S * nbmax;
   double* vs = qs + dmax;
   double* red = vs + dmax;
@@ -231,7 +245,8 @@ __global__ void __launch_bounds__(BLOCK)
     const int d = in.dim;
     // descriptor checks (no memory of a rejected instance is touched)
     bool ok_desc = d >= 1 && d <= dmax && d <= TEAM * SLOTS && in.nsteps >= 0 && in.nparams >= 1;
-    if (in.kind == IRKGL_RHS_NBODY) ok_desc = ok_desc && (d % 3 == 0) && in.nparams >= 1 + d / 3;
+    if (in.kind == IRKGL_RHS_NBODY)
+      ok_desc = ok_desc && (d % 3 == 0) && d / 3 <= kWideMaxBodies && in.nparams >= 1 + d / 3;
     else ok_desc = ok_desc && (in.kind == IRKGL_RHS_FPUT || in.kind == IRKGL_RHS_HARMONIC);
     if (!ok_desc) {
       if (tid == 0) {
@@ -243,7 +258,15 @@ __global__ void __launch_bounds__(BLOCK)
     }
     const double* p = a.params + in.param_offset;
     const double h = in.h;
-    const long long N = a.nsteps_call ? a.nsteps_call[t] : in.nsteps;
+    long long N = a.nsteps_call ? a.nsteps_call[t] : in.nsteps;
+    int st = ST_OK;
+    if (a.sticky_status && a.status) {
+      const int s0 = a.status[t];
+      if (s0 != ST_OK) {  // stopped in an earlier call: a failure is final
+        st = s0;
+        N = 0;
+      }
+    }
     const size_t off = static_cast<size_t>(in.offset);
 
     // load owned components, Rprev (zero for a fresh run), per-stage weights
@@ -271,10 +294,13 @@ __global__ void __launch_bounds__(BLOCK)
       if (a.dH_max) dHmax = a.dH_max[t];
       if (a.iters_total) itot = a.iters_total[t];
     }
+    bool have_h0 = false;
     if (a.H0_io && !a.h0_init) {
       H0 = a.H0_io[t];
       invH0 = 1.0 / H0;
-    } else if (a.monitor > 0 && N > 0) {
+      have_h0 = (H0 == H0);  // NaN: a trajectory joining a running batch
+    }
+    if (!have_h0 && a.monitor > 0 && N > 0) {
 #pragma unroll
       for (int s = 0; s < SLOTS; s++) {
         const int l = tid + s * TEAM;
@@ -292,7 +318,6 @@ __global__ void __launch_bounds__(BLOCK)
     team_sync<TEAM>();
 
     long long n = 0;
-    int st = ST_OK;
     while (n < N) {
       // init (fused Eq. IRK_init2): owner threads, all 8 stages of their components
 #pragma unroll
@@ -309,7 +334,7 @@ __global__ void __launch_bounds__(BLOCK)
 #pragma unroll
             for (int i = 0; i < S; i++) {
               const double cvil = cf.c[i] * vh[s];
-              CV[i * d + l] = cvil;
+              if constexpr (CVS) CV[i * d + l] = cvil;
               double T = fixed_row<true>(i, rb, emax);
               if (nf) T = __longlong_as_double(0x7ff8000000000000LL);
               Q[i * d + l] = fma(h, cvil + T, qh[s]);
@@ -318,7 +343,7 @@ __global__ void __launch_bounds__(BLOCK)
 #pragma unroll
             for (int i = 0; i < S; i++) {
               const double cvil = cf.c[i] * vh[s];
-              CV[i * d + l] = cvil;
+              if constexpr (CVS) CV[i * d + l] = cvil;
               double acc = cvil;
 #pragma unroll
               for (int j = 0; j < S; j++) acc = fma(cf.W[i * S + j], Rj[j], acc);
@@ -352,14 +377,15 @@ __global__ void __launch_bounds__(BLOCK)
               for (int i = 0; i < S; i++) {
                 double T = fixed_row<false>(i, rb, emax);
                 if (nf) T = __longlong_as_double(0x7ff8000000000000LL);
-                const double qn = fma(h, CV[i * d + l] + T, qh[s]);
+                const double cvil = CVS ? CV[i * d + l] : cf.c[i] * vh[s];
+                const double qn = fma(h, cvil + T, qh[s]);
                 dl = umax64(dl, abs_bits(qn - Q[i * d + l]));
                 Q[i * d + l] = qn;
               }
             } else {
 #pragma unroll
               for (int i = 0; i < S; i++) {
-                double acc = CV[i * d + l];
+                double acc = CVS ? CV[i * d + l] : cf.c[i] * vh[s];
 #pragma unroll
                 for (int j = 0; j < S; j++) acc = fma(cf.eta[i * S + j], Rj[j], acc);
                 const double qn = fma(h, acc, qh[s]);
@@ -454,9 +480,9 @@ __global__ void __launch_bounds__(BLOCK)
 }
 
 // shared memory bytes per block for a given dmax
-__host__ __device__ inline size_t wide_smem_bytes(int teams, int dmax) {
-  const int nbmax = dmax / 3 + 1;
-  const size_t per_team = 3 * S * dmax + (S + S * nbmax) + 2 * dmax + 32;
+__host__ __device__ inline size_t wide_smem_bytes(int teams, int dmax, int cvs = 1) {
+  const int nbmax = wide_nbmax(dmax);
+  const size_t per_team = (cvs ? 3 : 2) * S * dmax + (S + S * nbmax) + 2 * dmax + 32;
   return static_cast<size_t>(teams) * per_team * sizeof(double);
 }
 

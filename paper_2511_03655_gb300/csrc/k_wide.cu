@@ -7,16 +7,17 @@
 namespace irkgl {
 
 
-template <int TEAM, int BLOCK, int SLOTS, int MIX>
+template <int TEAM, int BLOCK, int SLOTS, int MIX, int CVS>
 void wide_launch(dim3 g, dim3 b, size_t smem, cudaStream_t st, const WideArgs& a, const Coef& c) {
-  irkgl_wide_kernel<TEAM, BLOCK, SLOTS, MIX><<<g, b, smem, st>>>(a, c);
+  irkgl_wide_kernel<TEAM, BLOCK, SLOTS, MIX, CVS><<<g, b, smem, st>>>(a, c);
 }
 
-#define IRKGL_WIDE_MIX(TEAM, BLOCK, SLOTS, MIX)                                                      \
+#define IRKGL_WIDE_SHAPE(TEAM, BLOCK, SLOTS, MIX, CVS)                                                \
   WideShape {                                                                                       \
-    TEAM, BLOCK, SLOTS, MIX, (const void*)irkgl_wide_kernel<TEAM, BLOCK, SLOTS, MIX>,               \
-        wide_launch<TEAM, BLOCK, SLOTS, MIX>                                                        \
+    TEAM, BLOCK, SLOTS, MIX, CVS, (const void*)irkgl_wide_kernel<TEAM, BLOCK, SLOTS, MIX, CVS>,     \
+        wide_launch<TEAM, BLOCK, SLOTS, MIX, CVS>                                                   \
   }
+#define IRKGL_WIDE_MIX(TEAM, BLOCK, SLOTS, MIX) IRKGL_WIDE_SHAPE(TEAM, BLOCK, SLOTS, MIX, 1)
 #define IRKGL_WIDE(TEAM, BLOCK, SLOTS) IRKGL_WIDE_MIX(TEAM, BLOCK, SLOTS, 0)
 
 static const WideShape kWide[] = {
@@ -26,12 +27,14 @@ static const WideShape kWide[] = {
     IRKGL_WIDE(128, 128, 4),   // d <= 512
     IRKGL_WIDE(256, 256, 2),   // d <= 512
     IRKGL_WIDE(256, 256, 4),   // d <= 1024
+    IRKGL_WIDE_SHAPE(256, 256, 6, 0, 0),  // d <= 1536, c_i v recomputed (shared memory)
     // fixed-point stage mixing (IRKGL_OPT_MIX = 1)
     IRKGL_WIDE_MIX(32, 128, 2, 1),
     IRKGL_WIDE_MIX(64, 64, 4, 1),
     IRKGL_WIDE_MIX(128, 128, 4, 1),
     IRKGL_WIDE_MIX(256, 256, 2, 1),
     IRKGL_WIDE_MIX(256, 256, 4, 1),
+    IRKGL_WIDE_SHAPE(256, 256, 6, 1, 0),
 };
 
 int wide_shapes(const WideShape** out) {

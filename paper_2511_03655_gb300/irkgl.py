@@ -14,6 +14,7 @@ import ctypes
 import os
 from dataclasses import dataclass
 
+import numpy as np
 import torch
 
 from . import build as _build
@@ -36,7 +37,7 @@ EXPORTS = ("irkgl_default_coeffs", "irkgl_create", "irkgl_set_option", "irkgl_st
            "irkgl_integrate", "irkgl_integrate_host", "irkgl_destroy", "irkgl_strerror",
            "irkgl_last_cuda_error", "irkgl_get_tile", "irkgl_probe_fp64_fma",
            "irkgl_integrate_noalloc", "irkgl_integrate_ragged", "irkgl_advance",
-           "irkgl_advance_ragged", "irkgl_diag_fixed_mix",
+           "irkgl_advance_multi", "irkgl_advance_ragged", "irkgl_diag_fixed_mix",
            "irkgl_diag_fixed_mix_rows", "irkgl_diag_rinv", "irkgl_diag_sincos")
 NOALLOC_MAX_PARAMS = 63
 
@@ -120,7 +121,9 @@ def load(path: str | None = None, build_if_missing: bool = False):
     L.irkgl_diag_rinv.argtypes = [_P, _P, ctypes.c_int, _P]
     L.irkgl_diag_sincos.argtypes = [_P, _P, ctypes.c_int, _P]
     L.irkgl_advance_ragged.argtypes = [_P, _P, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P, _P,
-                                       _P, _P, ctypes.c_int, _P, _P, _P, _P]
+                                       _P, _P, ctypes.c_int, _P, _P, _P, _P, _P]
+    L.irkgl_advance_multi.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int, _P, _P,
+                                      _P, _P, _P, ctypes.c_int, _P]
     L.irkgl_integrate_ragged.argtypes = [_P, _P, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P,
                                          ctypes.POINTER(irkgl_outputs), _P]
     L.irkgl_integrate_noalloc.argtypes = [irkgl_rhs, ctypes.c_int, ctypes.c_double, _P, _P,
@@ -129,8 +132,9 @@ def load(path: str | None = None, build_if_missing: bool = False):
     for name in ("irkgl_default_coeffs", "irkgl_create", "irkgl_set_option", "irkgl_step",
                  "irkgl_integrate", "irkgl_integrate_host", "irkgl_get_tile",
                  "irkgl_probe_fp64_fma", "irkgl_integrate_noalloc", "irkgl_integrate_ragged",
-                 "irkgl_advance", "irkgl_advance_ragged", "irkgl_diag_fixed_mix",
-                 "irkgl_diag_fixed_mix_rows", "irkgl_diag_rinv", "irkgl_diag_sincos"):
+                 "irkgl_advance", "irkgl_advance_multi", "irkgl_advance_ragged",
+                 "irkgl_diag_fixed_mix", "irkgl_diag_fixed_mix_rows", "irkgl_diag_rinv",
+                 "irkgl_diag_sincos"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -385,16 +389,27 @@ def irkgl_integrate_host(ctx: int, dim: int, q0, v0, out: Outputs, nsteps=None,
         ctypes.byref(st), _stream(stream)))
 
 
+# irkgl_instance as a numpy record (the C struct's natural alignment, 40 bytes)
+INSTANCE_DTYPE = np.dtype({"names": ["kind", "dim", "offset", "param_offset", "nparams", "h", "nsteps"],
+                           "formats": [np.int32, np.int32, np.int64, np.int32, np.int32, np.float64,
+                                       np.int64],
+                           "offsets": [0, 4, 8, 16, 20, 24, 32], "itemsize": 40})
+
+
+def instances_array(w: dict) -> np.ndarray:
+    """A ragged batch description (arrays kind, dim, offset, param_offset,
+    nparams, h, nsteps) as irkgl_instance records (numpy, host)."""
+    n = len(w["kind"])
+    rec = np.zeros(n, dtype=INSTANCE_DTYPE)
+    for name in INSTANCE_DTYPE.names:
+        rec[name] = np.asarray(w[name])
+    return rec
+
+
 def instances_tensor(w: dict, device) -> torch.Tensor:
     """Pack a ragged batch description (arrays kind, dim, offset, param_offset,
     nparams, h, nsteps) into a device byte tensor of irkgl_instance records."""
-    n = len(w["kind"])
-    arr = (irkgl_instance * n)()
-    for k in range(n):
-        arr[k] = irkgl_instance(int(w["kind"][k]), int(w["dim"][k]), int(w["offset"][k]),
-                                int(w["param_offset"][k]), int(w["nparams"][k]), float(w["h"][k]),
-                                int(w["nsteps"][k]))
-    raw = torch.frombuffer(bytearray(bytes(arr)), dtype=torch.uint8)
+    raw = torch.from_numpy(instances_array(w).view(np.uint8).copy())
     if torch.device(device).type == "cuda":
         return raw.pin_memory().to(device, non_blocking=True)
     return raw.to(device)
@@ -502,8 +517,9 @@ def irkgl_integrate_ragged(ctx: int, inst: torch.Tensor, ninst: int, dmax: int, 
 
 def irkgl_advance_ragged(ctx: int, inst: torch.Tensor, ninst: int, dmax: int, params, q, v, q_lo,
                          v_lo, r_prev, nsteps, H0=None, h0_init: bool = False, dH_max=None,
-                         iters=None, status=None, stream=None):
-    """Continue a ragged batch in place (packed device tensors); nsteps int64 [ninst]."""
+                         iters=None, status=None, order=None, stream=None):
+    """Continue a ragged batch in place (packed device tensors); nsteps int64
+    [ninst]; order int32 [ninst] (-1 entries skipped) or None."""
     f64 = torch.float64
     _check(load().irkgl_advance_ragged(
         _P(ctx), _ptr(inst, torch.uint8, None, "inst"), int(ninst), int(dmax),
@@ -512,7 +528,28 @@ def irkgl_advance_ragged(ctx: int, inst: torch.Tensor, ninst: int, dmax: int, pa
         _ptr(r_prev, f64, None, "r_prev"), _ptr(nsteps, torch.int64, (ninst,), "nsteps"),
         _ptr(H0, f64, (ninst,), "H0"), int(bool(h0_init)), _ptr(dH_max, f64, (ninst,), "dH_max"),
         _ptr(iters, torch.int64, (ninst,), "iters"), _ptr(status, torch.int32, (ninst,), "status"),
-        _stream(stream)))
+        _ptr(order, torch.int32, (ninst,), "order"), _stream(stream)))
+
+
+def irkgl_advance_multi(ctx: int, dim: int, q, v, q_lo, v_lo, r_prev, nsteps, h=None, params=None,
+                        param_stride: int = 0, order=None, H0=None, dH_max=None, iters=None,
+                        status=None, stream=None):
+    """Continue trajectories of many requests of one kind and dimension in
+    place (device tensors [B, dim], r_prev [B, 8, dim]); params [B, stride]
+    per trajectory or None; order int32 [B] (-1 entries skipped) or None; a
+    NaN entry of H0 is computed at that trajectory's first step."""
+    B = q.shape[0]
+    f64 = torch.float64
+    P = int(param_stride)
+    _check(load().irkgl_advance_multi(
+        _P(ctx), _ptr(q, f64, (B, dim), "q"), _ptr(v, f64, (B, dim), "v"),
+        _ptr(q_lo, f64, (B, dim), "q_lo"), _ptr(v_lo, f64, (B, dim), "v_lo"),
+        _ptr(r_prev, f64, (B, 8, dim), "r_prev"), _ptr(h, f64, (B,), "h"),
+        _ptr(nsteps, torch.int64, (B,), "nsteps"),
+        _ptr(params, f64, (B, P) if params is not None else None, "params"), P,
+        _ptr(order, torch.int32, (B,), "order"), _ptr(H0, f64, (B,), "H0"),
+        _ptr(dH_max, f64, (B,), "dH_max"), _ptr(iters, torch.int64, (B,), "iters"),
+        _ptr(status, torch.int32, (B,), "status"), B, _stream(stream)))
 
 
 def irkgl_integrate_noalloc(kind: int, params, dim: int, h: float, q0, v0, out: Outputs,

@@ -31,8 +31,8 @@ import torch
 from . import irkgl
 
 # Size buckets: N-body by body count N = d/3, FPUT and harmonic by d.
-NBODY_BUCKETS = ((3, 8), (9, 16), (17, 32), (33, 64), (65, 341))
-CHAIN_BUCKETS = ((1, 64), (65, 128), (129, 256), (257, 512), (513, 1024))
+NBODY_BUCKETS = ((3, 8), (9, 16), (17, 32), (33, 64), (65, 128))
+CHAIN_BUCKETS = ((1, 64), (65, 128), (129, 256), (257, 512), (513, 1024), (1025, 1536))
 INSTANCE_BYTES = 40  # sizeof(irkgl_instance)
 
 

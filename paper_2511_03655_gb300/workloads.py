@@ -312,9 +312,15 @@ def _logu(u, lo, hi):
 
 
 def serving_requests(n: int = 200, rate: float = 2000.0, seed_id: int = 5, batch_max: int = 4096,
-                     horizon_max: int = 100000, nb_max: int = 64, n_max: int = 1024,
+                     horizon_max: int = 100000, nb_max: int = 64, n_max: int = 1536,
                      families=("kepler", "nbody6", "nbody", "fput")):
-    """Request descriptions for the serving loop (dicts; see serve.Request)."""
+    """Request descriptions for the serving loop (dicts; see serve.Request).
+
+    Poisson arrivals at `rate`; each request picks a family of the Kepler
+    ensemble, the 6-body ensemble, the ragged batch's N-body systems (N in
+    {3..nb_max}) or its FPUT chains (n in {8..n_max}), with batch ~
+    logU[1, batch_max] and horizon ~ logU[1e2, horizon_max] steps.  The
+    defaults are the full ranges (D = 2d up to 3072)."""
     u = uniform(SEED_BASE + seed_id, 8 * n).reshape(n, 8)
     t = np.cumsum(-np.log(1.0 - u[:, 0]) / rate)  # exponential inter-arrival times
     out = []
@@ -334,7 +340,7 @@ def serving_requests(n: int = 200, rate: float = 2000.0, seed_id: int = 5, batch
             req = dict(kind="nbody", params=w["params"], dim=18, q0=w["q0"], v0=w["v0"],
                        h=float(w["h"][0]), nsteps=T)
         elif fam == "nbody":
-            nb = 7 + int(u[k, 4] * (nb_max - 6))
+            nb = 3 + int(u[k, 4] * (nb_max - 2))
             w = nbody_ensemble(copies=B, nbodies=nb, steps=T, seed_id=sid)
             req = dict(kind="nbody", params=w["params"], dim=3 * nb, q0=w["q0"], v0=w["v0"],
                        h=float(w["h"][0]), nsteps=T)

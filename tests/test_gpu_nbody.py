@@ -2,9 +2,10 @@
 
   * states over steps 1..10 within 1e-13 relative, sweep counts within +-1
     over the first 1,000 steps (perturbed copies of the system);
-  * chaotic-run criterion: over 64 copies x 10,000 steps the median, p90 and
-    max of max_n |dH/H| agree with the oracle's within a factor of 2, and are
-    <= 1e-13 where the oracle's are;
+  * chaotic-run criterion: over 64 copies x 10,000 steps, and over 128
+    copies at the configuration's full horizon of 100,000 steps, the median,
+    p90 and max of max_n |dH/H| agree with the oracle's within a factor of 2,
+    and are <= 1e-13 where the oracle's are;
   * chunked stepping == one persistent launch, bitwise; N = 3..5 variants.
 
 Every test runs with the FP64 stage mixing and with the fixed-point mixing
@@ -92,6 +93,48 @@ def test_nbody_energy_statistics_chaotic_criterion(torch_cuda, mix):
         assert sg <= 2 * so + 2e-15 and so <= 2 * sg + 2e-15, (sg, so)
         if so <= 1e-13:
             assert sg <= 1e-13
+    integ.close()
+
+
+FULL_COPIES, FULL_STEPS = 128, 100000
+
+
+@pytest.fixture(scope="module")
+def full_horizon_oracle():
+    """The oracle over 128 copies of the 6-body ensemble at the full 1e5
+    steps (the accuracy run of the configuration), once for both mixings."""
+    import os
+    w = workloads.nbody_ensemble(copies=FULL_COPIES, steps=FULL_STEPS)
+    r = cbind.run(cbind.NBODY, w["params"], w["q0"], w["v0"], w["h"], FULL_STEPS,
+                  nthreads=os.cpu_count() or 8)
+    return w, r
+
+
+@pytest.mark.parametrize("mix", [0, 1])
+def test_nbody_full_horizon_energy_statistics(torch_cuda, full_horizon_oracle, mix):
+    """1e5 steps (500 inner periods) of 128 perturbed copies: every copy
+    completes on both sides, and the median, p90 and max over the ensemble
+    of max_n |dH/H| agree within a factor of 2 (the chaotic-run criterion),
+    each <= 1e-13 where the oracle's is; the mean sweeps per step agree to
+    2 %."""
+    from paper_2511_03655_gb300 import irkgl
+    torch = torch_cuda
+    w, r = full_horizon_oracle
+    d, h = w["dim"], float(w["h"][0])
+    integ = irkgl.Integrator(irkgl.RHS_NBODY, w["params"], d, h, mix=mix)
+    out = integ.integrate(dev(torch, w["q0"]), dev(torch, w["v0"]), nsteps_all=FULL_STEPS)
+    torch.cuda.synchronize()
+    assert (out.status.cpu().numpy() == 0).all() and (r["status"] == 0).all()
+    assert (out.steps.cpu().numpy() == FULL_STEPS).all()
+    g, o = out.dH_max.cpu().numpy(), r["dH_max"]
+    for stat in (np.median, lambda x: np.percentile(x, 90), np.max):
+        sg, so = stat(g), stat(o)
+        assert sg <= 2 * so + 2e-15 and so <= 2 * sg + 2e-15, (sg, so)
+        if so <= 1e-13:
+            assert sg <= 1e-13
+    kg = out.iters.cpu().numpy().sum() / (FULL_COPIES * FULL_STEPS)
+    ko = r["iters_total"].sum() / (FULL_COPIES * FULL_STEPS)
+    assert abs(kg - ko) <= 0.02 * ko, (kg, ko)
     integ.close()
 
 

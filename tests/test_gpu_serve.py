@@ -1,6 +1,7 @@
 """The continuous-batching server: every request's result is the same alone and
-in the mix (bitwise: a chunked run continues exactly), admission respects the
-memory budget, and results agree with the oracle."""
+in the mix (bitwise: a chunked run continues exactly), the requests of a pool
+share one launch per tick, admission respects each pool's capacity, a
+failure is final, and results agree with the oracle."""
 import copy
 
 import numpy as np
@@ -22,25 +23,30 @@ def server_mod():
     return serve
 
 
-def small_requests(n=14):
-    return workloads.serving_requests(n=n, rate=4000.0, batch_max=64, horizon_max=400, nb_max=12,
+def small_requests(n=14, rate=4000.0):
+    return workloads.serving_requests(n=n, rate=rate, batch_max=64, horizon_max=400, nb_max=12,
                                       n_max=96)
+
+
+def same(a, b, dH=True):
+    ok = np.array_equal(a.q, b.q) and np.array_equal(a.v, b.v) and np.array_equal(a.iters, b.iters)
+    ok = ok and np.array_equal(a.status, b.status)
+    return ok and (np.array_equal(a.dH_max, b.dH_max) if dH else True)
 
 
 def test_result_same_alone_and_in_mix(server_mod):
     serve = server_mod
     descs = small_requests()
     mix = serve.make_requests(copy.deepcopy(descs))
-    st = serve.Server(nstreams=8, chunk_traj_steps=2e3).run(mix)
+    st = serve.Server(target_tick_s=0.002).run(mix)
     assert st.summary()["requests"] == len(descs)
     assert st.max_concurrent > 1  # requests really overlapped
     for d, r in zip(descs, mix):
         alone = serve.make_requests([copy.deepcopy(d)])
-        serve.Server(nstreams=1, chunk_traj_steps=7e2).run(alone)  # different chunking too
+        serve.Server(target_tick_s=0.0003).run(alone)  # different chunking too
         a = alone[0]
         assert (r.status == 0).all() and (a.status == 0).all()
-        assert np.array_equal(r.q, a.q) and np.array_equal(r.v, a.v), d["kind"]
-        assert np.array_equal(r.iters, a.iters) and np.array_equal(r.dH_max, a.dH_max)
+        assert same(r, a), d["kind"]
 
 
 @pytest.mark.parametrize("stage_mix", [0, 1])
@@ -50,31 +56,44 @@ def test_mix_matches_single_launch(server_mod, stage_mix):
     serve = server_mod
     descs = small_requests(8)
     mix = serve.make_requests(copy.deepcopy(descs))
-    serve.Server(nstreams=4, chunk_traj_steps=1e3, mix=stage_mix).run(mix)
+    serve.Server(target_tick_s=0.001, mix=stage_mix).run(mix)
     plain = serve.make_requests(copy.deepcopy(descs))
     serve.run_plain(plain, mix=stage_mix)
     for r, p in zip(mix, plain):
-        assert np.array_equal(r.q, p.q) and np.array_equal(r.v, p.v), r.kind
-        assert np.array_equal(r.iters, p.iters)
+        assert same(r, p), r.kind
 
 
-def test_admission_by_memory_budget(server_mod):
-    """Admitted requests never hold more device memory than the budget (a
-    request larger than the whole budget runs alone), every request
-    completes, and a larger budget admits more at once."""
+def test_one_launch_per_pool_per_tick(server_mod):
+    """Many requests, few pools: every tick launches at most one kernel per
+    pool, so the launches do not grow with the number of requests in flight."""
     serve = server_mod
-    descs = small_requests(10)
+    descs = workloads.serving_requests(n=60, rate=20000.0, batch_max=32, horizon_max=300,
+                                       families=("kepler", "fput"), n_max=60)
     reqs = serve.make_requests(copy.deepcopy(descs))
-    sizes = sorted(r.device_bytes() for r in reqs)
-    budget = sizes[0] + sizes[1]
-    st = serve.Server(mem_budget_bytes=budget, nstreams=4).run(reqs)
-    assert st.summary()["requests"] == 10 and all(r.q is not None for r in reqs)
-    assert st.peak_bytes <= max(budget, sizes[-1])
-    wide_open = serve.make_requests(copy.deepcopy(descs))
-    st2 = serve.Server(mem_budget_bytes=1 << 34, nstreams=4).run(wide_open)
+    srv = serve.Server(target_tick_s=0.002)
+    st = srv.run(reqs).summary()
+    assert st["requests"] == 60
+    assert st["launches_per_tick"] <= st["pools"] <= 2
+    assert st["max_concurrent_requests"] > 10
+    assert st["gpu_launches"] < sum(1 for _ in reqs) * 3  # not one launch per request and chunk
+    assert 0.0 < st["gpu_busy"] <= 1.0
+    srv.close()
+
+
+def test_admission_by_pool_capacity(server_mod):
+    """With pools that hold only a few requests, the others wait for room,
+    every request completes, and the results are those of roomy pools."""
+    serve = server_mod
+    descs = small_requests(12)
+    reqs = serve.make_requests(copy.deepcopy(descs))
+    big = max(r.device_bytes() for r in reqs)
+    st = serve.Server(pool_bytes=1, target_tick_s=0.001).run(reqs)  # each pool: 2x its largest request
+    assert st.summary()["requests"] == 12 and all(r.q is not None for r in reqs)
+    roomy = serve.make_requests(copy.deepcopy(descs))
+    st2 = serve.Server(pool_bytes=64 * big, target_tick_s=0.001).run(roomy)
     assert st2.max_concurrent >= st.max_concurrent
-    for a, b in zip(reqs, wide_open):
-        assert np.array_equal(a.q, b.q)
+    for a, b in zip(reqs, roomy):
+        assert same(a, b)
 
 
 @pytest.mark.parametrize("stage_mix", [0, 1])
@@ -82,7 +101,7 @@ def test_served_results_match_oracle(server_mod, stage_mix):
     serve = server_mod
     descs = [d for d in small_requests(20) if d["kind"] in ("kepler", "fput")][:4]
     reqs = serve.make_requests(copy.deepcopy(descs))
-    serve.Server(nstreams=4, chunk_traj_steps=1e3, mix=stage_mix).run(reqs)
+    serve.Server(target_tick_s=0.001, mix=stage_mix).run(reqs)
     for r in reqs:
         kind = cbind.KEPLER if r.kind == "kepler" else cbind.FPUT
         o = cbind.run(kind, r.params, r.q0, r.v0, r.h, r.nsteps, nthreads=8)
@@ -91,27 +110,23 @@ def test_served_results_match_oracle(server_mod, stage_mix):
         assert (np.abs(g - e).max(axis=1) / np.abs(e).max(axis=1)).max() <= 1e-11, r.kind
 
 
-def test_context_pool_reuse(server_mod):
-    """Contexts return to the pool when a request finishes and are reused:
-    the pool never holds more contexts than requests ran at once, and a
-    second run on the same server creates none."""
+def test_failure_is_final_and_zero_steps(server_mod):
+    """A trajectory that fails (a Kepler collision: non-finite stage values)
+    keeps its status and sweep total across ticks, as in one launch; a
+    request of zero steps returns its initial state."""
     serve = server_mod
-    descs = small_requests(20)
-    srv = serve.Server(nstreams=4, chunk_traj_steps=1e3)
-    st = srv.run(serve.make_requests(copy.deepcopy(descs)))
-    pooled = sum(len(v) for v in srv._pool.values())
-    assert 1 <= pooled <= st.max_concurrent
-    before = {k: list(v) for k, v in srv._pool.items()}
-    again = serve.make_requests(copy.deepcopy(descs))
-    srv2_stats = srv.run(again)
-    after = {k: list(v) for k, v in srv._pool.items()}
-    assert sum(len(v) for v in after.values()) <= max(pooled, srv2_stats.max_concurrent)
-    assert all(set(before[k]) <= set(after.get(k, [])) for k in before)  # the same contexts came back
-    first = serve.make_requests(copy.deepcopy(descs))
-    serve.Server(nstreams=4, chunk_traj_steps=1e3).run(first)
-    for a, b in zip(first, again):
-        assert np.array_equal(a.q, b.q) and np.array_equal(a.iters, b.iters)
-    srv.close()
+    q0 = np.array([[0.0, 0.0], [0.5, 0.0], [0.9, 0.0]])
+    v0 = np.array([[0.0, 0.0], [0.0, np.sqrt(3.0)], [0.0, 1.1]])
+    d = dict(rid=0, kind="kepler", params=[1.0], dim=2, q0=q0, v0=v0, h=2 * np.pi / 200, nsteps=300)
+    z = dict(rid=1, kind="kepler", params=[1.0], dim=2, q0=q0[1:], v0=v0[1:], h=0.01, nsteps=0)
+    served = serve.make_requests([copy.deepcopy(d), copy.deepcopy(z)])
+    serve.Server(target_tick_s=0.0002).run(served)
+    plain = serve.make_requests([copy.deepcopy(d), copy.deepcopy(z)])
+    serve.run_plain(plain)
+    assert served[0].status[0] == 2 and (served[0].status[1:] == 0).all()
+    assert same(served[0], plain[0])
+    assert np.array_equal(served[1].q, q0[1:]) and np.array_equal(served[1].v, v0[1:])
+    assert (served[1].iters == 0).all() and (served[1].status == 0).all()
 
 
 def test_sjf_policy_same_results_and_order(server_mod):
@@ -121,14 +136,33 @@ def test_sjf_policy_same_results_and_order(server_mod):
     serve = server_mod
     descs = small_requests(16)
     a = serve.make_requests(copy.deepcopy(descs))
-    serve.Server(nstreams=4, chunk_traj_steps=1e3).run(a)
+    serve.Server(target_tick_s=0.001).run(a)
     b = serve.make_requests(copy.deepcopy(descs))
-    serve.Server(nstreams=4, chunk_traj_steps=1e3, policy="sjf", max_active=1).run(b)
+    serve.Server(target_tick_s=0.001, policy="sjf", max_active=1).run(b)
     for x, y in zip(a, b):
-        assert np.array_equal(x.q, y.q) and np.array_equal(x.iters, y.iters)
+        assert same(x, y)
     # admission order under one slot: after the first, each admitted request
-    # was the cheapest among those that had arrived
+    # was the cheapest among those that had arrived (and routed to any pool)
     admitted = sorted(b, key=lambda r: r.t_admit)
     for k in range(1, len(admitted)):
-        waiting_then = [r for r in admitted[k:] if r.arrival <= admitted[k].t_admit]
+        waiting_then = [r for r in admitted[k:] if r.arrival <= admitted[k].t_admit
+                        and serve.pool_key(r) == serve.pool_key(admitted[k])]
         assert serve.estimated_flops(admitted[k]) <= min(serve.estimated_flops(r) for r in waiting_then)
+
+
+def test_server_reuse(server_mod):
+    """A server serves a second set of requests with the pools of the first
+    (no state leaks between runs: the results equal a fresh server's)."""
+    serve = server_mod
+    descs = small_requests(10)
+    srv = serve.Server(target_tick_s=0.001)
+    srv.run(serve.make_requests(copy.deepcopy(descs)))
+    pools = dict(srv.pools)
+    again = serve.make_requests(copy.deepcopy(descs))
+    srv.run(again)
+    assert all(srv.pools[k] is p for k, p in pools.items())
+    fresh = serve.make_requests(copy.deepcopy(descs))
+    serve.Server(target_tick_s=0.001).run(fresh)
+    for a, b in zip(again, fresh):
+        assert same(a, b)
+    srv.close()

@@ -152,3 +152,20 @@ def test_sincos_constants():
         s_ref, c_ref = math.sin(math.pi / 2 * f), math.cos(math.pi / 2 * f)
         assert abs(float(Fraction(f) * S) - s_ref) <= 4e-16 * abs(s_ref)
         assert abs(float(C) - c_ref) <= 4e-16
+
+
+def test_instance_record_matches_the_c_struct():
+    """The numpy record the serving loop packs instance descriptors with has
+    the C struct's size and field offsets (irkgl_instance, 40 bytes)."""
+    import ctypes
+
+    from paper_2511_03655_gb300 import irkgl
+    assert irkgl.INSTANCE_DTYPE.itemsize == ctypes.sizeof(irkgl.irkgl_instance) == 40
+    for name, _ in irkgl.irkgl_instance._fields_:
+        assert irkgl.INSTANCE_DTYPE.fields[name][1] == getattr(irkgl.irkgl_instance, name).offset
+    w = {"kind": [2, 3], "dim": [9, 17], "offset": [0, 9], "param_offset": [0, 4], "nparams": [4, 1],
+         "h": [0.01, 0.25], "nsteps": [7, 11]}
+    rec = irkgl.instances_array(w)
+    arr = (irkgl.irkgl_instance * 2)(*[irkgl.irkgl_instance(*(w[f][k] for f, _ in irkgl.irkgl_instance._fields_))
+                                       for k in range(2)])
+    assert rec.tobytes() == bytes(arr)

@@ -65,3 +65,46 @@ def test_noalloc_rejects_parameters_beyond_scratch():
     rc = irkgl.irkgl_integrate_noalloc(irkgl.RHS_NBODY, [1.0] * (n + 1), 3 * n, 0.1, q0, q0, out,
                                        nsteps_all=1)
     assert rc == irkgl.ERR_INVALID
+
+
+def test_noalloc_forced_henon_heiles_matches_regular_entry_point():
+    """The time-dependent kind: both calls start at t = 0 and leave the
+    energy monitor off (H(t) is not conserved), so dH_max stays 0 on both."""
+    import torch
+
+    from paper_2511_03655_gb300 import build, irkgl
+    build.build()
+    irkgl.load()
+    dev = torch.device("cuda")
+    q0n, v0n, _ = workloads.henon_heiles_ensemble(517)
+    q0 = torch.tensor(q0n, device=dev)
+    v0 = torch.tensor(v0n, device=dev)
+    integ = irkgl.Integrator(irkgl.RHS_HENON_HEILES_FORCED, [1.0, 0.1], 2, 0.25)
+    ref = integ.integrate(q0, v0, nsteps_all=150)
+    torch.cuda.synchronize()
+    for _ in range(2):
+        out = irkgl.Outputs.allocate(517, 2, device=dev)
+        rc = irkgl.irkgl_integrate_noalloc(irkgl.RHS_HENON_HEILES_FORCED, [1.0, 0.1], 2, 0.25,
+                                           q0, v0, out, nsteps_all=150)
+        assert rc == irkgl.OK
+        torch.cuda.synchronize()
+        assert _rel(out.q, ref.q) <= 1e-13 and _rel(out.v, ref.v) <= 1e-13
+        assert torch.equal(out.steps, ref.steps) and torch.equal(out.status, ref.status)
+        assert torch.equal(out.iters, ref.iters)
+        assert out.dH_max.abs().max().item() == 0.0 and ref.dH_max.abs().max().item() == 0.0
+    integ.close()
+
+
+def test_noalloc_rejects_first_order_kinds():
+    """First-order kinds take the irkgl_*1 calls, here as in irkgl_create's
+    second-order calls: IRKGL_ERR_INVALID, nothing launched."""
+    import torch
+
+    from paper_2511_03655_gb300 import build, irkgl
+    build.build()
+    irkgl.load()
+    dev = torch.device("cuda")
+    y = torch.ones((4, 2), dtype=torch.float64, device=dev)
+    out = irkgl.Outputs.allocate(4, 2, device=dev)
+    rc = irkgl.irkgl_integrate_noalloc(irkgl.RHS_HARMONIC1, [1.0], 2, 0.1, y, y, out, nsteps_all=1)
+    assert rc == irkgl.ERR_INVALID
