@@ -56,10 +56,27 @@ FLOPS_NBODY6 = (3882, 6456)
 # state is read once and kept in registers, so the traffic depends on the
 # batch, not on the horizon), valid only for the kernel source it was taken
 # on (kernel_sha(): the sources of the Kepler tiles), recorded per entry.
+# FP64 instructions per trajectory-step in the survey's unit (a DFMA counts
+# one; abs, max and compare are not counted): W(d, k) = d (160 init + 40
+# update) + k (d (16 R + 88 mix + 8 diff) + 8 C_g), C_g = 16 for Kepler,
+# so 400 per step + 352 per sweep at d = 2.
+FP64_INST_PER_STEP, FP64_INST_PER_SWEEP = 400, 352
+# Warp instructions the Kepler kernel issues per trajectory-step and per
+# sweep, from one ncu capture of the full 65,536-orbit batch over one period
+# (smsp__inst_executed.sum, sm__inst_executed_pipe_fp64.sum and the
+# launch's step and sweep totals; profiles/ncu_full_irkgl_kernel_cs_kepler_b65536_p1.md),
+# valid only for the kernel source it was taken on (kernel_sha()).
+# The FP64 count is sm__inst_executed_pipe_fp64's share of its peak (one
+# warp instruction per 16 SM cycles, 2 DFMA lanes per clock) times the
+# elapsed SM cycles.
+NCU_ISSUE = {  # (mixing, tile layout): (warp inst per traj-step, FP64 warp inst per traj-step, kernel_sha)
+    (1, "component split"): (6693960891 / 16064548, 0.59062109 * 0.0625 * 4782353724 / 16064548,
+                             "46fc8f73dbb82f65"),
+}
 NCU_TRAFFIC_BYTES_PER_LAUNCH = {  # (mixing, tile layout): (bytes per launch, kernel_sha at capture)
     (0, "stage split"): (4389888 + 68864, "68265a9b374b87ca"),
     (1, "stage split"): (4640000 + 595968, "68265a9b374b87ca"),
-    (1, "component split"): (4179456 + 81920, "a3d0963eec2c4a34"),
+    (1, "component split"): (3622656 + 132096, "46fc8f73dbb82f65"),
 }
 
 
@@ -98,6 +115,8 @@ def parse():
                     help="requests in the bounded serving window (0 = skip the serving measurement)")
     ap.add_argument("--serve-rates", default="2000",
                     help="--workload serving: comma-separated Poisson arrival rates per second")
+    ap.add_argument("--sweep-cases", default="",
+                    help="--workload sweeps: comma-separated case-name prefixes to run (default all)")
     ap.add_argument("--no-sublines", action="store_true",
                     help="skip the compact lines of the other configurations in the default run")
     return ap.parse_args()
@@ -174,27 +193,118 @@ def sweep_histogram(torch, irkgl, kind_g, kind_o, params, q0, v0, h, nsteps, cor
         ko = r["iters"][:, 0].astype(np.int64)
         dd = kg - ko
         for hist, vals in ((diff, dd), (kg_hist, kg), (ko_hist, ko)):
-            u, c = np.unique(vals, return_counts=True)
-            for a, b in zip(u.tolist(), c.tolist()):
-                hist[a] = hist.get(a, 0) + b
+            _hist_add(hist, vals)
         if len(worst) < 8:
             for b in np.flatnonzero(np.abs(dd) >= 2)[:8 - len(worst)]:
                 worst.append((n, int(b), int(kg[b]), int(ko[b])))
     integ.close()
-    total = B * nsteps
+    return _hist_summary(diff, kg_hist, ko_hist, B * nsteps, worst)
+
+
+def _hist_add(hist, vals):
+    u, c = np.unique(vals, return_counts=True)
+    for a, b in zip(u.tolist(), c.tolist()):
+        hist[a] = hist.get(a, 0) + b
+
+
+def _hist_summary(diff, kg_hist, ko_hist, total, worst):
     beyond = sum(c for a, c in diff.items() if abs(a) >= 2)
     return {"traj_steps": total, "diff_hist": {str(a): diff[a] for a in sorted(diff)},
             "k_gpu_hist": {str(a): kg_hist[a] for a in sorted(kg_hist)},
             "k_oracle_hist": {str(a): ko_hist[a] for a in sorted(ko_hist)},
             "rate_beyond_1": beyond / total, "max_abs_diff": max(abs(a) for a in diff),
-            "rate_equal": diff.get(0, 0) / total, "first_beyond_1": worst}
+            "rate_equal": diff.get(0, 0) / total,
+            "mean_abs_diff": sum(abs(a) * c for a, c in diff.items()) / total,
+            "first_beyond_1": worst}
+
+
+def sweep_histogram1(torch, irkgl, kind_g, kind_o, params, y0, h, nsteps, **integ_kw):
+    """sweep_histogram for the first-order form (Eqs. IRK_init, IRK_FP):
+    the GPU's y, y_lo and L_prev handed to the oracle before every step."""
+    from oracle import cbind
+    B, D = y0.shape
+    f = dict(dtype=torch.float64, device="cuda")
+    y = torch.tensor(y0, **f)
+    ylo = torch.zeros_like(y)
+    lp = torch.zeros((B, 8, D), **f)
+    it = torch.zeros(B, dtype=torch.int64, device="cuda")
+    ns = torch.ones(B, dtype=torch.int64, device="cuda")
+    integ = irkgl.Integrator(kind_g, params, D, h, **integ_kw)
+    diff, kg_hist, ko_hist, worst = {}, {}, {}, []
+    for n in range(nsteps):
+        yh, ylh, lph = y.cpu().numpy(), ylo.cpu().numpy(), lp.cpu().numpy()
+        before = it.clone()
+        integ.advance1(y, ylo, lp, ns, iters=it)
+        r = cbind.run1(kind_o, params, yh, h, 1, y_lo=ylh, l_prev=lph, iters_len=1)
+        kg = (it - before).cpu().numpy().astype(np.int64)
+        ko = r["iters"][:, 0].astype(np.int64)
+        dd = kg - ko
+        _hist_add(diff, dd)
+        _hist_add(kg_hist, kg)
+        _hist_add(ko_hist, ko)
+        if len(worst) < 8:
+            for b in np.flatnonzero(np.abs(dd) >= 2)[:8 - len(worst)]:
+                worst.append((n, int(b), int(kg[b]), int(ko[b])))
+    integ.close()
+    return _hist_summary(diff, kg_hist, ko_hist, B * nsteps, worst)
+
+
+def sweep_histogram_ragged(torch, irkgl, w, nsteps, team, mix):
+    """sweep_histogram for a ragged batch on the wide kernel
+    (irkgl_advance_ragged one step at a time), each instance's state handed
+    to the oracle before every step."""
+    from oracle import cbind
+    kinds = {2: cbind.NBODY, 3: cbind.FPUT, 5: cbind.HARMONIC}
+    n = len(w["kind"])
+    f = dict(dtype=torch.float64, device="cuda")
+    C = len(w["q0"])
+    q, v = torch.tensor(w["q0"], **f), torch.tensor(w["v0"], **f)
+    ql, vl, rp = torch.zeros(C, **f), torch.zeros(C, **f), torch.zeros(8 * C, **f)
+    it = torch.zeros(n, dtype=torch.int64, device="cuda")
+    st = torch.zeros(n, dtype=torch.int32, device="cuda")
+    ns = torch.ones(n, dtype=torch.int64, device="cuda")
+    par = torch.tensor(w["params"], **f)
+    ctx = irkgl.irkgl_create(irkgl.RHS_HARMONIC, [1.0], 1, 1.0)
+    irkgl.irkgl_set_option(ctx, irkgl.OPT_WIDE_TEAM, team)
+    irkgl.irkgl_set_option(ctx, irkgl.OPT_MIX, mix)
+    inst = irkgl.instances_tensor(w, "cuda")
+    dmax = int(np.asarray(w["dim"]).max())
+    diff, kg_hist, ko_hist, worst = {}, {}, {}, []
+    for s in range(nsteps):
+        qh, vh, qlh, vlh, rph = (t.cpu().numpy() for t in (q, v, ql, vl, rp))
+        before = it.clone()
+        irkgl.irkgl_advance_ragged(ctx, inst, n, dmax, par, q, v, ql, vl, rp, ns, iters=it, status=st)
+        kg = (it - before).cpu().numpy().astype(np.int64)
+        stn = st.cpu().numpy()
+        ko = np.zeros(n, dtype=np.int64)
+        for k in range(n):
+            o, d = int(w["offset"][k]), int(w["dim"][k])
+            po, pn = int(w["param_offset"][k]), int(w["nparams"][k])
+            r = cbind.run(kinds[int(w["kind"][k])], w["params"][po:po + pn], qh[o:o + d], vh[o:o + d],
+                          w["h"][k], 1, q_lo=qlh[o:o + d], v_lo=vlh[o:o + d],
+                          r_prev=rph[8 * o:8 * (o + d)], iters_len=1)
+            ko[k] = r["iters"][0, 0]
+        ok = stn == 0  # a failed step (sweep cap, non-finite) is not compared
+        dd = (kg - ko)[ok]
+        _hist_add(diff, dd)
+        _hist_add(kg_hist, kg[ok])
+        _hist_add(ko_hist, ko[ok])
+        if len(worst) < 8:
+            for b in np.flatnonzero(np.abs(kg - ko) >= 2)[:8 - len(worst)]:
+                if ok[b]:
+                    worst.append((s, int(b), int(kg[b]), int(ko[b])))
+    irkgl.irkgl_destroy(ctx)
+    total = sum(diff.values())
+    return _hist_summary(diff, kg_hist, ko_hist, total, worst)
 
 
 def run_sweeps(args):
     """Sweep-count parity, step by step from the identical state: the
     65,536-orbit Kepler ensemble (both stage mixings) over 1,000 steps, the
-    Henon-Heiles orbit of Sec. 5.1 over 2 pi 1e4 at h = 1.0, and a
-    4,096-orbit Henon-Heiles ensemble over 1,000 steps at h = 0.7."""
+    Henon-Heiles orbit of Sec. 5.1 over 2 pi 1e4 at h = 1.0, a 4,096-orbit
+    Henon-Heiles ensemble over 1,000 steps at h = 0.7, 4,096 copies of the
+    6-body system over 1,000 steps, and 8,192 first-order Schwarzschild
+    orbits over 500 steps at h = 4 and h = 16."""
     import torch
 
     from paper_2511_03655_gb300 import build, irkgl, workloads
@@ -205,27 +315,62 @@ def run_sweeps(args):
     cores = os.cpu_count() or 1
     n = args.traj_steps or 1000
     kw = workloads.kepler_ensemble(batch=args.batch, periods=1)
+    only = [x for x in (args.sweep_cases or "").split(",") if x]
     rows = {}
-    for mix in (1, 0):
+
+    def case(name, fn, *a, **k):
+        # one case at a time, each also printed to stderr as it completes
+        if only and not any(name.startswith(p) for p in only):
+            return
         t0 = time.perf_counter()
-        rows[f"kepler_ensemble_mix{mix}"] = sweep_histogram(
-            torch, irkgl, irkgl.RHS_KEPLER, cbind.KEPLER, [1.0], kw["q0"], kw["v0"], kw["h"], n, cores,
-            mix=mix)
-        rows[f"kepler_ensemble_mix{mix}"]["seconds"] = time.perf_counter() - t0
+        try:
+            rows[name] = fn(*a, **k)
+        except Exception as e:  # noqa: BLE001 - recorded in the line, the other cases run
+            rows[name] = {"error": repr(e)[:300]}
+        rows[name]["seconds"] = time.perf_counter() - t0
+        print(json.dumps({name: rows[name]}), file=sys.stderr, flush=True)
+
+    for mix in (1, 0):
+        case(f"kepler_ensemble_mix{mix}", sweep_histogram, torch, irkgl, irkgl.RHS_KEPLER, cbind.KEPLER,
+             [1.0], kw["q0"], kw["v0"], kw["h"], n, cores, mix=mix)
     q0, v0 = workloads.henon_heiles_ic()
     nhh = int(round(2 * math.pi * 1e4 / 1.0))
     for mix in (1, 0):
-        rows[f"henon_heiles_orbit_mix{mix}"] = sweep_histogram(
-            torch, irkgl, irkgl.RHS_HENON_HEILES, cbind.HENON_HEILES, [1.0], q0, v0, 1.0, nhh, cores,
-            mix=mix)
+        case(f"henon_heiles_orbit_mix{mix}", sweep_histogram, torch, irkgl, irkgl.RHS_HENON_HEILES,
+             cbind.HENON_HEILES, [1.0], q0, v0, 1.0, nhh, cores, mix=mix)
         hq, hv, _ = workloads.henon_heiles_ensemble(4096)
-        rows[f"henon_heiles_ensemble_mix{mix}"] = sweep_histogram(
-            torch, irkgl, irkgl.RHS_HENON_HEILES, cbind.HENON_HEILES, [1.0], hq, hv, 0.7, n, cores,
-            mix=mix)
+        case(f"henon_heiles_ensemble_mix{mix}", sweep_histogram, torch, irkgl, irkgl.RHS_HENON_HEILES,
+             cbind.HENON_HEILES, [1.0], hq, hv, 0.7, n, cores, mix=mix)
+    nb = workloads.nbody_ensemble(copies=4096, steps=n)
+    for mix in (0, 1):
+        case(f"nbody6_ensemble_mix{mix}", sweep_histogram, torch, irkgl, irkgl.RHS_NBODY, cbind.NBODY,
+             nb["params"], nb["q0"], nb["v0"], nb["h"], n, cores, mix=mix)
+    # uncoupled oscillators (the closed-form case), 4,096 x 3 components; the
+    # harmonic kind has the FP64 mixing only
+    rs = np.random.default_rng(2511036550 + 12)
+    hq, hv = rs.uniform(-1, 1, (4096, 3)), rs.uniform(-1, 1, (4096, 3))
+    case("harmonic_mix0", sweep_histogram, torch, irkgl, irkgl.RHS_HARMONIC, cbind.HARMONIC, [1.3], hq, hv,
+         0.4, n, cores, mix=0)
+    # the ragged batch's instances on the wide kernel (its step table)
+    from paper_2511_03655_gb300 import autotune
+    tuned = autotune.load_table()
+    wr = workloads.uneven_batch(ninst=128, steps=200, step_table=tuned["step_table"] if tuned else None)
+    for mix in (1, 0):
+        case(f"ragged_wide_mix{mix}", sweep_histogram_ragged, torch, irkgl, wr, 200, 256, mix)
+    y0 = workloads.schwarzschild_ensemble(8192)
+    par = list(workloads.SBH_PARAMS)
+    for hsb in (4.0, 16.0):
+        for mix in (0, 1):
+            case(f"schwarzschild_h{int(hsb)}_mix{mix}", sweep_histogram1, torch, irkgl,
+                 irkgl.RHS_SCHWARZSCHILD, cbind.SCHWARZSCHILD, par, y0, hsb, 500, mix=mix)
     line = {"metric": "sweep-count parity (k_gpu - k_oracle per step, identical state before each step)",
             "config": {"workload": f"Kepler ensemble B={args.batch} e~U[0,0.9) h=2pi/round(200+100e) "
                                    f"x {n} steps; Henon-Heiles orbit (Sec. 5.1, H = 1/12) h = 1.0 x "
-                                   f"{nhh} steps; Henon-Heiles ensemble B=4096 h = 0.7 x {n} steps"},
+                                   f"{nhh} steps; Henon-Heiles ensemble B=4096 h = 0.7 x {n} steps; "
+                                   f"6-body ensemble 4,096 copies x {n} steps; harmonic 4,096 x 3 "
+                                   f"components h = 0.4 x {n} steps; ragged batch 128 instances "
+                                   "(wide kernel, step table) x 200 steps; Schwarzschild 8,192 "
+                                   "orbits x 500 steps at h = 4 and 16"},
             "cases": rows}
     print(json.dumps(line))
     return 0
@@ -655,9 +800,13 @@ def run_first_order(args):
                              mix=args.mix)
     out = irkgl.Outputs1.allocate(B, 4, device=dev)
     peak = fp64_peak_tflops(irkgl, torch, stream, dev)
+    # similar orbits next to each other (by r0, the initial radius): the
+    # lanes of a warp then need similar sweep counts; the order changes no
+    # trajectory's bits
+    od = None if args.no_order else torch.tensor(workloads.similarity_order(-y0h[:, 0]), device=dev)
 
     def run():
-        integ.integrate1(y0, out=out, nsteps_all=nsteps)
+        integ.integrate1(y0, out=out, nsteps_all=nsteps, order=od)
 
     for _ in range(args.warmup):
         run()
@@ -699,6 +848,7 @@ def run_first_order(args):
                                "one persistent launch of the first-order (mu form) kernel",
                    "lanes_per_traj": integ.tile, "tile_layout": integ.layout,
                    "mixing": "fixed-point (integer pipes)" if args.mix else "FP64 FMA chain",
+                   "order": "natural" if args.no_order else "similarity (r0 ascending)",
                    "l2": "state ~10 MB < L2; L2 flushed with a 256 MiB write before every timed step",
                    "parallelism": f"dp{world} (independent shards, no collective on the data path)"},
         "value_all": args.steps * steps_all / t_max,
@@ -1025,6 +1175,30 @@ def main():
     cap = NCU_TRAFFIC_BYTES_PER_LAUNCH.get((args.mix, integ.layout))
     traffic = (cap[0] if cap and cap[1] == kernel_sha() and args.workload == "kepler"
                and args.batch == 65536 else None)
+    t_launch = statistics.mean(times)
+    # the survey's FP64-instruction count against the measured DFMA rate
+    inst_launch = FP64_INST_PER_STEP * float(steps.sum()) + FP64_INST_PER_SWEEP * float(iters.sum())
+    fp64_inst = {"per_traj_step": inst_launch / max(float(steps.sum()), 1.0),
+                 "achieved": inst_launch / t_launch, "peak": fma_per_s, "unit": "FP64 inst/s",
+                 "frac": inst_launch / t_launch / fma_per_s,
+                 "note": "W(d,k) = d (160 + 40) + k (d (16 + 88 + 8) + 8 C_g), C_g = 16: the FP64 "
+                         "operations the method needs; the kernel executes the mixing and "
+                         "x^(-3/2) ones on the integer pipes, so this reads above 1"} \
+        if args.workload == "kepler" else None
+    # issue slots: the kernel's warp instructions (ncu, per traj-step) against
+    # 4 schedulers x SMs x the SM clock measured during the timed region
+    iss = NCU_ISSUE.get((args.mix, integ.layout))
+    issue = None
+    if iss and iss[2] == kernel_sha() and args.workload == "kepler" and clk.get("sm_mhz"):
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        slots = 4 * sms * clk["sm_mhz"] * 1e6
+        per_launch = iss[0] * float(steps.sum())
+        issue = {"warp_inst_per_traj_step": iss[0], "achieved": per_launch / t_launch, "peak": slots,
+                 "unit": "warp inst/s", "frac": per_launch / t_launch / slots,
+                 "fp64_pipe_frac_of_probe": iss[1] * 32 * float(steps.sum()) / t_launch / fma_per_s,
+                 "source": "ncu smsp__inst_executed.sum and sm__inst_executed_pipe_fp64.sum per "
+                           "traj-step (profiles/), scaled by this run's traj-steps and CUDA-event "
+                           "time; peak = 4 issue slots per SM per clock at the sampled SM clock"}
 
     line = {
         "metric": METRIC, "value": value, "unit": "traj-steps/s", "n_gpus": world,
@@ -1046,6 +1220,7 @@ def main():
         "gpu_launches": args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops, "traffic": traffic,
+                     "fp64_inst": fp64_inst, "issue": issue,
                      "peak_source": "FP64 FMA-chain probe (irkgl_probe_fp64_fma) measured live, "
                                     "2 flops per FMA",
                      "kernel": ("irkgl_kernel_cs" if integ.layout == "component split" else "irkgl_kernel")

@@ -8,6 +8,7 @@ import pytest
 
 from oracle import cbind
 from paper_2511_03655_gb300 import workloads
+from tests import sweep_contract
 
 pytestmark = pytest.mark.gpu
 PAR = list(workloads.SBH_PARAMS)
@@ -47,7 +48,7 @@ def test_schwarzschild_cs_against_oracle(torch_cuda, mix):
         assert (out.status.cpu().numpy() == 0).all()
         assert rel(out.y.cpu().numpy(), r["y"]).max() <= tol, (n, mix)
         tot = r["iters_total"].astype(np.float64)
-        assert np.abs(out.iters.cpu().numpy() - tot).max() <= 0.05 * tot.max() + 3
+        assert (np.abs(out.iters.cpu().numpy() - tot) <= sweep_contract.total_bound("schwarzschild", n)).all()
         dg, do = out.dH_max.cpu().numpy(), r["dH_max"]
         assert np.all(dg <= 2 * do + 2e-15)
     ig.close()
@@ -61,7 +62,9 @@ def test_schwarzschild_cs_matches_stage_split(torch_cuda):
     b = integ(0, 1).integrate1(d, nsteps_all=300)
     torch.cuda.synchronize()
     assert rel(a.y.cpu().numpy(), b.y.cpu().numpy()).max() <= 1e-11
-    assert np.abs(a.iters.cpu().numpy() - b.iters.cpu().numpy()).max() <= 0.05 * b.iters.cpu().numpy().max()
+    # two GPU tiles: each within the contract of the oracle, so of each other twice over
+    assert (np.abs(a.iters.cpu().numpy() - b.iters.cpu().numpy())
+            <= 2 * sweep_contract.total_bound("schwarzschild", 300)).all()
 
 
 def test_default_layout_with_fixed_point_and_chunks(torch_cuda):

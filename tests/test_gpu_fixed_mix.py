@@ -11,6 +11,7 @@ import pytest
 
 from oracle import cbind, coeffs
 from paper_2511_03655_gb300 import workloads
+from tests import sweep_contract
 
 pytestmark = pytest.mark.gpu
 
@@ -73,17 +74,11 @@ def test_mixed_kernel_kepler_parity(lib, block, layout, tile):
         g = np.concatenate([q.cpu().numpy(), v.cpu().numpy()], axis=1)
         e = np.concatenate([r["q"], r["v"]], axis=1)
         assert (np.abs(g - e).max() / np.abs(e).max()) <= 1e-13, s
-    it = torch.zeros((1, 1000), dtype=torch.int32, device="cuda")
-    q, v = torch.tensor(w["q0"], device="cuda"), torch.tensor(w["v0"], device="cuda")
-    integ.step(q, v, torch.zeros_like(q), torch.zeros_like(v), torch.zeros_like(rp), nsteps=1000,
-               iters=it)
-    r = cbind.run(cbind.KEPLER, [1.0], w["q0"], w["v0"], w["h"], 1000, iters_len=1000)
-    diff = it.cpu().numpy()[0] - r["iters"][0]
-    # +-1 but for at most a couple of roundoff-floor steps (see the ensemble
-    # rate test in test_gpu_parity); the exact sums round differently from
-    # the oracle's separately rounded ones, so fewer steps match exactly than
-    # with the FMA chain (measured 79.7 % on GB300)
-    assert np.abs(diff).max() <= 3 and (np.abs(diff) >= 2).sum() <= 2
+    # sweep counts over 1,000 steps from the identical state: the contract;
+    # the exact sums round differently from the oracle's separately rounded
+    # ones, so fewer steps match exactly than with the FMA chain
+    diff = sweep_contract.identical_state_diffs(torch, integ, cbind.KEPLER, [1.0], w["q0"], w["v0"], h, 1000)
+    sweep_contract.check_steps(diff, "kepler")
     assert (diff == 0).mean() > 0.7
     out = integ.integrate(torch.tensor(w["q0"], device="cuda"), torch.tensor(w["v0"], device="cuda"),
                           nsteps_all=20000)
@@ -110,7 +105,7 @@ def test_mixed_kernel_ensemble(lib):
     assert (np.abs(g - e).max(axis=1) / np.abs(e).max(axis=1)).max() <= 1e-11
     assert (out.status.cpu().numpy() == 0).all()
     ig = out.iters.cpu().numpy()
-    assert (np.abs(ig - r["iters_total"]) <= 0.1 * r["iters_total"] + 2).all()
+    assert (np.abs(ig - r["iters_total"]) <= sweep_contract.total_bound("kepler", w["nsteps"])).all()
     integ.close()
 
 

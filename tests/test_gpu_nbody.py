@@ -16,6 +16,7 @@ import pytest
 
 from oracle import cbind
 from paper_2511_03655_gb300 import workloads
+from tests import sweep_contract
 
 pytestmark = pytest.mark.gpu
 
@@ -57,18 +58,13 @@ def test_nbody_first_steps_and_iterations(torch_cuda, mix):
                       v_lo=st["v_lo"], r_prev=st["r_prev"])
         st = dict(q=r["q"], v=r["v"], q_lo=r["q_lo"], v_lo=r["v_lo"], r_prev=r["r_prev"])
         assert rel(q.cpu(), v.cpu(), r["q"], r["v"]).max() <= 1e-13, s
-    it = torch.zeros((8, 1000), dtype=torch.int32, device="cuda")
-    q, v = dev(torch, w["q0"]), dev(torch, w["v0"])
-    integ.step(q, v, torch.zeros_like(q), torch.zeros_like(v), torch.zeros_like(rp), nsteps=1000,
-               iters=it)
-    r = cbind.run(cbind.NBODY, w["params"], w["q0"], w["v0"], h, 1000, iters_len=1000, nthreads=8)
-    # this well-separated system converges at the roundoff floor (about two
-    # sweeps per step): a step stops at k = 2 when Delta = 0 exactly, or at
-    # k = 4 by the min rule of Eq. stopping when one side's last bit still
-    # moves, so a few steps differ by 2; the rest by at most 1
-    diff = np.abs(it.cpu().numpy() - r["iters"])
-    assert diff.max() <= 3 and (diff <= 1).mean() >= 0.99, (diff.max(), (diff <= 1).mean())
-    assert (diff == 0).mean() > 0.8
+    # sweep counts over 1,000 steps from the identical state (the contract:
+    # this well-separated system converges at the roundoff floor, about two
+    # sweeps per step, and the counts almost always agree)
+    diff = sweep_contract.identical_state_diffs(torch, integ, cbind.NBODY, w["params"], w["q0"], w["v0"],
+                                                h, 1000)
+    sweep_contract.check_steps(diff, "nbody6")
+    assert (diff == 0).mean() > 0.99
     integ.close()
 
 
@@ -115,8 +111,7 @@ def test_nbody_full_horizon_energy_statistics(torch_cuda, full_horizon_oracle, m
     """1e5 steps (500 inner periods) of 128 perturbed copies: every copy
     completes on both sides, and the median, p90 and max over the ensemble
     of max_n |dH/H| agree within a factor of 2 (the chaotic-run criterion),
-    each <= 1e-13 where the oracle's is; the mean sweeps per step agree to
-    2 %."""
+    each <= 1e-13 where the oracle's is; sweep totals within the contract."""
     from paper_2511_03655_gb300 import irkgl
     torch = torch_cuda
     w, r = full_horizon_oracle
@@ -132,9 +127,9 @@ def test_nbody_full_horizon_energy_statistics(torch_cuda, full_horizon_oracle, m
         assert sg <= 2 * so + 2e-15 and so <= 2 * sg + 2e-15, (sg, so)
         if so <= 1e-13:
             assert sg <= 1e-13
-    kg = out.iters.cpu().numpy().sum() / (FULL_COPIES * FULL_STEPS)
-    ko = r["iters_total"].sum() / (FULL_COPIES * FULL_STEPS)
-    assert abs(kg - ko) <= 0.02 * ko, (kg, ko)
+    # sweep totals per copy within the contract's bound
+    bound = sweep_contract.total_bound("nbody6", FULL_STEPS)
+    assert (np.abs(out.iters.cpu().numpy() - r["iters_total"]) <= bound).all()
     integ.close()
 
 

@@ -7,6 +7,7 @@ import pytest
 
 from oracle import cbind
 from paper_2511_03655_gb300 import workloads
+from tests import sweep_contract
 
 pytestmark = pytest.mark.gpu
 
@@ -63,7 +64,7 @@ def test_ragged_matches_oracle_per_instance(torch_cuda):
         g = np.concatenate([q[o:o + d], v[o:o + d]])
         e = np.concatenate([r["q"][0], r["v"][0]])
         assert np.abs(g - e).max() / np.abs(e).max() <= 1e-11, (k, int(w["kind"][k]), d)
-        assert abs(it[k] - r["iters_total"][0]) <= 0.1 * r["iters_total"][0] + 2, k
+        assert abs(it[k] - r["iters_total"][0]) <= sweep_contract.total_bound("ragged", int(w["nsteps"][k])), k
         assert dH[k] <= max(4 * r["dH_max"][0], 4e-15), (k, dH[k], r["dH_max"][0])
 
 
@@ -174,9 +175,70 @@ def test_fixed_point_mixing_ragged(torch_cuda):
         g = np.concatenate([q[o:o + d], v[o:o + d]])
         e = np.concatenate([r["q"][0], r["v"][0]])
         assert np.abs(g - e).max() / np.abs(e).max() <= 1e-11, (k, int(w["kind"][k]), d)
-        assert abs(it[k] - r["iters_total"][0]) <= 0.1 * r["iters_total"][0] + 2, k
+        assert abs(it[k] - r["iters_total"][0]) <= sweep_contract.total_bound("ragged", int(w["nsteps"][k])), k
     ref = run_gpu(torch_cuda, w, team=64, mix=1)
     for team in (128, 256):
         other = run_gpu(torch_cuda, w, team=team, mix=1)
         for f in ("q", "v", "q_lo", "v_lo", "r_prev", "iters", "steps", "status"):
             assert torch_cuda.equal(getattr(ref, f), getattr(other, f)), (team, f)
+
+
+def nbody_instances(nbs, steps, frac=0.0025):
+    """N-body systems of the given body counts (the ragged batch's generator)
+    packed as one ragged batch, h = frac of each system's innermost period."""
+    kinds, dims, params, qs, vs, hs = [], [], [], [], [], []
+    for k, nb in enumerate(nbs):
+        s = workloads.nbody_system(nb, seed_id=30000 + k)
+        kinds.append(2)
+        dims.append(3 * nb)
+        params.append([1.0] + list(s["masses"]))
+        qs.append(s["q"])
+        vs.append(s["v"])
+        hs.append(frac * s["period_inner"])
+    off = np.concatenate([[0], np.cumsum(dims)[:-1]]).astype(np.int64)
+    pc = np.array([len(p) for p in params])
+    return {"kind": np.array(kinds, np.int32), "dim": np.array(dims, np.int32), "offset": off,
+            "param_offset": np.concatenate([[0], np.cumsum(pc)[:-1]]).astype(np.int32),
+            "nparams": pc.astype(np.int32), "h": np.array(hs), "nsteps": np.full(len(nbs), steps, np.int64),
+            "params": np.concatenate([np.asarray(p, np.float64) for p in params]),
+            "q0": np.concatenate(qs), "v0": np.concatenate(vs)}
+
+
+@pytest.mark.parametrize("mix", [0, 1])
+def test_pairs_once_match_oracle(torch_cuda, mix):
+    """Systems of 21 to 128 bodies take the form that evaluates every pair
+    once per stage (tiles of 8, round-robin tile pairs): over 10 steps the
+    states agree with the oracle within 1e-13."""
+    nbs = [21, 24, 30, 33, 40, 47, 48, 64, 100, 128]
+    w = nbody_instances(nbs, 10)
+    out = run_gpu(torch_cuda, w, mix=mix)
+    q, v = out.q.cpu().numpy(), out.v.cpu().numpy()
+    st = out.status.cpu().numpy()
+    for k, nb in enumerate(nbs):
+        r = oracle_instance(w, k)
+        o, d = int(w["offset"][k]), int(w["dim"][k])
+        assert st[k] == r["status"][0] == 0, nb
+        g = np.concatenate([q[o:o + d], v[o:o + d]])
+        e = np.concatenate([r["q"][0], r["v"][0]])
+        assert np.abs(g - e).max() / np.abs(e).max() <= 1e-13, nb
+
+
+def test_pairs_once_team_shapes_agree_bitwise(torch_cuda):
+    """The pair-once form sums each body's force in an order fixed by the
+    tile schedule, so every team size gives the same bits."""
+    w = nbody_instances([21, 33, 40, 64], 25)
+    ref = run_gpu(torch_cuda, w, team=64)
+    for team in (128, 256):
+        out = run_gpu(torch_cuda, w, team=team)
+        for f in ("q", "v", "q_lo", "v_lo", "r_prev", "iters", "steps", "status"):
+            assert torch_cuda.equal(getattr(ref, f), getattr(out, f)), (team, f)
+    w = nbody_instances([21], 25)  # d = 63 also fits the one-warp team
+    a = run_gpu(torch_cuda, w, team=32)
+    b = run_gpu(torch_cuda, w, team=256)
+    for f in ("q", "v", "iters"):
+        assert torch_cuda.equal(getattr(a, f), getattr(b, f)), f
+    w = nbody_instances([100, 128], 10)
+    a = run_gpu(torch_cuda, w, team=128)
+    b = run_gpu(torch_cuda, w, team=256)
+    for f in ("q", "v", "iters"):
+        assert torch_cuda.equal(getattr(a, f), getattr(b, f)), f
