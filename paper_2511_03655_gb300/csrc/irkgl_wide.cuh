@@ -460,16 +460,19 @@ __global__ void __launch_bounds__(BLOCK)
             const int emax = fixed_column(Rj, rb, nf);
 #pragma unroll
             for (int i = 0; i < S; i++) {
-              const double cvil = cf.c[i] * vh[s];
+              // c_i v and c_i v + T rounded separately on every shape: the
+              // intrinsics keep the compiler from fusing them into one FMA
+              // in some shapes and not in others (team shapes stay bitwise equal)
+              const double cvil = __dmul_rn(cf.c[i], vh[s]);
               if constexpr (CVS) CV[i * d + l] = cvil;
               double T = fixed_row<true>(i, rb, emax);
               if (nf) T = __longlong_as_double(0x7ff8000000000000LL);
-              Q[i * d + l] = fma(h, cvil + T, qh[s]);
+              Q[i * d + l] = fma(h, __dadd_rn(cvil, T), qh[s]);
             }
           } else {
 #pragma unroll
             for (int i = 0; i < S; i++) {
-              const double cvil = cf.c[i] * vh[s];
+              const double cvil = __dmul_rn(cf.c[i], vh[s]);
               if constexpr (CVS) CV[i * d + l] = cvil;
               double acc = cvil;
 #pragma unroll
@@ -504,15 +507,15 @@ __global__ void __launch_bounds__(BLOCK)
               for (int i = 0; i < S; i++) {
                 double T = fixed_row<false>(i, rb, emax);
                 if (nf) T = __longlong_as_double(0x7ff8000000000000LL);
-                const double cvil = CVS ? CV[i * d + l] : cf.c[i] * vh[s];
-                const double qn = fma(h, cvil + T, qh[s]);
+                const double cvil = CVS ? CV[i * d + l] : __dmul_rn(cf.c[i], vh[s]);
+                const double qn = fma(h, __dadd_rn(cvil, T), qh[s]);
                 dl = umax64(dl, abs_bits(qn - Q[i * d + l]));
                 Q[i * d + l] = qn;
               }
             } else {
 #pragma unroll
               for (int i = 0; i < S; i++) {
-                double acc = CVS ? CV[i * d + l] : cf.c[i] * vh[s];
+                double acc = CVS ? CV[i * d + l] : __dmul_rn(cf.c[i], vh[s]);
 #pragma unroll
                 for (int j = 0; j < S; j++) acc = fma(cf.eta[i * S + j], Rj[j], acc);
                 const double qn = fma(h, acc, qh[s]);

@@ -176,6 +176,19 @@ class RaggedRunner:
             done.record(s)
             cur.wait_event(done)
 
+    def capture(self, out: irkgl.RaggedOutputs) -> torch.cuda.CUDAGraph:
+        """Record run(out) as a CUDA graph: every bucket's counter reset and
+        launch on its own stream, forked from and joined to the capturing
+        stream.  graph.replay() then repeats the whole bucketed integration
+        into `out` with one host call; the results are those of run(out)
+        bit for bit.  Inputs and outputs stay at the addresses captured."""
+        self.run(out)  # resolves each bucket's shape and shared-memory attribute first
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, capture_error_mode="relaxed"):
+            self.run(out)
+        return g
+
     def single(self, out: irkgl.RaggedOutputs, team: int = 0):
         if team not in self.ctx:
             self.ctx[team] = self._ctx(team)

@@ -242,3 +242,31 @@ def test_pairs_once_team_shapes_agree_bitwise(torch_cuda):
     b = run_gpu(torch_cuda, w, team=256)
     for f in ("q", "v", "iters"):
         assert torch_cuda.equal(getattr(a, f), getattr(b, f)), f
+
+
+def test_bucketed_run_captured_in_a_cuda_graph(torch_cuda):
+    """The bucketed launches (one per size bucket, each on its own stream)
+    recorded as one CUDA graph: a replay gives the bits of the direct run,
+    and replays repeat them."""
+    from paper_2511_03655_gb300 import irkgl, ragged
+    torch = torch_cuda
+    w = small_batch(ninst=40, steps=60, nmax_body=40, nmax_chain=300)
+    plan = ragged.RaggedPlan(w)
+    dev = torch.device("cuda")
+    runner = ragged.RaggedRunner(plan, torch.tensor(w["params"], device=dev),
+                                 torch.tensor(w["q0"], device=dev), torch.tensor(w["v0"], device=dev),
+                                 device=dev, mix=1)
+    direct = irkgl.RaggedOutputs.allocate(len(w["q0"]), len(w["kind"]), device=dev)
+    runner.run(direct)
+    torch.cuda.synchronize()
+    out = irkgl.RaggedOutputs.allocate(len(w["q0"]), len(w["kind"]), device=dev)
+    g = runner.capture(out)
+    for _ in range(2):
+        for f in ("q", "v"):
+            getattr(out, f).zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        for f in ("q", "v", "q_lo", "v_lo", "r_prev", "iters", "steps", "status", "dH_max"):
+            assert torch.equal(getattr(direct, f), getattr(out, f)), f
+    assert len(plan.buckets) > 1
+    runner.close()

@@ -166,3 +166,32 @@ def test_server_reuse(server_mod):
     for a, b in zip(again, fresh):
         assert same(a, b)
     srv.close()
+
+
+def test_requests_at_the_top_of_the_config5_ranges(server_mod):
+    """An FPUT chain of 1,500 particles (D = 3,000, the wide kernel's
+    longest-chain shape), a 64-body system (d = 192) and a Kepler batch,
+    served together: each equals the plain per-request form bit for bit and
+    the chain agrees with the oracle."""
+    serve = server_mod
+    c = workloads.fput_chain(1500)
+    q = np.repeat(c["q"][None, :], 3, axis=0) * (1.0 + 1e-8 * np.arange(3)[:, None])
+    nb = workloads.nbody_ensemble(copies=2, nbodies=64, steps=40, seed_id=77)
+    kq, kv = workloads.kepler_ic(np.array([0.1, 0.5, 0.8]))
+    descs = [dict(rid=0, kind="fput", params=c["params"], dim=1500, q0=q, v0=np.zeros_like(q), h=0.25,
+                  nsteps=60),
+             dict(rid=1, kind="nbody", params=nb["params"], dim=192, q0=nb["q0"], v0=nb["v0"],
+                  h=float(nb["h"][0]), nsteps=40),
+             dict(rid=2, kind="kepler", params=[1.0], dim=2, q0=kq, v0=kv, h=2 * np.pi / 250, nsteps=500)]
+    served = serve.make_requests(copy.deepcopy(descs))
+    st = serve.Server(target_tick_s=0.002).run(served)
+    assert st.pools == 3
+    plain = serve.make_requests(copy.deepcopy(descs))
+    serve.run_plain(plain)
+    for a, b in zip(served, plain):
+        assert (a.status == 0).all()
+        assert same(a, b), a.kind
+    o = cbind.run(cbind.FPUT, c["params"], q, np.zeros_like(q), 0.25, 60, nthreads=8)
+    g = np.concatenate([served[0].q, served[0].v], axis=1)
+    e = np.concatenate([o["q"], o["v"]], axis=1)
+    assert (np.abs(g - e).max(axis=1) / np.abs(e).max(axis=1)).max() <= 1e-12
