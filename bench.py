@@ -218,24 +218,25 @@ def _hist_summary(diff, kg_hist, ko_hist, total, worst):
             "first_beyond_1": worst}
 
 
-def sweep_histogram1(torch, irkgl, kind_g, kind_o, params, y0, h, nsteps, **integ_kw):
-    """sweep_histogram for the first-order form (Eqs. IRK_init, IRK_FP):
-    the GPU's y, y_lo and L_prev handed to the oracle before every step."""
+def sweep_histogram1(torch, irkgl, kind_g, kind_o, params, y0, h, nsteps, stages=8, **integ_kw):
+    """sweep_histogram for the first-order form (Eqs. IRK_init, IRK_FP), with
+    s = `stages` stages: the GPU's y, y_lo and L_prev handed to the oracle
+    before every step."""
     from oracle import cbind
     B, D = y0.shape
     f = dict(dtype=torch.float64, device="cuda")
     y = torch.tensor(y0, **f)
     ylo = torch.zeros_like(y)
-    lp = torch.zeros((B, 8, D), **f)
+    lp = torch.zeros((B, stages, D), **f)
     it = torch.zeros(B, dtype=torch.int64, device="cuda")
     ns = torch.ones(B, dtype=torch.int64, device="cuda")
-    integ = irkgl.Integrator(kind_g, params, D, h, **integ_kw)
+    integ = irkgl.Integrator(kind_g, params, D, h, stages=stages, **integ_kw)
     diff, kg_hist, ko_hist, worst = {}, {}, {}, []
     for n in range(nsteps):
         yh, ylh, lph = y.cpu().numpy(), ylo.cpu().numpy(), lp.cpu().numpy()
         before = it.clone()
         integ.advance1(y, ylo, lp, ns, iters=it)
-        r = cbind.run1(kind_o, params, yh, h, 1, y_lo=ylh, l_prev=lph, iters_len=1)
+        r = cbind.run1(kind_o, params, yh, h, 1, y_lo=ylh, l_prev=lph, iters_len=1, stages=stages)
         kg = (it - before).cpu().numpy().astype(np.int64)
         ko = r["iters"][:, 0].astype(np.int64)
         dd = kg - ko
@@ -363,6 +364,10 @@ def run_sweeps(args):
         for mix in (0, 1):
             case(f"schwarzschild_h{int(hsb)}_mix{mix}", sweep_histogram1, torch, irkgl,
                  irkgl.RHS_SCHWARZSCHILD, cbind.SCHWARZSCHILD, par, y0, hsb, 500, mix=mix)
+    # the s-stage schemes of Sec. 5.2 (FP64 mixing, the default for s < 8)
+    for s, hs in ((2, 0.5), (4, 2.0), (6, 2.0)):
+        case(f"schwarzschild_s{s}_h{hs:g}_mix0", sweep_histogram1, torch, irkgl, irkgl.RHS_SCHWARZSCHILD,
+             cbind.SCHWARZSCHILD, par, y0, hs, 500, stages=s)
     line = {"metric": "sweep-count parity (k_gpu - k_oracle per step, identical state before each step)",
             "config": {"workload": f"Kepler ensemble B={args.batch} e~U[0,0.9) h=2pi/round(200+100e) "
                                    f"x {n} steps; Henon-Heiles orbit (Sec. 5.1, H = 1/12) h = 1.0 x "
@@ -370,7 +375,8 @@ def run_sweeps(args):
                                    f"6-body ensemble 4,096 copies x {n} steps; harmonic 4,096 x 3 "
                                    f"components h = 0.4 x {n} steps; ragged batch 128 instances "
                                    "(wide kernel, step table) x 200 steps; Schwarzschild 8,192 "
-                                   "orbits x 500 steps at h = 4 and 16"},
+                                   "orbits x 500 steps at h = 4 and 16, and with s = 2, 4, 6 "
+                                   "stages at h = 0.5, 2, 2"},
             "cases": rows}
     print(json.dumps(line))
     return 0

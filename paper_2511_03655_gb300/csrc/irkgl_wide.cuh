@@ -117,6 +117,17 @@ __device__ __forceinline__ double team_sum(double x, double* red) {
   }
 }
 
+// x^(-3/2) of the wide kernel's pair forces.  kWideRinv3Fp64 selects the
+// FP64 form (six dependent FP64 operations after the FP32 seed) over the
+// integer one (about forty dependent integer operations).  The integer form
+// is the faster one on GB300 here too (ragged batch: 1.66e6 against 1.42e6
+// trajectory-steps/s with the FP64 form), although its chain is longer.
+constexpr bool kWideRinv3Fp64 = false;
+__device__ __forceinline__ double wide_rinv3(double x) {
+  if (!positive_normal(x)) return rinv3_special(x);
+  return kWideRinv3Fp64 ? rinv3_fp64(x) : rinv3_int(x);
+}
+
 // N-body g with every pair evaluated once per stage (Newton's third law:
 // the pair (x, y) adds w_y z dx to body x and -w_x z dx to body y, with dx =
 // q_y - q_x and z = |dx|^-3), for systems of at least kTiledMinBodies bodies.
@@ -167,7 +178,7 @@ __device__ __forceinline__ void nbody_rhs_pairs_once(int nb, int d, const double
       const int by = I * kTile + ((a + r) & (kTile - 1));
       if (vx && by < nb && (r < kTile / 2 || a < kTile / 2)) {
         const double dx = Qi[3 * by] - px, dy = Qi[3 * by + 1] - py, dz = Qi[3 * by + 2] - pz;
-        const double z = rinv3(fma(dx, dx, fma(dy, dy, dz * dz)));
+        const double z = wide_rinv3(fma(dx, dx, fma(dy, dy, dz * dz)));
         const double wyz = wi[by] * z, wxz = wx * z;
         gx = fma(wyz, dx, gx);
         gy = fma(wyz, dy, gy);
@@ -209,7 +220,7 @@ __device__ __forceinline__ void nbody_rhs_pairs_once(int nb, int d, const double
         const int by = J * kTile + ((a + r) & (kTile - 1));
         if (vx && by < nb) {
           const double dx = Qi[3 * by] - px, dy = Qi[3 * by + 1] - py, dz = Qi[3 * by + 2] - pz;
-          const double z = rinv3(fma(dx, dx, fma(dy, dy, dz * dz)));
+          const double z = wide_rinv3(fma(dx, dx, fma(dy, dy, dz * dz)));
           const double wyz = wi[by] * z, wxz = wx * z;
           gx = fma(wyz, dx, gx);
           gy = fma(wyz, dy, gy);
@@ -260,7 +271,7 @@ __device__ __forceinline__ void team_rhs(int kind, int d, const double* p, const
       for (int b = 0; b < nb; b++) {
         if (b == a) continue;
         const double dx = Qi[3 * b] - xa, dy = Qi[3 * b + 1] - ya, dz = Qi[3 * b + 2] - za;
-        const double wz = wi[b] * rinv3(fma(dx, dx, fma(dy, dy, dz * dz)));
+        const double wz = wi[b] * wide_rinv3(fma(dx, dx, fma(dy, dy, dz * dz)));
         gx = fma(wz, dx, gx);
         gy = fma(wz, dy, gy);
         gz = fma(wz, dz, gz);

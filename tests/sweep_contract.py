@@ -22,12 +22,14 @@ profiles/sweep_parity_gb300.md):
   nbody6            4.1e7 per mixing   3.5e-5 / 3.2e-5              2         0.0014
   schwarzschild     4.1e6 (h = 4)      4.9e-4 / 4.1e-4              4         0.050
                     4.1e6 (h = 16)     2.1e-3 / 1.9e-3              5         0.134
+                    4.1e6 each, s = 2, 4, 6 stages (h = 0.5, 2, 2):
+                                       1.4e-4 / 3.2e-4 / 3.2e-4     4         0.038
   harmonic          4.1e7 (FP64)       1.3e-2                       4         0.102
   ragged (wide)     2.5e4 per mixing   3.8e-2 / 3.5e-3              4         0.239
 (Kepler: the 65,536-orbit ensemble over 10,000 steps; Henon-Heiles: the
 orbit of Sec. 5.1 over 2 pi 1e4, and a 4,096-orbit ensemble; 6-body: 4,096
 copies over 10,000 steps; Schwarzschild: 8,192 first-order orbits over 500
-steps; harmonic: 4,096 three-component oscillators at omega h = 0.52 over
+steps, also with the s-stage schemes of Sec. 5.2; harmonic: 4,096 three-component oscillators at omega h = 0.52 over
 10,000 steps; ragged: 128 instances of the ragged batch on the wide kernel
 over 200 steps, steps that failed on the GPU left out.)
 
