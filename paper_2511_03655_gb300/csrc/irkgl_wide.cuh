@@ -122,131 +122,19 @@ __device__ __forceinline__ double team_sum(double x, double* red) {
 // integer one (about forty dependent integer operations).  The integer form
 // is the faster one on GB300 here too (ragged batch: 1.66e6 against 1.42e6
 // trajectory-steps/s with the FP64 form), although its chain is longer.
+//
+// The pair force is evaluated from both ends (each body sums over all
+// others).  Evaluating each pair once per stage, with tiles of 8 or 16
+// bodies whose pairs a round-robin schedule visits (a travelling
+// accumulator carrying the partner's sum through the lanes), cut the FP64
+// instructions of the 33-64-body bucket by only 8 % (partly filled tiles
+// and masked lanes cost full warp instructions) and ran 1.39x slower
+// (2,285 against 1,644 ms for 1,090 systems x 1,000 steps), so it is not
+// used.
 constexpr bool kWideRinv3Fp64 = false;
 __device__ __forceinline__ double wide_rinv3(double x) {
   if (!positive_normal(x)) return rinv3_special(x);
   return kWideRinv3Fp64 ? rinv3_fp64(x) : rinv3_int(x);
-}
-
-// N-body g with every pair evaluated once per stage (Newton's third law:
-// the pair (x, y) adds w_y z dx to body x and -w_x z dx to body y, with dx =
-// q_y - q_x and z = |dx|^-3), for systems of at least kTiledMinBodies bodies.
-//   * Bodies form tiles of kTile = 8; a group of 8 lanes works on one
-//     (stage, tile pair) item: lane a holds body x of the row tile and
-//     visits the column tile's bodies y = (a + r) mod 8 in rounds r, keeping
-//     the row body's sum in registers and the column body's sum in a
-//     travelling accumulator that moves one lane down each round, so it is
-//     back on its owner's lane at the end.  A diagonal item (a tile with
-//     itself) does the same over the rounds r = 1..4, the last one on half
-//     the lanes.  (FP64 instructions cost the same with masked lanes, so a
-//     small tile wastes less on partly filled tiles than a wide one.)
-//   * Round 0 runs the diagonal items and writes R; then the tile pairs are
-//     visited by the round-robin tournament of ntE (even) tiles: in every
-//     round each tile appears in exactly one pair, so the items of a round
-//     write disjoint rows of R, and each body's force is summed in the same
-//     order (its diagonal item, then its partners in round order) whatever
-//     the team size.
-// A padding tile (odd number of tiles) and bodies beyond nb are skipped.
-constexpr int kTile = 8;
-constexpr int kTiledMinBodies = 21;
-
-template <int TEAM>
-__device__ __forceinline__ void nbody_rhs_pairs_once(int nb, int d, const double* w8, const double* Q,
-                                                     double* R, int tid) {
-  constexpr int NHW = TEAM / kTile;  // lane groups in the team
-  const int hw = tid / kTile;
-  const int a = tid & (kTile - 1);
-  const unsigned seg = ((1u << kTile) - 1u) << (threadIdx.x & (32 - kTile));  // this group's lanes
-  const int nt = (nb + kTile - 1) / kTile;
-  const int ntE = nt + (nt & 1);
-
-  // round 0: each tile with itself
-  for (int x = hw; x < S * nt; x += NHW) {
-    const int i = x / nt, I = x - i * nt;
-    const double* Qi = Q + i * d;
-    const double* wi = w8 + S + i * nb;
-    const int bx = I * kTile + a;
-    const bool vx = bx < nb;
-    const double px = vx ? Qi[3 * bx] : 0.0, py = vx ? Qi[3 * bx + 1] : 0.0,
-                 pz = vx ? Qi[3 * bx + 2] : 0.0, wx = vx ? wi[bx] : 0.0;
-    double gx = 0.0, gy = 0.0, gz = 0.0, tx = 0.0, ty = 0.0, tz = 0.0;
-    for (int r = 1; r <= kTile / 2; r++) {
-      const int src = (a + 1) & (kTile - 1);
-      tx = __shfl_sync(seg, tx, src, kTile);
-      ty = __shfl_sync(seg, ty, src, kTile);
-      tz = __shfl_sync(seg, tz, src, kTile);
-      const int by = I * kTile + ((a + r) & (kTile - 1));
-      if (vx && by < nb && (r < kTile / 2 || a < kTile / 2)) {
-        const double dx = Qi[3 * by] - px, dy = Qi[3 * by + 1] - py, dz = Qi[3 * by + 2] - pz;
-        const double z = wide_rinv3(fma(dx, dx, fma(dy, dy, dz * dz)));
-        const double wyz = wi[by] * z, wxz = wx * z;
-        gx = fma(wyz, dx, gx);
-        gy = fma(wyz, dy, gy);
-        gz = fma(wyz, dz, gz);
-        tx = fma(-wxz, dx, tx);
-        ty = fma(-wxz, dy, ty);
-        tz = fma(-wxz, dz, tz);
-      }
-    }
-    // body b's travelling sum sits on lane (b - kTile / 2) mod kTile
-    const int back = (a - kTile / 2) & (kTile - 1);
-    tx = __shfl_sync(seg, tx, back, kTile);
-    ty = __shfl_sync(seg, ty, back, kTile);
-    tz = __shfl_sync(seg, tz, back, kTile);
-    if (vx) {
-      R[i * d + 3 * bx] = gx + tx;
-      R[i * d + 3 * bx + 1] = gy + ty;
-      R[i * d + 3 * bx + 2] = gz + tz;
-    }
-  }
-  // rounds 1..ntE-1: the round-robin pairs (circle method, tile ntE-1 fixed)
-  const int half = ntE / 2;
-  for (int k = 0; k < ntE - 1; k++) {
-    team_sync<TEAM>();  // the previous round's rows of R are written
-    for (int x = hw; x < S * half; x += NHW) {
-      const int i = x / half, p = x - i * half;
-      const int A = p == 0 ? k : (k + p) % (ntE - 1);
-      const int B = p == 0 ? ntE - 1 : (k - p + ntE - 1) % (ntE - 1);
-      const int I = A < B ? A : B, J = A < B ? B : A;
-      if (J >= nt) continue;  // paired with the padding tile
-      const double* Qi = Q + i * d;
-      const double* wi = w8 + S + i * nb;
-      const int bx = I * kTile + a;
-      const bool vx = bx < nb;
-      const double px = vx ? Qi[3 * bx] : 0.0, py = vx ? Qi[3 * bx + 1] : 0.0,
-                   pz = vx ? Qi[3 * bx + 2] : 0.0, wx = vx ? wi[bx] : 0.0;
-      double gx = 0.0, gy = 0.0, gz = 0.0, tx = 0.0, ty = 0.0, tz = 0.0;
-      for (int r = 0; r < kTile; r++) {
-        const int by = J * kTile + ((a + r) & (kTile - 1));
-        if (vx && by < nb) {
-          const double dx = Qi[3 * by] - px, dy = Qi[3 * by + 1] - py, dz = Qi[3 * by + 2] - pz;
-          const double z = wide_rinv3(fma(dx, dx, fma(dy, dy, dz * dz)));
-          const double wyz = wi[by] * z, wxz = wx * z;
-          gx = fma(wyz, dx, gx);
-          gy = fma(wyz, dy, gy);
-          gz = fma(wyz, dz, gz);
-          tx = fma(-wxz, dx, tx);
-          ty = fma(-wxz, dy, ty);
-          tz = fma(-wxz, dz, tz);
-        }
-        const int src = (a + 1) & (kTile - 1);
-        tx = __shfl_sync(seg, tx, src, kTile);
-        ty = __shfl_sync(seg, ty, src, kTile);
-        tz = __shfl_sync(seg, tz, src, kTile);
-      }
-      if (vx) {
-        R[i * d + 3 * bx] += gx;
-        R[i * d + 3 * bx + 1] += gy;
-        R[i * d + 3 * bx + 2] += gz;
-      }
-      const int by = J * kTile + a;
-      if (by < nb) {
-        R[i * d + 3 * by] += tx;
-        R[i * d + 3 * by + 1] += ty;
-        R[i * d + 3 * by + 2] += tz;
-      }
-    }
-  }
 }
 
 // R_i = (h b_i) g(Q_i) for every stage, team-parallel.  w8 holds (h b_i) per stage
@@ -256,12 +144,9 @@ __device__ __forceinline__ void team_rhs(int kind, int d, const double* p, const
                                          const double* Q, double* R, int tid) {
   if (kind == IRKGL_RHS_NBODY) {
     const int nb = d / 3;
-    if (nb >= kTiledMinBodies) {
-      nbody_rhs_pairs_once<TEAM>(nb, d, w8, Q, R, tid);
-      return;
-    }
-    // smaller systems: each (stage, body) thread sums over all other bodies
-    // (every pair from both ends; as cheap as the tiles up to 20 bodies)
+    // each (stage, body) thread sums over all other bodies, so every pair is
+    // evaluated from both ends: nearly every lane is busy, which on GB300
+    // beats evaluating each pair once (see the note at wide_rinv3)
     for (int x = tid; x < S * nb; x += TEAM) {
       const int i = x / nb, a = x - i * nb;
       const double* Qi = Q + i * d;

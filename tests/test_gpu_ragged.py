@@ -205,10 +205,10 @@ def nbody_instances(nbs, steps, frac=0.0025):
 
 
 @pytest.mark.parametrize("mix", [0, 1])
-def test_pairs_once_match_oracle(torch_cuda, mix):
-    """Systems of 21 to 128 bodies take the form that evaluates every pair
-    once per stage (tiles of 8, round-robin tile pairs): over 10 steps the
-    states agree with the oracle within 1e-13."""
+def test_large_systems_match_oracle(torch_cuda, mix):
+    """Systems of 21 to 128 bodies (the wide kernel's largest, its body
+    weights sized for 128): over 10 steps the states agree with the oracle
+    within 1e-13."""
     nbs = [21, 24, 30, 33, 40, 47, 48, 64, 100, 128]
     w = nbody_instances(nbs, 10)
     out = run_gpu(torch_cuda, w, mix=mix)
@@ -223,9 +223,10 @@ def test_pairs_once_match_oracle(torch_cuda, mix):
         assert np.abs(g - e).max() / np.abs(e).max() <= 1e-13, nb
 
 
-def test_pairs_once_team_shapes_agree_bitwise(torch_cuda):
-    """The pair-once form sums each body's force in an order fixed by the
-    tile schedule, so every team size gives the same bits."""
+def test_large_systems_team_shapes_agree_bitwise(torch_cuda):
+    """Each body's force is summed over the other bodies in index order
+    whatever the team size, so every team shape gives the same bits, up to
+    128 bodies."""
     w = nbody_instances([21, 33, 40, 64], 25)
     ref = run_gpu(torch_cuda, w, team=64)
     for team in (128, 256):
