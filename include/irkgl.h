@@ -297,8 +297,8 @@ int irkgl_integrate1(struct irkgl_ctx* ctx, const double* y0, int batch, const l
 
 /* irkgl_advance1: continue device-resident first-order trajectories in place
  * (y, y_lo [batch][D], l_prev [batch][8][D], all required), carrying H0 /
- * dH_max / iters like irkgl_advance, so chunked runs give the bits of one
- * run. */
+ * dH_max / iters like irkgl_advance (a NaN entry of H0 included), so chunked
+ * runs give the bits of one run. */
 int irkgl_advance1(struct irkgl_ctx* ctx, double* y, double* y_lo, double* l_prev, const double* h,
                    const long long* nsteps, double* H0, int h0_init, double* dH_max,
                    long long* iters, int* status, int batch, void* cuda_stream);

@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(BLOCK)
     if (__all_sync(FULL, exhausted && !active)) break;
 
     {
-      const bool want = active && n == 0 && a.monitor > 0 && (!a.H0_io || a.h0_init);
+      const bool want = active && n == 0 && a.monitor > 0 && (!a.H0_io || a.h0_init || (H0 != H0 && N > 0));
       const unsigned h0mask = __ballot_sync(FULL, want);
       if (want) {
         H0 = energy(h0mask);

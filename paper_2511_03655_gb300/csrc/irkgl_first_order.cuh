@@ -48,7 +48,8 @@ struct KArgs1 {
   long long* steps_done;
   unsigned int* counter;
   const double* params;
-  double* H0_io;
+  double* H0_io;  // read, or written when h0_init or when the entry is NaN (computed at
+                  // the trajectory's first step of the call)
   int h0_init;
   int accumulate;
   int monitor_local;  // 1: dH_max = max_n |(H_n - H_{n-1}) / H_{n-1}| (Eq. DHlocmax)
@@ -259,7 +260,7 @@ __global__ void __launch_bounds__(BLOCK)
 
     // ---------------- H_0 before the first step (exact ballot of the lanes)
     {
-      const bool want = active && n == 0 && a.monitor > 0 && (!a.H0_io || a.h0_init);
+      const bool want = active && n == 0 && a.monitor > 0 && (!a.H0_io || a.h0_init || (H0 != H0 && N > 0));
       const unsigned h0mask = __ballot_sync(FULL, want);
       if (want) {
         H0 = group_energy1<Rhs, LPT, NS>(rhs, yh, h0mask, gbase);

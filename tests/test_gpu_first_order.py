@@ -149,3 +149,27 @@ def test_wrong_form_calls_are_rejected(torch_cuda):
     with pytest.raises(irkgl.IrkglError):
         kep.integrate1(torch.zeros((4, 2), dtype=torch.float64, device="cuda"), nsteps_all=1)
     kep.close()
+
+
+def test_advance1_nan_h0_joins_like_a_fresh_run(torch_cuda):
+    """irkgl_advance1 with h0_init = 0 and H0 entries holding NaN computes
+    H0 at each trajectory's first step: two chunks give the bits of one
+    fresh integrate1 (state, sweeps, dH_max)."""
+    torch = torch_cuda
+    y0 = workloads.schwarzschild_ensemble(96, seed_id=41)
+    ig = integ()
+    one = ig.integrate1(torch.tensor(y0, device="cuda"), nsteps_all=90)
+    f = dict(dtype=torch.float64, device="cuda")
+    y = torch.tensor(y0, **f)
+    ylo = torch.zeros_like(y)
+    lp = torch.zeros((96, 8, 4), **f)
+    H0 = torch.full((96,), float("nan"), **f)
+    dH = torch.zeros(96, **f)
+    it = torch.zeros(96, dtype=torch.int64, device="cuda")
+    for k in (40, 50):
+        ns = torch.full((96,), k, dtype=torch.int64, device="cuda")
+        ig.advance1(y, ylo, lp, ns, H0=H0, h0_init=False, dH_max=dH, iters=it)
+    torch.cuda.synchronize()
+    assert torch.equal(one.y, y) and torch.equal(one.iters, it) and torch.equal(one.dH_max, dH)
+    assert torch.isfinite(H0).all()
+    ig.close()
