@@ -250,30 +250,31 @@ class _Pool:
         self.waiting: list[Request] = []
         self.event: torch.cuda.Event | None = None  # end of the launch in flight
         self.launch_events: list = []              # (start, end, traj-steps) per launch
-        self.rate = None                           # traj-steps per second, measured
-        self.steps_in_flight = 0
+        self.K = 16                                # steps per tick, adapted to the target
+        self._rated = 0                            # launches whose time has set K
+        self._k_of_launch: list = []               # largest k of each launch
+        self._traj_last = 0                        # trajectories of the last launch
         self.ctx = 0
         self.allocated = False
-
-    # one K for every member of a tick: about `target` seconds of work
-    def _tick_steps(self, live_traj: int) -> int:
-        if self.rate is None or live_traj == 0:
-            return 16
-        return int(max(1, min(1 << 20, self.target * self.rate / live_traj)))
 
     def idle(self) -> bool:
         return self.event is None or self.event.query()
 
     def settle(self):
-        """After the launch in flight: update the measured rate and return the
-        members whose horizon is reached."""
-        if self.launch_events:
-            a, b, n = self.launch_events[-1]
-            if n > 0 and b.query():
+        """After the launch in flight: size the next tick from the time per
+        step of the last one (K steps take about `target` seconds, whatever
+        the batch: a pool holding one long trajectory gets short ticks too,
+        so requests that arrive behind it wait one tick at most), and return
+        the members whose horizon is reached."""
+        if self._rated < len(self.launch_events):
+            a, b, _ = self.launch_events[-1]
+            k_last = self._k_of_launch[-1]
+            if b.query():
+                self._rated = len(self.launch_events)
                 dt = a.elapsed_time(b) * 1e-3
-                if dt > 0:
-                    r = n / dt
-                    self.rate = r if self.rate is None else 0.5 * self.rate + 0.5 * r
+                if dt > 0 and k_last > 0:
+                    want = k_last * self.target / dt
+                    self.K = int(max(1, min(1 << 20, k_last * 4, max(k_last / 4, want))))
         finished = [m for m in self.members if m.remaining == 0 and m.k >= 0]
         return finished
 
@@ -281,7 +282,13 @@ class _Pool:
         live = [m for m in self.members if m.remaining > 0]
         if not live:
             return 0
-        K = self._tick_steps(sum(m.req.batch for m in live))
+        # K was measured on the last launch's trajectories: when more joined
+        # since, a step may take proportionally longer, so shorten the tick
+        traj = sum(m.req.batch for m in live)
+        K = self.K
+        if self._traj_last and traj > self._traj_last:
+            K = max(1, int(K * self._traj_last / traj))
+        self._traj_last = traj
         for m in live:
             m.k = min(m.remaining, K)
         start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -291,6 +298,7 @@ class _Pool:
             self._launch(live)
             end.record(self.stream)
         self.launch_events.append((start, end, sum(m.k * m.req.batch for m in live)))
+        self._k_of_launch.append(max(m.k for m in live))
         for m in live:
             m.remaining -= m.k
         self.event = end
@@ -584,8 +592,9 @@ class Server:
     when the pool's first request is admitted; a pool whose largest request
     is bigger gets that size): requests wait until their pool has room.
     mix = 1 runs the fixed-point stage mixing wherever a kernel with it is
-    compiled (``new_context``).  target_tick_s sizes the steps per tick of
-    each pool from its measured rate."""
+    compiled (``new_context``).  target_tick_s is the wanted duration of a
+    tick: each pool sizes its steps per tick from the time per step of its
+    previous tick."""
 
     def __init__(self, pool_bytes: int = 1 << 30, max_active: int = 1 << 20, device=None,
                  policy: str = "fifo", mix: int = 1, target_tick_s: float = 0.01):
@@ -633,7 +642,7 @@ class Server:
         pending = sorted(requests, key=lambda r: r.arrival)
         self._pools_for(pending)
         for p in self.pools.values():
-            p.launch_events = []
+            p.launch_events, p._k_of_launch, p._rated, p._traj_last = [], [], 0, 0
         finishing: list[tuple[_Pool, _Member]] = []
         active = 0
         torch.cuda.synchronize(self.device)
