@@ -107,8 +107,10 @@ def parse():
     ap.add_argument("--ninst", type=int, default=4096, help="instances for the uneven workload")
     ap.add_argument("--stage-sweep", action="store_true",
                     help="schwarzschild: also the work-precision sweep of the s = 2, 4, 6, 8 schemes")
-    ap.add_argument("--mix", type=int, default=None, choices=[0, 1],
-                    help="stage mixing: 1 fixed-point sums on the integer pipes, 0 FP64 FMA chain; "
+    ap.add_argument("--mix", type=int, default=None, choices=[0, 1, 2],
+                    help="stage mixing: 1 fixed-point sums on the integer pipes, 0 FP64 FMA chain, "
+                         "2 the reproducible form (kepler, nbody6: the plain operation sequence, "
+                         "bit-identical to any IEEE FP64 program of it); "
                          "default: the faster measured on GB300 (fixed point everywhere except the "
                          "6-body register tile, where the integer chains cost occupancy)")
     ap.add_argument("--serve-requests", type=int, default=16,
@@ -125,6 +127,10 @@ def parse():
 # --------------------------------------------------------------------------
 # compact lines of the other configurations (each its own bench.py run)
 # --------------------------------------------------------------------------
+MIXING = {0: "FP64 FMA chain", 1: "fixed-point (integer pipes)",
+          2: "reproducible: the plain operation sequence, every FP64 operation rounded, "
+             "one thread per trajectory"}
+
 SUBLINES = {
     "nbody6": ["--workload", "nbody6", "--batch", "16384", "--traj-steps", "1000", "--steps", "2",
                "--warmup", "1", "--skip-extras"],
@@ -132,6 +138,8 @@ SUBLINES = {
                "--warmup", "1", "--skip-extras"],
     "schwarzschild": ["--workload", "schwarzschild", "--batch", "16384", "--steps", "2", "--warmup",
                       "1", "--skip-extras"],
+    "kepler_reproducible": ["--workload", "kepler", "--mix", "2", "--periods", "10", "--steps", "2",
+                            "--warmup", "1", "--skip-extras"],
 }
 
 
@@ -1223,7 +1231,7 @@ def main():
         "config": {"workload": desc, "batch_per_gpu": args.batch,
                    "periods": args.periods if args.workload == "kepler" else None,
                    "lanes_per_traj": integ.tile, "tile_layout": integ.layout,
-                   "mixing": "fixed-point (integer pipes)" if mix else "FP64 FMA chain",
+                   "mixing": MIXING[mix],
                    "order": "natural" if args.no_order else "similarity (e descending)",
                    "l2": "state ~12.6 MB < L2; L2 flushed with a 256 MiB write before every timed step",
                    "parallelism": f"dp{world} (independent shards, no collective on the data path)"},
@@ -1238,9 +1246,15 @@ def main():
                      "fp64_inst": fp64_inst, "issue": issue,
                      "peak_source": "FP64 FMA-chain probe (irkgl_probe_fp64_fma) measured live, "
                                     "2 flops per FMA",
-                     "kernel": ("irkgl_kernel_cs" if integ.layout == "component split" else "irkgl_kernel")
+                     "kernel": {"component split": "irkgl_kernel_cs", "stage split": "irkgl_kernel",
+                                "reproducible": "irkgl_kernel_repro"}[integ.layout]
                                + f"<{args.workload}>", "flops_per_launch": flops_launch,
-                     "note": ("the algorithmic count includes the 9 flops of each x^(-3/2), which "
+                     "note": ("the method's algorithmic count; the reproducible form runs the "
+                              "plain sequence entirely on the FP64 pipe, with IEEE division and "
+                              "square root (multi-instruction FP64 sequences) and the two-matrix "
+                              "initial guess, so it executes more FP64 instructions than counted"
+                              if mix == 2 else
+                              "the algorithmic count includes the 9 flops of each x^(-3/2), which "
                               "run on the integer pipes (an integer correction of an FP32 seed)"
                               + ("; with the fixed-point stage mixing the mixing flops of each sweep "
                                  "(and the initial guess's) run as exact 128-bit integer multiply-adds "

@@ -152,8 +152,20 @@ enum {
                                    chain (default); 1 = exact fixed-point sums on the integer
                                    pipes, rounded once (the one-lane and component-split tiles,
                                    the tiles with the stage rows spread over lanes, the wide
-                                   kernel); needs the default tables.  A call with no compiled
-                                   kernel for the choice returns IRKGL_ERR_UNSUPPORTED */
+                                   kernel); needs the default tables.  2 = reproducible: every
+                                   FP64 operation of the method's plain definition rounded
+                                   separately, in that definition's order (the two-matrix
+                                   initial guess of Eq. IRK_init2 with nu and mu, sums left to
+                                   right from j = 1, g and H with IEEE division and square root,
+                                   dH as |(H_n - H_0) / H_0|), one thread per trajectory; any
+                                   IEEE-754 binary64 program of the same sequence (no
+                                   contraction, no flush to zero) returns the same bits, sweep
+                                   counts included.  Uses the context's own tables.  Second-order
+                                   calls of the register kinds only (Kepler, Henon-Heiles,
+                                   harmonic d <= 3, N-body 3..6 bodies; not the time-dependent
+                                   kind, whose sin(t) is not correctly rounded, nor the ragged
+                                   calls).  A call with no compiled kernel for the choice
+                                   returns IRKGL_ERR_UNSUPPORTED */
   IRKGL_OPT_TILE_LAYOUT = 10,   /* second-order kinds: 1 = the stage-split tiles (LPT lanes per
                                    trajectory share the stages); 2 = the component-split tile for
                                    d = 2 (Kepler, Henon-Heiles): two lanes per trajectory, each
@@ -397,7 +409,8 @@ const char* irkgl_last_cuda_error(void);
 int irkgl_get_tile(struct irkgl_ctx* ctx);
 
 /* The tile layout a call on this context runs: 1 = stage split, 2 = component
- * split (IRKGL_OPT_TILE_LAYOUT resolved); first-order contexts report 1.
+ * split (IRKGL_OPT_TILE_LAYOUT resolved), 3 = the reproducible form's one
+ * thread per trajectory (IRKGL_OPT_MIX = 2); first-order contexts report 1.
  * Returns IRKGL_ERR_INVALID for a NULL context. */
 int irkgl_get_layout(struct irkgl_ctx* ctx);
 

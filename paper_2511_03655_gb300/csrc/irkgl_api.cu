@@ -55,6 +55,13 @@ const KernelEntry* find_kernel(int kind, int dim, int lpt, int block, int mix = 
   return nullptr;
 }
 
+const irkgl::ReproEntry* find_repro(int kind, int dim) {
+  const irkgl::ReproTable t = irkgl::kernels_repro();
+  for (int i = 0; i < t.count; i++)
+    if (t.entries[i].kind == kind && t.entries[i].dim == dim) return &t.entries[i];
+  return nullptr;
+}
+
 // Built-in default tile per (kind, dim): the smallest LPT that is compiled,
 // preferring 2 for d = 2 (both components' compensated updates in one pass).
 const irkgl::KernelEntry1* find_kernel1(int kind, int dim, int lpt, int block, int nst = 8, int mix = 0,
@@ -143,6 +150,7 @@ struct irkgl_ctx {
   int sm_count;
   Coef coef;
   Coef1 coef1;  // first-order kinds: b, mu, nu
+  irkgl::CoefRepro coefr;  // the caller's tables for the reproducible form (mix = 2)
   double* d_params;
   int nparams;
   unsigned* d_counter;
@@ -269,6 +277,15 @@ int irkgl_create(irkgl_ctx** out, irkgl_rhs f, int dim, double h, const irkgl_co
   }
   for (int x = 0; x < 64; x++) c->coef.eta[x] = tab.eta[x];
   for (int i = 0; i < 8; i++) c->coef1.b[i] = tab.b[i];
+  for (int i = 0; i < 8; i++) {
+    c->coefr.c[i] = tab.c[i];
+    c->coefr.b[i] = tab.b[i];
+  }
+  for (int x = 0; x < 64; x++) {
+    c->coefr.mu[x] = tab.mu[x];
+    c->coefr.nu[x] = tab.nu[x];
+    c->coefr.eta[x] = tab.eta[x];
+  }
   for (int x = 0; x < 64; x++) {
     c->coef1.mu[x] = tab.mu[x];
     c->coef1.nu[x] = tab.nu[x];
@@ -332,7 +349,7 @@ int irkgl_set_option(irkgl_ctx* c, int option, long long value) {
       c->grid_blocks = static_cast<int>(value);
       return IRKGL_OK;
     case IRKGL_OPT_MIX:
-      if (value != 0 && value != 1) return IRKGL_ERR_INVALID;
+      if (value < 0 || value > 2) return IRKGL_ERR_INVALID;
       c->mix = static_cast<int>(value);
       return IRKGL_OK;
     case IRKGL_OPT_TILE_LAYOUT:
@@ -377,6 +394,7 @@ int irkgl_get_layout(irkgl_ctx* c) {
   if (!c) return IRKGL_ERR_INVALID;
   int lpt = 0, layout = 0;
   if (first_order_kind(c->kind)) resolve_tile1(c, &lpt, &layout);
+  else if (c->mix == 2) return 3;  // the reproducible form: one thread per trajectory
   else resolve_tile(c, &lpt, &layout);
   return layout ? 2 : 1;
 }
@@ -389,6 +407,7 @@ int irkgl_get_tile(irkgl_ctx* c) {
     return find_kernel1(c->kind, c->dim, lpt, c->block, c->stages, c->mix, layout) ? lpt : 0;
   }
   int lpt = 0, layout = 0;
+  if (c->mix == 2) return find_repro(c->kind, c->dim) ? 1 : 0;
   if (!first_order_kind(c->kind)) {
     resolve_tile(c, &lpt, &layout);
     return find_kernel(c->kind, c->dim, lpt, c->block, c->mix, layout) ? lpt : 0;
@@ -416,9 +435,37 @@ static void resolve_tile(const irkgl_ctx* c, int* lpt, int* layout) {
   }
 }
 
+// The reproducible form: one thread per trajectory, a persistent grid of the
+// occupancy's full wave (or the requested size), capped at the batch.
+static int run_repro(irkgl_ctx* c, KArgs& a, cudaStream_t st) {
+  const irkgl::ReproEntry* ke = find_repro(c->kind, c->dim);
+  if (!ke) return IRKGL_ERR_UNSUPPORTED;
+  constexpr int kBlock = 128;
+  a.counter = c->d_counter;
+  if (!a.params) a.params = c->d_params;
+  a.kmax = c->kmax;
+  a.monitor = c->monitor;
+  a.monitor_local = c->monitor_local;
+  const long long need = (static_cast<long long>(a.batch) + kBlock - 1) / kBlock;
+  int grid = c->grid_blocks;
+  if (grid <= 0) {
+    int per_sm = 0;
+    IRKGL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ke->fn, kBlock, 0));
+    if (per_sm < 1) per_sm = 1;
+    grid = per_sm * c->sm_count;
+  }
+  if (grid > need) grid = static_cast<int>(need);
+  if (grid < 1) grid = 1;
+  IRKGL_CUDA(cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned), st));
+  ke->launch(dim3(grid), dim3(kBlock), st, a, c->coefr);
+  IRKGL_CUDA(cudaGetLastError());
+  return IRKGL_OK;
+}
+
 static int run(irkgl_ctx* c, KArgs& a, cudaStream_t st) {
   if (first_order_kind(c->kind)) return IRKGL_ERR_INVALID;  // use the irkgl_*1 calls
   if (c->stages != 8) return IRKGL_ERR_UNSUPPORTED;        // s-stage variants: first-order form only
+  if (c->mix == 2) return run_repro(c, a, st);
   if (c->mix && !c->default_tables) return IRKGL_ERR_UNSUPPORTED;
   int lpt = 0, layout = 0;
   resolve_tile(c, &lpt, &layout);

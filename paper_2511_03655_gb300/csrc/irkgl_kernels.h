@@ -9,6 +9,7 @@
 
 #include "irkgl_cs.cuh"
 #include "irkgl_device.cuh"
+#include "irkgl_repro.cuh"
 
 namespace irkgl {
 
@@ -38,6 +39,25 @@ struct KernelTable {
   int count;
 };
 
+// the reproducible form (IRKGL_OPT_MIX = 2): one thread per trajectory
+struct ReproEntry {
+  int kind;
+  int dim;
+  const void* fn;
+  void (*launch)(dim3, dim3, cudaStream_t, const KArgs&, const CoefRepro&);
+};
+
+template <class Rhs, int BLOCK, int MINB>
+void launch_repro_impl(dim3 grid, dim3 block, cudaStream_t st, const KArgs& a, const CoefRepro& c) {
+  irkgl_kernel_repro<Rhs, BLOCK, MINB><<<grid, block, 0, st>>>(a, c);
+}
+
+struct ReproTable {
+  const ReproEntry* entries;
+  int count;
+};
+ReproTable kernels_repro();
+
 KernelTable kernels_kepler();
 KernelTable kernels_henon_heiles();
 KernelTable kernels_harmonic();
@@ -58,3 +78,8 @@ KernelTable kernels_nbody();
   }
 #define IRKGL_ENTRY_MIX(KIND, DIM, RHS, LPT, BLOCK, MIX) IRKGL_ENTRY_TUNED(KIND, DIM, RHS, LPT, BLOCK, MIX, 1)
 #define IRKGL_ENTRY(KIND, DIM, RHS, LPT, BLOCK) IRKGL_ENTRY_MIX(KIND, DIM, RHS, LPT, BLOCK, 0)
+#define IRKGL_ENTRY_REPRO(KIND, DIM, RHS, BLOCK, MINB)                                          \
+  ::irkgl::ReproEntry {                                                                          \
+    KIND, DIM, (const void*)::irkgl::irkgl_kernel_repro<RHS, BLOCK, MINB>,                       \
+        ::irkgl::launch_repro_impl<RHS, BLOCK, MINB>                                             \
+  }

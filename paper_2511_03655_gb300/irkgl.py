@@ -600,8 +600,10 @@ class Integrator:
 
     @property
     def layout(self) -> str:
-        """The tile layout calls run: "stage split" or "component split"."""
-        return {1: "stage split", 2: "component split"}[load().irkgl_get_layout(_P(self.ctx))]
+        """The tile layout calls run: "stage split", "component split", or
+        "reproducible" (one thread per trajectory, mix = 2)."""
+        return {1: "stage split", 2: "component split",
+                3: "reproducible"}[load().irkgl_get_layout(_P(self.ctx))]
 
     def step(self, *args, **kw):
         return irkgl_step(self.ctx, self.dim, *args, **kw)

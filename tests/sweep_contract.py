@@ -33,6 +33,10 @@ steps, also with the s-stage schemes of Sec. 5.2; harmonic: 4,096 three-componen
 10,000 steps; ragged: 128 instances of the ragged batch on the wide kernel
 over 200 steps, steps that failed on the GPU left out.)
 
+The reproducible form (IRKGL_OPT_MIX = 2) needs no contract: it performs
+the oracle's operation sequence, and tests/test_gpu_reproducible.py requires
+every step's sweep count to be equal.
+
 A test of n compared steps passes when no step differs by more than the
 class's largest difference and the number of steps beyond +-1 stays below
 the 1e-6 upper tail of a Poisson count with mean MARGIN x rate x n.  Sweep

@@ -1,0 +1,226 @@
+"""The reproducible form (IRKGL_OPT_MIX = 2) against the oracle, bit for bit.
+
+Both sides perform the plain operation sequence of the method: the two-matrix
+initial guess of Eq. IRK_init2, the sweep of Eq. IRK_FP2 with sums left to
+right, Eqs. Delta_n / stopping on FP64 values, the compensated update of
+Eq. qnvn2, and g and H with IEEE division and square root, every operation
+rounded once.  So every output must be equal, not close: q, v and their
+compensation parts, R_prev, the sweep count of every step and their totals,
+dH_max, steps and status.  The +-1 sweep requirement therefore holds with a
+difference of 0 on every step, including the workloads whose fast tiles
+differ beyond +-1 at the roundoff floor (Henon-Heiles at h = 1).
+"""
+import numpy as np
+import pytest
+
+from oracle import cbind, coeffs
+from paper_2511_03655_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    from paper_2511_03655_gb300 import build, irkgl
+    build.build()
+    irkgl.load()
+    torch.cuda.init()
+    return torch, irkgl
+
+
+def same(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return a.shape == b.shape and a.dtype == b.dtype and np.array_equal(a.view(np.uint8), b.view(np.uint8))
+
+
+def cases():
+    w = workloads.kepler_ensemble(batch=512, periods=2)
+    hq, hv, _ = workloads.henon_heiles_ensemble(256)
+    nb = workloads.nbody_ensemble(copies=48, nbodies=6, steps=600)
+    rng = np.random.default_rng(11)
+    return {
+        "kepler": (irkgl_kind("KEPLER"), cbind.KEPLER, [1.0], w["q0"], w["v0"], w["h"], w["nsteps"]),
+        "henon_heiles_h1": (irkgl_kind("HENON_HEILES"), cbind.HENON_HEILES, [1.0], hq, hv,
+                            np.full(len(hq), 1.0), np.full(len(hq), 400, dtype=np.int64)),
+        "harmonic3": (irkgl_kind("HARMONIC"), cbind.HARMONIC, [1.3], rng.standard_normal((128, 3)),
+                      rng.standard_normal((128, 3)), np.full(128, 0.4), np.full(128, 500, dtype=np.int64)),
+        "nbody6": (irkgl_kind("NBODY"), cbind.NBODY, nb["params"], nb["q0"], nb["v0"], nb["h"], nb["nsteps"]),
+    }
+
+
+def irkgl_kind(name):
+    from paper_2511_03655_gb300 import irkgl
+    return getattr(irkgl, "RHS_" + name)
+
+
+def oracle(ko, params, q0, v0, h, nsteps, **kw):
+    return cbind.run(ko, params, q0, v0, h, nsteps, nthreads=8, **kw)
+
+
+@pytest.mark.parametrize("name", ["kepler", "henon_heiles_h1", "harmonic3", "nbody6"])
+def test_integrate_bitwise(env, name):
+    torch, irkgl = env
+    kg, ko, params, q0, v0, h, ns = cases()[name]
+    B, d = q0.shape
+    integ = irkgl.Integrator(kg, params, d, float(h[0]), mix=2)
+    assert integ.layout == "reproducible" and integ.tile == 1
+    f = dict(device="cuda")
+    out = integ.integrate(torch.tensor(q0, **f), torch.tensor(v0, **f), nsteps=torch.tensor(ns, **f),
+                          h=torch.tensor(h, **f))
+    torch.cuda.synchronize()
+    o = oracle(ko, params, q0, v0, h, ns)
+    g = {k: getattr(out, k).cpu().numpy() for k in ("q", "v", "q_lo", "v_lo", "r_prev", "dH_max",
+                                                      "iters", "steps", "status")}
+    assert (o["status"] == 0).all()
+    for k, ok in (("q", "q"), ("v", "v"), ("q_lo", "q_lo"), ("v_lo", "v_lo"), ("r_prev", "r_prev"),
+                  ("dH_max", "dH_max")):
+        assert same(g[k], o[ok]), (name, k)
+    assert np.array_equal(g["iters"], o["iters_total"]), name
+    assert np.array_equal(g["steps"], o["steps"]) and np.array_equal(g["status"], o["status"])
+    integ.close()
+
+
+@pytest.mark.parametrize("name", ["kepler", "henon_heiles_h1"])
+def test_sweep_counts_equal_on_every_step(env, name):
+    """irkgl_step with the per-step sweep history: every step's count equals
+    the oracle's (difference 0 on all steps), and the state after the last
+    step is the oracle's."""
+    torch, irkgl = env
+    kg, ko, params, q0, v0, h, _ = cases()[name]
+    n = 300
+    B, d = q0.shape
+    integ = irkgl.Integrator(kg, params, d, float(h[0]), mix=2)
+    f = dict(dtype=torch.float64, device="cuda")
+    q, v = torch.tensor(q0, **f), torch.tensor(v0, **f)
+    ql, vl = torch.zeros_like(q), torch.zeros_like(v)
+    rp = torch.zeros((B, 8, d), **f)
+    it = torch.zeros((B, n), dtype=torch.int32, device="cuda")
+    st = torch.zeros(B, dtype=torch.int32, device="cuda")
+    integ.step(q, v, ql, vl, rp, h=torch.tensor(h, **f), nsteps=n, iters=it, status=st)
+    torch.cuda.synchronize()
+    o = oracle(ko, params, q0, v0, h, n, iters_len=n)
+    assert np.array_equal(it.cpu().numpy(), o["iters"])
+    assert np.array_equal(st.cpu().numpy(), o["status"])
+    for a, k in ((q, "q"), (v, "v"), (ql, "q_lo"), (vl, "v_lo"), (rp, "r_prev")):
+        assert same(a.cpu().numpy(), o[k]), k
+    integ.close()
+
+
+def test_chunked_advance_and_host_buffers(env):
+    """irkgl_advance in three chunks (H0 carried, dH_max and sweep totals
+    accumulated) and irkgl_integrate_host give the oracle's single run."""
+    torch, irkgl = env
+    kg, ko, params, q0, v0, h, ns = cases()["kepler"]
+    B, d = q0.shape
+    f = dict(dtype=torch.float64, device="cuda")
+    integ = irkgl.Integrator(kg, params, d, float(h[0]), mix=2)
+    q, v = torch.tensor(q0, **f), torch.tensor(v0, **f)
+    ql, vl = torch.zeros_like(q), torch.zeros_like(v)
+    rp = torch.zeros((B, 8, d), **f)
+    H0 = torch.zeros(B, **f)
+    dH = torch.zeros(B, **f)
+    it = torch.zeros(B, dtype=torch.int64, device="cuda")
+    st = torch.zeros(B, dtype=torch.int32, device="cuda")
+    hh = torch.tensor(h, **f)
+    left = ns.copy()
+    for c, frac in enumerate((0.3, 0.5, 1.0)):
+        k = np.minimum(left, np.ceil(frac * ns).astype(np.int64) - (ns - left))
+        integ.advance(q, v, ql, vl, rp, h=hh, nsteps=torch.tensor(k, device="cuda"), H0=H0,
+                      h0_init=(c == 0), dH_max=dH, iters=it, status=st)
+        left -= k
+    assert (left == 0).all()
+    torch.cuda.synchronize()
+    o = oracle(ko, params, q0, v0, h, ns)
+    for a, k in ((q, "q"), (v, "v"), (ql, "q_lo"), (vl, "v_lo"), (rp, "r_prev"), (dH, "dH_max")):
+        assert same(a.cpu().numpy(), o[k]), k
+    assert np.array_equal(it.cpu().numpy(), o["iters_total"])
+    host = integ.integrate_host(torch.tensor(q0), torch.tensor(v0), nsteps=torch.tensor(ns),
+                                h=torch.tensor(h))
+    assert same(host.q.numpy(), o["q"]) and same(host.v.numpy(), o["v"])
+    assert np.array_equal(host.iters.numpy(), o["iters_total"])
+    integ.close()
+
+
+def test_failures_and_own_tables(env):
+    """Status 1 (sweep cap) and 2 (non-finite stage value, a Kepler
+    collision) at the oracle's step with its state, and a context built
+    with its own tables (nu = 0: the guess from v alone) follows them."""
+    torch, irkgl = env
+    q0 = np.array([[0.0, 0.0], [0.5, 0.0], [0.9, 0.0], [1.0, 0.0]])
+    v0 = np.array([[0.0, 0.0], [0.0, np.sqrt(3.0)], [0.0, 1.1], [0.0, 1.0]])
+    h = np.full(4, 2 * np.pi / 120)
+    ns = np.full(4, 400, dtype=np.int64)
+    f = dict(device="cuda")
+    for kmax in (100, 4):
+        integ = irkgl.Integrator(irkgl.RHS_KEPLER, [1.0], 2, h[0], mix=2, kmax=kmax)
+        out = integ.integrate(torch.tensor(q0, **f), torch.tensor(v0, **f), nsteps=torch.tensor(ns, **f),
+                              h=torch.tensor(h, **f))
+        o = oracle(cbind.KEPLER, [1.0], q0, v0, h, ns, kmax=kmax)
+        assert np.array_equal(out.status.cpu().numpy(), o["status"])
+        assert (o["status"] != 0).any()
+        assert np.array_equal(out.steps.cpu().numpy(), o["steps"])
+        assert np.array_equal(out.iters.cpu().numpy(), o["iters_total"])
+        assert same(out.q.cpu().numpy(), o["q"]) and same(out.v.cpu().numpy(), o["v"])
+        integ.close()
+    tab = {k: np.array(val, dtype=np.float64) for k, val in coeffs.fp64_tables().items()
+           if k in ("c", "b", "mu", "eta", "nu")}
+    tab["nu"] = np.zeros_like(tab["nu"])
+    w = workloads.kepler_ensemble(batch=128, periods=1)
+    own = {k: tab[k] for k in ("c", "b", "mu", "eta", "nu")}
+    integ = irkgl.Integrator(irkgl.RHS_KEPLER, [1.0], 2, float(w["h"][0]), coeffs=own, mix=2)
+    out = integ.integrate(torch.tensor(w["q0"], **f), torch.tensor(w["v0"], **f),
+                          nsteps=torch.tensor(w["nsteps"], **f), h=torch.tensor(w["h"], **f))
+    o = oracle(cbind.KEPLER, [1.0], w["q0"], w["v0"], w["h"], w["nsteps"], tab=tab)
+    assert same(out.q.cpu().numpy(), o["q"]) and same(out.v.cpu().numpy(), o["v"])
+    assert np.array_equal(out.iters.cpu().numpy(), o["iters_total"])
+    integ.close()
+
+
+def test_per_trajectory_params_multi(env):
+    """irkgl_advance_multi with per-trajectory mu (Kepler) in the reproducible
+    form: each trajectory equals the oracle run with its own parameter."""
+    torch, irkgl = env
+    w = workloads.kepler_ensemble(batch=256, periods=1)
+    B = 256
+    mu = 0.5 + np.linspace(0.0, 1.0, B)
+    f = dict(dtype=torch.float64, device="cuda")
+    integ = irkgl.Integrator(irkgl.RHS_KEPLER, [1.0], 2, float(w["h"][0]), mix=2)
+    q, v = torch.tensor(w["q0"], **f), torch.tensor(w["v0"], **f)
+    ql, vl = torch.zeros_like(q), torch.zeros_like(v)
+    rp = torch.zeros((B, 8, 2), **f)
+    H0 = torch.full((B,), float("nan"), **f)
+    dH = torch.zeros(B, **f)
+    it = torch.zeros(B, dtype=torch.int64, device="cuda")
+    st = torch.zeros(B, dtype=torch.int32, device="cuda")
+    irkgl.irkgl_advance_multi(integ.ctx, 2, q, v, ql, vl, rp, torch.tensor(w["nsteps"], device="cuda"),
+                              h=torch.tensor(w["h"], **f), params=torch.tensor(mu[:, None], **f),
+                              param_stride=1, H0=H0, dH_max=dH, iters=it, status=st)
+    torch.cuda.synchronize()
+    o = oracle(cbind.KEPLER, mu[:, None], w["q0"], w["v0"], w["h"], w["nsteps"])
+    for a, k in ((q, "q"), (v, "v"), (rp, "r_prev"), (dH, "dH_max")):
+        assert same(a.cpu().numpy(), o[k]), k
+    assert np.array_equal(it.cpu().numpy(), o["iters_total"])
+    integ.close()
+
+
+def test_full_ensemble_sampled(env):
+    """The 65,536-orbit Kepler ensemble over its full 100 periods in one
+    launch; 192 orbits (every 512th, and the 64 most eccentric) equal the
+    oracle's full-horizon runs bit for bit, sweep totals and dH_max included."""
+    torch, irkgl = env
+    w = workloads.kepler_ensemble()
+    B = len(w["e"])
+    f = dict(device="cuda")
+    integ = irkgl.Integrator(irkgl.RHS_KEPLER, [1.0], 2, float(w["h"][0]), mix=2)
+    out = integ.integrate(torch.tensor(w["q0"], **f), torch.tensor(w["v0"], **f),
+                          nsteps=torch.tensor(w["nsteps"], **f), h=torch.tensor(w["h"], **f))
+    torch.cuda.synchronize()
+    idx = np.unique(np.concatenate([np.arange(0, B, 512), np.argsort(w["e"])[-64:]]))
+    o = oracle(cbind.KEPLER, [1.0], w["q0"][idx], w["v0"][idx], w["h"][idx], w["nsteps"][idx])
+    for k in ("q", "v", "q_lo", "v_lo", "dH_max"):
+        assert same(getattr(out, k).cpu().numpy()[idx], o[k]), k
+    assert np.array_equal(out.iters.cpu().numpy()[idx], o["iters_total"])
+    assert np.array_equal(out.status.cpu().numpy()[idx], o["status"])
+    assert (out.status.cpu().numpy() == 0).all()
+    integ.close()
