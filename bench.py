@@ -653,7 +653,7 @@ def run_uneven(args):
                                f"(central mass + N-1 bodies), half FPUT alpha=0.25 n~U{{8..512}}, "
                                f"h from the step table, {args.traj_steps} steps each",
                    "step_table": "tuning/gb300.json" if tuned else "built-in defaults",
-                   "mixing": "fixed-point (integer pipes)" if args.mix else "FP64 FMA chain",
+                   "mixing": MIXING[args.mix],
                    "tiling": "autotuned: one launch per size bucket on its own stream, team from "
                              "the tile table" if tiles else "bucketed, library team per bucket",
                    "buckets": [{"label": b.label, "instances": b.count, "dmax": b.dmax, "team": b.team}
@@ -870,7 +870,7 @@ def run_first_order(args):
                                f"p_r=0, H=-1/2; t in [0, {SBH_T:g}], h={SBH_H:g} ({nsteps} steps); "
                                "one persistent launch of the first-order (mu form) kernel",
                    "lanes_per_traj": integ.tile, "tile_layout": integ.layout,
-                   "mixing": "fixed-point (integer pipes)" if args.mix else "FP64 FMA chain",
+                   "mixing": MIXING[args.mix],
                    "order": "natural" if args.no_order else "similarity (r0 ascending)",
                    "l2": "state ~10 MB < L2; L2 flushed with a 256 MiB write before every timed step",
                    "parallelism": f"dp{world} (independent shards, no collective on the data path)"},

@@ -160,11 +160,13 @@ enum {
                                    dH as |(H_n - H_0) / H_0|), one thread per trajectory; any
                                    IEEE-754 binary64 program of the same sequence (no
                                    contraction, no flush to zero) returns the same bits, sweep
-                                   counts included.  Uses the context's own tables.  Second-order
-                                   calls of the register kinds only (Kepler, Henon-Heiles,
-                                   harmonic d <= 3, N-body 3..6 bodies; not the time-dependent
-                                   kind, whose sin(t) is not correctly rounded, nor the ragged
-                                   calls).  A call with no compiled kernel for the choice
+                                   counts included.  Uses the context's own tables.  The
+                                   second-order calls of the register kinds (Kepler, Henon-Heiles,
+                                   harmonic d <= 3, N-body 3..6 bodies) and the ragged calls
+                                   (N-body up to 128 bodies, FPUT, harmonic; d <= 1536, every
+                                   team size giving the same bits); not the time-dependent kind,
+                                   whose sin(t) is not correctly rounded, nor the first-order
+                                   calls.  A call with no compiled kernel for the choice
                                    returns IRKGL_ERR_UNSUPPORTED */
   IRKGL_OPT_TILE_LAYOUT = 10,   /* second-order kinds: 1 = the stage-split tiles (LPT lanes per
                                    trajectory share the stages); 2 = the component-split tile for

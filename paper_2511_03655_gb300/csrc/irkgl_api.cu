@@ -18,6 +18,7 @@
 #include "irkgl_kernels.h"
 #include "irkgl_split.cuh"
 #include "irkgl_wide.cuh"
+#include "irkgl_wide_repro.cuh"
 #include "irkgl_tables.h"
 
 using irkgl::Coef;
@@ -807,10 +808,47 @@ int irkgl_integrate(irkgl_ctx* c, const double* q0, const double* v0, int batch,
   return run(c, a, static_cast<cudaStream_t>(stream));
 }
 
+// The reproducible wide kernel: the same team-shape rule as run_wide.
+static int run_wide_repro(irkgl_ctx* c, irkgl::WideArgs& a, int ninst, int dmax, cudaStream_t st) {
+  const irkgl::WideReproShape* shapes = nullptr;
+  const int ns = irkgl::wide_repro_shapes(&shapes);
+  const irkgl::WideReproShape* ws = nullptr;
+  const int want_team = c->wide_team ? c->wide_team : 256;
+  size_t smem = 0;
+  for (int i = 0; i < ns && !ws; i++) {
+    const irkgl::WideReproShape& x = shapes[i];
+    if (x.team * x.slots < dmax || x.team != want_team) continue;
+    const size_t need_smem = irkgl::wide_repro_smem_bytes(x.block / x.team, dmax);
+    if (need_smem > 227 * 1024) continue;
+    ws = &x;
+    smem = need_smem;
+  }
+  if (!ws) return IRKGL_ERR_UNSUPPORTED;
+  const int teams = ws->block / ws->team;
+  IRKGL_CUDA(cudaFuncSetAttribute(ws->fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  static_cast<int>(smem)));
+  int per_sm = 0;
+  IRKGL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ws->fn, ws->block, smem));
+  if (per_sm < 1) return IRKGL_ERR_UNSUPPORTED;
+  int grid = c->grid_blocks > 0 ? c->grid_blocks : per_sm * c->sm_count;
+  const int need = (ninst + teams - 1) / teams;
+  if (grid > need) grid = need;
+  a.ninst = ninst;
+  a.kmax = c->kmax;
+  a.dmax = dmax;
+  a.counter = c->d_counter;
+  a.monitor_local = c->monitor_local;
+  IRKGL_CUDA(cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned), st));
+  ws->launch(dim3(grid), dim3(ws->block), smem, st, a, c->coefr);
+  IRKGL_CUDA(cudaGetLastError());
+  return IRKGL_OK;
+}
+
 static int run_wide(irkgl_ctx* c, irkgl::WideArgs& a, int ninst, int dmax, cudaStream_t st) {
   static_assert(sizeof(irkgl_instance) == sizeof(irkgl::WideInstance), "instance layout");
   if (dmax < 1) return IRKGL_ERR_INVALID;
   if (dmax > 1536) return IRKGL_ERR_UNSUPPORTED;
+  if (c->mix == 2) return run_wide_repro(c, a, ninst, dmax, st);
   if (c->mix && !c->default_tables) return IRKGL_ERR_UNSUPPORTED;  // fixed point: built-in tables
   // team shape: the requested team size, else 256-thread teams (the
   // right-hand side runs team-parallel over (stage, body or particle), and

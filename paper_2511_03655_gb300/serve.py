@@ -117,10 +117,17 @@ FP64_MIX_FASTER = {"nbody"}
 def new_context(kind: str, params, dim: int, h: float, mix: int) -> int:
     """A context for the register kernel of (kind, dim): with the fixed-point
     stage mixing when mix = 1, a kernel with it is compiled and it is the
-    faster form, else with the FP64 mixing. The choice depends only on
-    (kind, dim, mix), so the server and run_plain integrate a request with
-    the same kernel."""
+    faster form, else with the FP64 mixing; mix = 2 is the reproducible form,
+    which every register (kind, dim) has (an error otherwise, never a
+    silent fallback). The choice depends only on (kind, dim, mix), so the
+    server and run_plain integrate a request with the same kernel."""
     ctx = irkgl.irkgl_create(KIND_IDS[kind], params, dim, h)
+    if mix == 2:
+        irkgl.irkgl_set_option(ctx, irkgl.OPT_MIX, 2)
+        if irkgl.irkgl_get_tile(ctx) <= 0:
+            irkgl.irkgl_destroy(ctx)
+            raise irkgl.IrkglError(f"no reproducible kernel for {kind} d={dim}")
+        return ctx
     if mix and kind not in FP64_MIX_FASTER:
         irkgl.irkgl_set_option(ctx, irkgl.OPT_MIX, 1)
         if irkgl.irkgl_get_tile(ctx) <= 0:
@@ -131,7 +138,7 @@ def new_context(kind: str, params, dim: int, h: float, mix: int) -> int:
 def new_wide_context(mix: int, team: int = 0) -> int:
     """A context for the wide kernel (the kinds come per instance)."""
     ctx = irkgl.irkgl_create(irkgl.RHS_HARMONIC, [1.0], 1, 1.0)
-    irkgl.irkgl_set_option(ctx, irkgl.OPT_MIX, 1 if mix else 0)
+    irkgl.irkgl_set_option(ctx, irkgl.OPT_MIX, mix if mix in (0, 2) else 1)
     if team:
         irkgl.irkgl_set_option(ctx, irkgl.OPT_WIDE_TEAM, team)
     return ctx
@@ -592,7 +599,9 @@ class Server:
     when the pool's first request is admitted; a pool whose largest request
     is bigger gets that size): requests wait until their pool has room.
     mix = 1 runs the fixed-point stage mixing wherever a kernel with it is
-    compiled (``new_context``).  target_tick_s is the wanted duration of a
+    compiled (``new_context``); mix = 2 runs every pool in the reproducible
+    form (each request's results are then those of any IEEE FP64 program of
+    the method's plain sequence).  target_tick_s is the wanted duration of a
     tick: each pool sizes its steps per tick from the time per step of its
     previous tick."""
 
@@ -601,7 +610,9 @@ class Server:
         if policy not in ("fifo", "sjf"):
             raise ValueError(policy)
         self.policy = policy
-        self.mix = 1 if mix else 0
+        if mix not in (0, 1, 2):
+            raise ValueError(f"mix {mix}: 0, 1 or 2")
+        self.mix = mix
         self.pool_bytes = int(pool_bytes)
         self.device = device or torch.device("cuda")
         self.max_active = max_active

@@ -224,3 +224,107 @@ def test_full_ensemble_sampled(env):
     assert np.array_equal(out.status.cpu().numpy()[idx], o["status"])
     assert (out.status.cpu().numpy() == 0).all()
     integ.close()
+
+
+def ragged_oracle(w, k, nsteps=None):
+    o, d = int(w["offset"][k]), int(w["dim"][k])
+    po, pn = int(w["param_offset"][k]), int(w["nparams"][k])
+    kind = {2: cbind.NBODY, 3: cbind.FPUT, 5: cbind.HARMONIC}[int(w["kind"][k])]
+    n = int(w["nsteps"][k]) if nsteps is None else int(nsteps)
+    return cbind.run(kind, w["params"][po:po + pn], w["q0"][o:o + d], w["v0"][o:o + d], w["h"][k], n)
+
+
+def ragged_run(torch, irkgl, w, team=0):
+    n = len(w["kind"])
+    integ = irkgl.Integrator(irkgl.RHS_HARMONIC, [1.0], 1, 0.1, mix=2)  # tables and options
+    integ.set(irkgl.OPT_WIDE_TEAM, team)
+    out = irkgl.RaggedOutputs.allocate(len(w["q0"]), n)
+    irkgl.irkgl_integrate_ragged(integ.ctx, irkgl.instances_tensor(w, "cuda"), n, int(w["dim"].max()),
+                                 torch.tensor(w["params"], device="cuda"),
+                                 torch.tensor(w["q0"], device="cuda"), torch.tensor(w["v0"], device="cuda"),
+                                 out)
+    torch.cuda.synchronize()
+    integ.close()
+    return {k: getattr(out, k).cpu().numpy() for k in ("q", "v", "q_lo", "v_lo", "r_prev", "dH_max",
+                                                       "iters", "steps", "status")}
+
+
+def check_ragged_instance(g, w, k, o):
+    off, d = int(w["offset"][k]), int(w["dim"][k])
+    for key in ("q", "v", "q_lo", "v_lo"):
+        assert same(g[key][off:off + d], o[key][0]), (k, key)
+    assert same(g["r_prev"][8 * off:8 * (off + d)], o["r_prev"][0].ravel()), (k, "r_prev")
+    assert same(g["dH_max"][k:k + 1], o["dH_max"]), (k, "dH_max")
+    assert g["iters"][k] == o["iters_total"][0] and g["status"][k] == o["status"][0]
+    assert g["steps"][k] == o["steps"][0]
+
+
+def test_ragged_bitwise_every_team_size(env):
+    """Small N-body systems and FPUT chains in one ragged launch: every team
+    size (32 to 256 threads) returns the same bits, the oracle's."""
+    torch, irkgl = env
+    w = workloads.uneven_batch(ninst=16, steps=150, nmax_body=20, nmax_chain=60)
+    runs = {team: ragged_run(torch, irkgl, w, team) for team in (32, 64, 128, 256)}
+    for k in range(len(w["kind"])):
+        check_ragged_instance(runs[32], w, k, ragged_oracle(w, k))
+    for team in (64, 128, 256):
+        for key in runs[32]:
+            assert same(runs[team][key], runs[32][key]), (team, key)
+
+
+def test_ragged_bitwise_largest_sizes_and_continuation(env):
+    """N-body systems up to 64 bodies and FPUT chains up to 1,536 particles
+    (the wide kernel's largest shape), in one launch and as two
+    irkgl_advance_ragged calls (H0, sweep totals and dH_max carried): the
+    oracle's bits both ways."""
+    torch, irkgl = env
+    w = workloads.uneven_batch(ninst=10, steps=60, nmax_body=64, nmax_chain=1536)
+    n = len(w["kind"])
+    g = ragged_run(torch, irkgl, w)
+    refs = [ragged_oracle(w, k) for k in range(n)]
+    for k in range(n):
+        check_ragged_instance(g, w, k, refs[k])
+    f = dict(dtype=torch.float64, device="cuda")
+    integ = irkgl.Integrator(irkgl.RHS_HARMONIC, [1.0], 1, 0.1, mix=2)
+    inst = irkgl.instances_tensor(w, "cuda")
+    q, v = torch.tensor(w["q0"], **f), torch.tensor(w["v0"], **f)
+    ql, vl = torch.zeros_like(q), torch.zeros_like(v)
+    rp = torch.zeros(8 * len(w["q0"]), **f)
+    H0, dH = torch.zeros(n, **f), torch.zeros(n, **f)
+    it = torch.zeros(n, dtype=torch.int64, device="cuda")
+    st = torch.zeros(n, dtype=torch.int32, device="cuda")
+    par = torch.tensor(w["params"], **f)
+    first = np.full(n, 25, dtype=np.int64)
+    for c, k in enumerate((first, w["nsteps"] - first)):
+        irkgl.irkgl_advance_ragged(integ.ctx, inst, n, int(w["dim"].max()), par, q, v, ql, vl, rp,
+                                   torch.tensor(k, device="cuda"), H0=H0, h0_init=(c == 0), dH_max=dH,
+                                   iters=it, status=st)
+    torch.cuda.synchronize()
+    cont = {"q": q.cpu().numpy(), "v": v.cpu().numpy(), "q_lo": ql.cpu().numpy(), "v_lo": vl.cpu().numpy(),
+            "r_prev": rp.cpu().numpy(), "dH_max": dH.cpu().numpy(), "iters": it.cpu().numpy(),
+            "steps": w["nsteps"].copy(), "status": st.cpu().numpy()}
+    for k in range(n):
+        check_ragged_instance(cont, w, k, refs[k])
+    integ.close()
+
+
+def test_served_requests_bitwise(env):
+    """The continuous-batching server in the reproducible form: requests of
+    every family, served in shared register and wide pools over many ticks,
+    each return the oracle's bits for that request run alone."""
+    torch, irkgl = env
+    import copy
+
+    from paper_2511_03655_gb300 import serve
+    descs = workloads.serving_requests(n=14, rate=4000.0, batch_max=48, horizon_max=300, nb_max=12,
+                                       n_max=96)
+    reqs = serve.make_requests(copy.deepcopy(descs))
+    st = serve.Server(target_tick_s=0.001, mix=2).run(reqs)
+    assert st.max_concurrent > 1
+    kinds = {"kepler": cbind.KEPLER, "nbody": cbind.NBODY, "fput": cbind.FPUT,
+             "henon_heiles": cbind.HENON_HEILES, "harmonic": cbind.HARMONIC}
+    for r in reqs:
+        o = cbind.run(kinds[r.kind], r.params, r.q0, r.v0, r.h, r.nsteps, nthreads=8)
+        assert same(r.q, o["q"]) and same(r.v, o["v"]), r.kind
+        assert same(r.dH_max, o["dH_max"]), r.kind
+        assert np.array_equal(r.iters, o["iters_total"]) and np.array_equal(r.status, o["status"])
