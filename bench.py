@@ -70,13 +70,13 @@ FP64_INST_PER_STEP, FP64_INST_PER_SWEEP = 400, 352
 # warp instruction per 16 SM cycles, 2 DFMA lanes per clock) times the
 # elapsed SM cycles.
 NCU_ISSUE = {  # (mixing, tile layout): (warp inst per traj-step, FP64 warp inst per traj-step, kernel_sha)
-    (1, "component split"): (6693960891 / 16064548, 0.59062109 * 0.0625 * 4782353724 / 16064548,
-                             "46fc8f73dbb82f65"),
+    (1, "component split"): (6693990408 / 16064548, 0.59552777 * 0.0625 * 4742016216 / 16064548,
+                             "2d7230f64dddcbca"),
 }
 NCU_TRAFFIC_BYTES_PER_LAUNCH = {  # (mixing, tile layout): (bytes per launch, kernel_sha at capture)
     (0, "stage split"): (4389888 + 68864, "68265a9b374b87ca"),
     (1, "stage split"): (4640000 + 595968, "68265a9b374b87ca"),
-    (1, "component split"): (3622656 + 132096, "46fc8f73dbb82f65"),
+    (1, "component split"): (3621632 + 131328, "2d7230f64dddcbca"),
 }
 
 
