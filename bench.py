@@ -209,6 +209,80 @@ def sweep_histogram(torch, irkgl, kind_g, kind_o, params, q0, v0, h, nsteps, cor
     return _hist_summary(diff, kg_hist, ko_hist, B * nsteps, worst)
 
 
+def sweep_repro(torch, irkgl, kind_g, kind_o, params, q0, v0, h, nsteps, cores, chunk=500):
+    """The reproducible form (mix = 2) against the oracle over a long run:
+    both sides carry their own state, and after every chunk of steps the
+    sweep count of every step and the whole state (hi, lo, R_prev) are
+    compared.  The two states are expected to stay bit-identical, so no
+    state is handed over."""
+    from oracle import cbind
+    B, d = q0.shape
+    f = dict(dtype=torch.float64, device="cuda")
+    q, v = torch.tensor(q0, **f), torch.tensor(v0, **f)
+    ql, vl = torch.zeros_like(q), torch.zeros_like(v)
+    rp = torch.zeros((B, 8, d), **f)
+    st = torch.zeros(B, dtype=torch.int32, device="cuda")
+    hs = np.broadcast_to(np.asarray(h, dtype=np.float64), (B,)).copy()
+    hh = torch.tensor(hs, **f)
+    integ = irkgl.Integrator(kind_g, params, d, float(hs[0]), mix=2)
+    o = {"q": np.array(q0, dtype=np.float64), "v": np.array(v0, dtype=np.float64),
+         "q_lo": np.zeros((B, d)), "v_lo": np.zeros((B, d)), "r_prev": np.zeros((B, 8, d))}
+    diff, kg_hist, ko_hist = {}, {}, {}
+    states_equal, done = True, 0
+    while done < nsteps:
+        c = min(chunk, nsteps - done)
+        it = torch.zeros((B, c), dtype=torch.int32, device="cuda")
+        integ.step(q, v, ql, vl, rp, h=hh, nsteps=c, iters=it, status=st)
+        o = cbind.run(kind_o, params, o["q"], o["v"], hs, c, q_lo=o["q_lo"], v_lo=o["v_lo"],
+                      r_prev=o["r_prev"], iters_len=c, nthreads=cores)
+        kg = it.cpu().numpy().astype(np.int64)
+        ko = o["iters"].astype(np.int64)
+        for hist, vals in ((diff, (kg - ko).ravel()), (kg_hist, kg.ravel()), (ko_hist, ko.ravel())):
+            _hist_add(hist, vals)
+        for t, key in ((q, "q"), (v, "v"), (ql, "q_lo"), (vl, "v_lo"), (rp, "r_prev")):
+            states_equal = states_equal and np.array_equal(t.cpu().numpy().view(np.uint8),
+                                                           np.ascontiguousarray(o[key]).view(np.uint8))
+        done += c
+    integ.close()
+    out = _hist_summary(diff, kg_hist, ko_hist, B * nsteps, [])
+    out["states_bit_identical_after_every_chunk"] = bool(states_equal)
+    out["status_equal"] = bool(np.array_equal(st.cpu().numpy(), o["status"]))
+    out["chunk_steps"] = chunk
+    return out
+
+
+def sweep_repro_ragged(torch, irkgl, w, cores):
+    """The reproducible wide kernel against the oracle run per instance:
+    sweep totals, status and the final state (hi, lo, R_prev) bit for bit."""
+    from oracle import cbind
+    n = len(w["kind"])
+    integ = irkgl.Integrator(irkgl.RHS_HARMONIC, [1.0], 1, 0.1, mix=2)
+    out = irkgl.RaggedOutputs.allocate(len(w["q0"]), n)
+    irkgl.irkgl_integrate_ragged(integ.ctx, irkgl.instances_tensor(w, "cuda"), n, int(w["dim"].max()),
+                                 torch.tensor(w["params"], device="cuda"), torch.tensor(w["q0"], device="cuda"),
+                                 torch.tensor(w["v0"], device="cuda"), out)
+    torch.cuda.synchronize()
+    integ.close()
+    g = {k: getattr(out, k).cpu().numpy() for k in ("q", "v", "q_lo", "v_lo", "r_prev", "iters", "status")}
+    same_state, same_iters = 0, 0
+    for k in range(n):
+        o_, d = int(w["offset"][k]), int(w["dim"][k])
+        po, pn = int(w["param_offset"][k]), int(w["nparams"][k])
+        kind = {2: cbind.NBODY, 3: cbind.FPUT, 5: cbind.HARMONIC}[int(w["kind"][k])]
+        r = cbind.run(kind, w["params"][po:po + pn], w["q0"][o_:o_ + d], w["v0"][o_:o_ + d], w["h"][k],
+                      int(w["nsteps"][k]))
+        eq = all(np.array_equal(g[key][o_:o_ + d].view(np.uint8), np.ascontiguousarray(r[key][0]).view(np.uint8))
+                 for key in ("q", "v", "q_lo", "v_lo"))
+        if g["status"][k] == 0:  # R_prev is written for trajectories that completed their steps
+            eq = eq and np.array_equal(g["r_prev"][8 * o_:8 * (o_ + d)].view(np.uint8),
+                                       np.ascontiguousarray(r["r_prev"][0]).ravel().view(np.uint8))
+        same_state += int(eq)
+        same_iters += int(g["iters"][k] == r["iters_total"][0] and g["status"][k] == r["status"][0])
+    return {"instances": n, "traj_steps": int(w["nsteps"].sum()), "state_bit_identical": same_state,
+            "sweep_totals_and_status_equal": same_iters, "failed_on_both_sides": int((g["status"] != 0).sum()),
+            "note": "state = q, v and their compensation parts, and R_prev where the instance completed"}
+
+
 def _hist_add(hist, vals):
     u, c = np.unique(vals, return_counts=True)
     for a, b in zip(u.tolist(), c.tolist()):
@@ -366,6 +440,18 @@ def run_sweeps(args):
     wr = workloads.uneven_batch(ninst=128, steps=200, step_table=tuned["step_table"] if tuned else None)
     for mix in (1, 0):
         case(f"ragged_wide_mix{mix}", sweep_histogram_ragged, torch, irkgl, wr, 200, 256, mix)
+    # the reproducible form: long runs, no state handed over, sweep counts of
+    # every step and the whole state compared after every chunk
+    case("kepler_ensemble_mix2", sweep_repro, torch, irkgl, irkgl.RHS_KEPLER, cbind.KEPLER, [1.0],
+         kw["q0"], kw["v0"], kw["h"], n, cores)
+    case("henon_heiles_orbit_mix2", sweep_repro, torch, irkgl, irkgl.RHS_HENON_HEILES, cbind.HENON_HEILES,
+         [1.0], q0, v0, 1.0, nhh, cores, chunk=nhh)
+    hq, hv, _ = workloads.henon_heiles_ensemble(4096)
+    case("henon_heiles_ensemble_mix2", sweep_repro, torch, irkgl, irkgl.RHS_HENON_HEILES,
+         cbind.HENON_HEILES, [1.0], hq, hv, 0.7, n, cores)
+    case("nbody6_ensemble_mix2", sweep_repro, torch, irkgl, irkgl.RHS_NBODY, cbind.NBODY, nb["params"],
+         nb["q0"], nb["v0"], nb["h"], n, cores)
+    case("ragged_wide_mix2", sweep_repro_ragged, torch, irkgl, wr, cores)
     y0 = workloads.schwarzschild_ensemble(8192)
     par = list(workloads.SBH_PARAMS)
     for hsb in (4.0, 16.0):
@@ -384,7 +470,9 @@ def run_sweeps(args):
                                    f"components h = 0.4 x {n} steps; ragged batch 128 instances "
                                    "(wide kernel, step table) x 200 steps; Schwarzschild 8,192 "
                                    "orbits x 500 steps at h = 4 and 16, and with s = 2, 4, 6 "
-                                   "stages at h = 0.5, 2, 2"},
+                                   "stages at h = 0.5, 2, 2; the reproducible form (mix2 cases): "
+                                   "the Kepler, Henon-Heiles, 6-body and ragged workloads as long "
+                                   "runs with no state handed over, compared after every chunk"},
             "cases": rows}
     print(json.dumps(line))
     return 0
