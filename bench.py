@@ -134,9 +134,9 @@ MIXING = {0: "FP64 FMA chain", 1: "fixed-point (integer pipes)",
 SUBLINES = {
     "nbody6": ["--workload", "nbody6", "--batch", "16384", "--traj-steps", "1000", "--steps", "2",
                "--warmup", "1", "--skip-extras"],
-    "uneven": ["--workload", "uneven", "--ninst", "1024", "--traj-steps", "1000", "--steps", "2",
+    "uneven": ["--workload", "uneven", "--ninst", "4096", "--traj-steps", "1000", "--steps", "2",
                "--warmup", "1", "--skip-extras"],
-    "schwarzschild": ["--workload", "schwarzschild", "--batch", "16384", "--steps", "2", "--warmup",
+    "schwarzschild": ["--workload", "schwarzschild", "--batch", "65536", "--steps", "2", "--warmup",
                       "1", "--skip-extras"],
     "kepler_reproducible": ["--workload", "kepler", "--mix", "2", "--periods", "10", "--steps", "2",
                             "--warmup", "1", "--skip-extras"],
