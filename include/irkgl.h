@@ -164,10 +164,12 @@ enum {
                                    second-order calls of the register kinds (Kepler, Henon-Heiles,
                                    harmonic d <= 3, N-body 3..6 bodies) and the ragged calls
                                    (N-body up to 128 bodies, FPUT, harmonic; d <= 1536, every
-                                   team size giving the same bits); not the time-dependent kind,
-                                   whose sin(t) is not correctly rounded, nor the first-order
-                                   calls.  A call with no compiled kernel for the choice
-                                   returns IRKGL_ERR_UNSUPPORTED */
+                                   team size giving the same bits), and the first-order calls of
+                                   IRKGL_RHS_HARMONIC1 for every IRKGL_OPT_STAGES; not the
+                                   kinds whose sin and cos are not correctly rounded (the
+                                   time-dependent kind, Schwarzschild).  A call with no
+                                   compiled kernel for the choice returns
+                                   IRKGL_ERR_UNSUPPORTED */
   IRKGL_OPT_TILE_LAYOUT = 10,   /* second-order kinds: 1 = the stage-split tiles (LPT lanes per
                                    trajectory share the stages); 2 = the component-split tile for
                                    d = 2 (Kepler, Henon-Heiles): two lanes per trajectory, each

@@ -16,6 +16,7 @@
 #include "irkgl.h"
 #include "irkgl_first_order.cuh"
 #include "irkgl_kernels.h"
+#include "irkgl_repro1.cuh"
 #include "irkgl_split.cuh"
 #include "irkgl_wide.cuh"
 #include "irkgl_wide_repro.cuh"
@@ -74,6 +75,13 @@ const irkgl::KernelEntry1* find_kernel1(int kind, int dim, int lpt, int block, i
         e.layout == layout)
       return &e;
   }
+  return nullptr;
+}
+
+const irkgl::KernelEntry1* find_repro1(int kind, int dim, int nst) {
+  const irkgl::KernelTable1 t = irkgl::kernels_first_order_repro();
+  for (int i = 0; i < t.count; i++)
+    if (t.entries[i].kind == kind && t.entries[i].dim == dim && t.entries[i].nst == nst) return &t.entries[i];
   return nullptr;
 }
 
@@ -394,8 +402,8 @@ static void resolve_tile1(const irkgl_ctx* c, int* lpt, int* layout) {
 int irkgl_get_layout(irkgl_ctx* c) {
   if (!c) return IRKGL_ERR_INVALID;
   int lpt = 0, layout = 0;
+  if (c->mix == 2) return 3;  // the reproducible form: one thread per trajectory
   if (first_order_kind(c->kind)) resolve_tile1(c, &lpt, &layout);
-  else if (c->mix == 2) return 3;  // the reproducible form: one thread per trajectory
   else resolve_tile(c, &lpt, &layout);
   return layout ? 2 : 1;
 }
@@ -403,6 +411,7 @@ int irkgl_get_layout(irkgl_ctx* c) {
 int irkgl_get_tile(irkgl_ctx* c) {
   if (!c) return IRKGL_ERR_INVALID;
   if (first_order_kind(c->kind)) {
+    if (c->mix == 2) return find_repro1(c->kind, c->dim, c->stages) ? 1 : 0;
     int lpt = 0, layout = 0;
     resolve_tile1(c, &lpt, &layout);
     return find_kernel1(c->kind, c->dim, lpt, c->block, c->stages, c->mix, layout) ? lpt : 0;
@@ -640,11 +649,18 @@ int irkgl_advance_t(irkgl_ctx* c, double* q, double* v, double* q_lo, double* v_
 
 static int run1(irkgl_ctx* c, KArgs1& a, cudaStream_t st) {
   if (!first_order_kind(c->kind)) return IRKGL_ERR_INVALID;
-  if (c->mix && !c->default_tables) return IRKGL_ERR_UNSUPPORTED;  // fixed point: built-in tables
+  if (c->mix == 1 && !c->default_tables) return IRKGL_ERR_UNSUPPORTED;  // fixed point: built-in tables
   int lpt = 0, layout = 0;
-  resolve_tile1(c, &lpt, &layout);
-  const irkgl::KernelEntry1* ke =
-      lpt ? find_kernel1(c->kind, c->dim, lpt, c->block, c->stages, c->mix, layout) : nullptr;
+  int block = c->block;
+  const irkgl::KernelEntry1* ke = nullptr;
+  if (c->mix == 2) {  // the reproducible form: one thread per trajectory
+    ke = find_repro1(c->kind, c->dim, c->stages);
+    lpt = 1;
+    if (ke) block = ke->block;  // its one compiled block size
+  } else {
+    resolve_tile1(c, &lpt, &layout);
+    ke = lpt ? find_kernel1(c->kind, c->dim, lpt, c->block, c->stages, c->mix, layout) : nullptr;
+  }
   if (!ke) return IRKGL_ERR_UNSUPPORTED;
   Coef1 small;
   if (c->stages != 8 && !small_stage_tables(c->stages, &small)) return IRKGL_ERR_UNSUPPORTED;
@@ -653,19 +669,19 @@ static int run1(irkgl_ctx* c, KArgs1& a, cudaStream_t st) {
   a.kmax = c->kmax;
   a.monitor = c->monitor;
   a.monitor_local = c->monitor_local;
-  const int traj_per_block = c->block / lpt;
+  const int traj_per_block = block / lpt;
   const long long need = (static_cast<long long>(a.batch) + traj_per_block - 1) / traj_per_block;
   int grid = c->grid_blocks;
   if (grid <= 0) {
     int per_sm = 0;
-    IRKGL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ke->fn, c->block, 0));
+    IRKGL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ke->fn, block, 0));
     if (per_sm < 1) per_sm = 1;
     grid = per_sm * c->sm_count;
   }
   if (grid > need) grid = static_cast<int>(need);
   if (grid < 1) grid = 1;
   IRKGL_CUDA(cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned), st));
-  ke->launch(dim3(grid), dim3(c->block), st, a, c->stages == 8 ? c->coef1 : small);
+  ke->launch(dim3(grid), dim3(block), st, a, c->stages == 8 ? c->coef1 : small);
   IRKGL_CUDA(cudaGetLastError());
   return IRKGL_OK;
 }

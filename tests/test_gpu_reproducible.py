@@ -328,3 +328,38 @@ def test_served_requests_bitwise(env):
         assert same(r.q, o["q"]) and same(r.v, o["v"]), r.kind
         assert same(r.dH_max, o["dH_max"]), r.kind
         assert np.array_equal(r.iters, o["iters_total"]) and np.array_equal(r.status, o["status"])
+
+
+@pytest.mark.parametrize("stages", [8, 6, 4, 2])
+def test_first_order_bitwise(env, stages):
+    """The first-order form (Eq. Yi2) in the reproducible form, for every
+    s-stage scheme: irkgl_integrate1 and two irkgl_advance1 calls give the
+    oracle's bits (y, y_lo, L_prev, dH_max, sweep totals, status)."""
+    torch, irkgl = env
+    rng = np.random.default_rng(21 + stages)
+    y0 = rng.uniform(-1.0, 1.0, (256, 2))
+    h = {8: 0.6, 6: 0.45, 4: 0.25, 2: 0.05}[stages]
+    ns = 300
+    integ = irkgl.Integrator(irkgl.RHS_HARMONIC1, [1.3], 2, h, mix=2, stages=stages)
+    assert integ.layout == "reproducible" and integ.tile == 1
+    out = integ.integrate1(torch.tensor(y0, device="cuda"), nsteps_all=ns)
+    torch.cuda.synchronize()
+    o = cbind.run1(cbind.HARMONIC1, [1.3], y0, h, ns, stages=stages)
+    for key in ("y", "y_lo", "l_prev", "dH_max"):
+        assert same(getattr(out, key).cpu().numpy(), o[key]), key
+    assert np.array_equal(out.iters.cpu().numpy(), o["iters_total"])
+    assert np.array_equal(out.status.cpu().numpy(), o["status"]) and (o["status"] == 0).all()
+    f = dict(dtype=torch.float64, device="cuda")
+    y, ylo = torch.tensor(y0, **f), torch.zeros((256, 2), **f)
+    lp = torch.zeros((256, stages, 2), **f)
+    H0, dH = torch.zeros(256, **f), torch.zeros(256, **f)
+    it = torch.zeros(256, dtype=torch.int64, device="cuda")
+    st = torch.zeros(256, dtype=torch.int32, device="cuda")
+    for c, k in enumerate((120, ns - 120)):
+        integ.advance1(y, ylo, lp, torch.full((256,), k, dtype=torch.int64, device="cuda"),
+                       h=torch.full((256,), h, **f), H0=H0, h0_init=(c == 0), dH_max=dH, iters=it, status=st)
+    torch.cuda.synchronize()
+    for a, key in ((y, "y"), (ylo, "y_lo"), (lp, "l_prev"), (dH, "dH_max")):
+        assert same(a.cpu().numpy(), o[key]), ("advance1", key)
+    assert np.array_equal(it.cpu().numpy(), o["iters_total"])
+    integ.close()
