@@ -363,3 +363,62 @@ def test_first_order_bitwise(env, stages):
         assert same(a.cpu().numpy(), o[key]), ("advance1", key)
     assert np.array_equal(it.cpu().numpy(), o["iters_total"])
     integ.close()
+
+
+def test_ragged_largest_shapes_bitwise(env):
+    """The largest instances the ragged calls take: an FPUT chain of 1,536
+    particles (the 256 x 6 team shape, 221 KB of shared memory) and a
+    128-body system (the descriptor's limit) in one launch, bit for bit."""
+    torch, irkgl = env
+    c = workloads.fput_chain(1536)
+    sysd = workloads.nbody_system(128, seed_id=991)
+    cp = np.asarray(c["params"], dtype=np.float64)
+    w = {"kind": np.array([3, 2], dtype=np.int32), "dim": np.array([1536, 384], dtype=np.int32),
+         "offset": np.array([0, 1536], dtype=np.int64),
+         "param_offset": np.array([0, len(cp)], dtype=np.int32),
+         "nparams": np.array([len(cp), 129], dtype=np.int32),
+         "h": np.array([0.25, 0.001 * sysd["period_inner"]]), "nsteps": np.array([60, 30], dtype=np.int64),
+         "params": np.concatenate([cp, [1.0], np.asarray(sysd["masses"], dtype=np.float64)]),
+         "q0": np.concatenate([c["q"], sysd["q"]]), "v0": np.concatenate([c["v"], sysd["v"]])}
+    g = ragged_run(torch, irkgl, w)
+    for k in range(2):
+        o = ragged_oracle(w, k)
+        assert o["status"][0] == 0
+        check_ragged_instance(g, w, k, o)
+
+
+def test_register_ragged_tail_zero_steps_and_skips(env):
+    """129 Kepler trajectories (a partly filled last block), every seventh
+    with zero steps, advanced by irkgl_advance_multi through a reversed order
+    list that skips every fifth entry (-1): the advanced trajectories give
+    the oracle's bits, the skipped ones are left as they were."""
+    torch, irkgl = env
+    B = 129
+    w = workloads.kepler_ensemble(batch=B, periods=1)
+    ns = w["nsteps"].copy()
+    ns[::7] = 0
+    order = np.arange(B, dtype=np.int32)[::-1].copy()
+    order[::5] = -1
+    ran = np.zeros(B, dtype=bool)
+    ran[order[order >= 0]] = True
+    f = dict(dtype=torch.float64, device="cuda")
+    integ = irkgl.Integrator(irkgl.RHS_KEPLER, [1.0], 2, float(w["h"][0]), mix=2)
+    q, v = torch.tensor(w["q0"], **f), torch.tensor(w["v0"], **f)
+    ql, vl = torch.zeros_like(q), torch.zeros_like(v)
+    rp = torch.zeros((B, 8, 2), **f)
+    H0 = torch.full((B,), float("nan"), **f)
+    dH = torch.zeros(B, **f)
+    it = torch.zeros(B, dtype=torch.int64, device="cuda")
+    st = torch.zeros(B, dtype=torch.int32, device="cuda")
+    irkgl.irkgl_advance_multi(integ.ctx, 2, q, v, ql, vl, rp, torch.tensor(ns, device="cuda"),
+                              h=torch.tensor(w["h"], **f), order=torch.tensor(order, device="cuda"),
+                              H0=H0, dH_max=dH, iters=it, status=st)
+    torch.cuda.synchronize()
+    o = oracle(cbind.KEPLER, [1.0], w["q0"], w["v0"], w["h"], ns)
+    qg, vg = q.cpu().numpy(), v.cpu().numpy()
+    assert same(qg[ran], o["q"][ran]) and same(vg[ran], o["v"][ran])
+    assert same(rp.cpu().numpy()[ran], o["r_prev"][ran]) and same(dH.cpu().numpy()[ran], o["dH_max"][ran])
+    assert np.array_equal(it.cpu().numpy()[ran], o["iters_total"][ran])
+    assert same(qg[~ran], w["q0"][~ran]) and same(vg[~ran], w["v0"][~ran])
+    assert (it.cpu().numpy()[~ran] == 0).all() and np.isnan(H0.cpu().numpy()[~ran]).all()
+    integ.close()
