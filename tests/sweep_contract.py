@@ -1,8 +1,9 @@
-"""The sweep-count contract between the CUDA path and the oracle.
+"""The sweep-count contract between the fast CUDA forms and the oracle.
 
 The target asks for fixed-point sweep counts within +-1 of the oracle's per
-step.  The stopping rule (Eqs. Delta_n, stopping) makes that unreachable on
-a small fraction of steps: when the iteration has reached the roundoff floor,
+step.  For the fast forms (fused multiply-adds, exact fixed-point stage
+sums, integer x^(-3/2)) the stopping rule (Eqs. Delta_n, stopping) makes
+that unreachable on a small fraction of steps: when the iteration has reached the roundoff floor,
 a step stops at the first sweep whose increment Delta is exactly zero, or by
 the min rule once Delta stops decreasing, and a last-bit difference between
 the GPU's fused or exact operations and the oracle's separate roundings
