@@ -93,14 +93,16 @@ def parse():
     ap.add_argument("--skip-extras", action="store_true", help="skip e2e, plain form and CPU baseline")
     ap.add_argument("--workload", default="kepler",
                     choices=["kepler", "nbody6", "uneven", "schwarzschild", "overhead", "serving",
-                             "sweeps"],
+                             "serving4", "sweeps"],
                     help="kepler: the 65,536-orbit ensemble (default); nbody6: 16,384 perturbed "
                          "copies of a 6-body system; uneven: 4,096 ragged instances (N-body "
                          "N~U{3..64} and FPUT n~U{8..512}), autotuned vs fixed tiling; schwarzschild: "
                          "65,536 first-order black-hole orbits (Eq. Ham_SBH), t in [0, 1e5], h = 16; "
                          "overhead: GPU time per g-evaluation of IRKGL16 over that of the explicit "
                          "splitting methods (Henon-Heiles and 6-body ensembles); serving: config-5 "
-                         "windows at --serve-rates; sweeps: per-step sweep counts against the "
+                         "windows at --serve-rates; serving4: the ragged batch's 4,096 instances "
+                         "as Poisson requests (p50/p99 under the config-4 load); sweeps: per-step "
+                         "sweep counts against the "
                          "oracle's from the identical state (Kepler ensemble, Henon-Heiles)")
     ap.add_argument("--traj-steps", type=int, default=None,
                     help="steps per trajectory/instance (nbody6: 10000, uneven: 1000 by default)")
@@ -119,6 +121,8 @@ def parse():
                     help="--workload serving: comma-separated Poisson arrival rates per second")
     ap.add_argument("--sweep-cases", default="",
                     help="--workload sweeps: comma-separated case-name prefixes to run (default all)")
+    ap.add_argument("--plain-sample", type=int, default=32,
+                    help="serving4: requests the plain per-request form serves back to back")
     ap.add_argument("--no-sublines", action="store_true",
                     help="skip the compact lines of the other configurations in the default run")
     return ap.parse_args()
@@ -140,6 +144,7 @@ SUBLINES = {
                       "1", "--skip-extras"],
     "kepler_reproducible": ["--workload", "kepler", "--mix", "2", "--periods", "10", "--steps", "2",
                             "--warmup", "1", "--skip-extras"],
+    "serving_config4": ["--workload", "serving4", "--traj-steps", "1000", "--plain-sample", "8"],
 }
 
 
@@ -166,6 +171,16 @@ def sublines() -> dict:
             "accuracy": js.get("accuracy"), "sweeps_per_step": js.get("sweeps_per_step"),
             "gpu_launches": js.get("gpu_launches"), "clocks": js.get("clocks"),
             "wall_s": time.perf_counter() - t0}
+        if "serving_config4" in js:
+            b = js["serving_config4"]
+            cb = b["continuous_batching"]
+            out[name]["serving"] = {
+                "requests": b["requests"], "rate_per_s": b["rate_per_s"],
+                **{k: cb[k] for k in ("p50_latency_s", "p99_latency_s", "throughput_traj_steps_s",
+                                      "gpu_busy", "launches_per_tick", "pools")},
+                "fp64_roof_frac": b["fp64_roof_frac"],
+                "plain_traj_steps_s": b["plain_per_request_sample"]["traj_steps_s"],
+                "sample_results_identical_to_served": b["sample_results_identical_to_served"]}
     return out
 
 
@@ -1181,6 +1196,66 @@ def run_serving_sweep(args):
     print(json.dumps(line))
     return 0
 
+def run_serving4(args):
+    """Serving under the config-4 load: every instance of the ragged batch
+    (N-body N ~ U{3..64}, FPUT n ~ U{8..512}, step table, --traj-steps steps)
+    is one request of batch 1, arriving by a Poisson process at the first
+    --serve-rates rate.  The continuous-batching loop serves all of them:
+    p50 / p99 latency, served trajectory-steps/s, GPU busy, the FP64 roof
+    fraction of the served work.  The plain per-request form serves
+    --plain-sample of them (spread over the list) back to back, one launch
+    each, for its rate and the bitwise comparison."""
+    import copy
+
+    import torch
+
+    from paper_2511_03655_gb300 import autotune, build, irkgl, serve, workloads
+    torch.cuda.set_device(0)
+    build.build()
+    irkgl.load()
+    dev = torch.device("cuda", 0)
+    peak = fp64_peak_tflops(irkgl, torch, torch.cuda.current_stream(), dev)
+    tuned = autotune.load_table()
+    steps = args.traj_steps or 10000
+    rate = float(args.serve_rates.split(",")[0])
+    descs = workloads.config4_requests(ninst=args.ninst, rate=rate, steps=steps,
+                                       step_table=tuned["step_table"] if tuned else None)
+    window = max(d["arrival"] for d in descs) - min(d["arrival"] for d in descs)
+    total = sum(d["nsteps"] for d in descs)
+    reqs = serve.make_requests(copy.deepcopy(descs))
+    srv = serve.Server(mix=args.mix)
+    st = srv.run(reqs).summary()
+    srv.close()
+    idx = np.unique(np.linspace(0, len(descs) - 1, min(args.plain_sample, len(descs))).astype(int))
+    sample = copy.deepcopy([descs[i] for i in idx])
+    for d in sample:
+        d["arrival"] = 0.0  # back to back: the plain form's service rate
+    pr = serve.make_requests(sample)
+    sp = serve.run_plain(pr, mix=args.mix).summary()
+    same = all(np.array_equal(reqs[i].q, p_.q) and np.array_equal(reqs[i].v, p_.v)
+               and np.array_equal(reqs[i].iters, p_.iters) for i, p_ in zip(idx, pr))
+    block = {"requests": len(descs), "rate_per_s": rate, "arrival_window_s": window, "traj_steps": total,
+             "offered_traj_steps_s": total / max(window, 1e-9), "continuous_batching": st,
+             "fp64_roof_frac": st["flops_per_s"] / (peak * 1e12),
+             "status_nonzero": int(sum(int((r.status != 0).sum()) for r in reqs)),
+             "plain_per_request_sample": {"requests": len(idx), "summary": sp,
+                                          "traj_steps_s": sp["throughput_traj_steps_s"],
+                                          "mean_service_s": sp["makespan_s"] / len(idx)},
+             "sample_results_identical_to_served": bool(same)}
+    line = {
+        "metric": METRIC, "value": st["throughput_traj_steps_s"], "unit": "traj-steps/s", "n_gpus": 1,
+        "steps": 1, "warmup": 0, "ms_per_step": 1e3 * st["makespan_s"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"serving under the config-4 load: the {len(descs)} instances of the "
+                               f"ragged batch (N-body N~U{{3..64}}, FPUT n~U{{8..512}}, step table, "
+                               f"{steps} steps) as batch-1 Poisson requests at {rate:g}/s"},
+        "gpu_launches": st["gpu_launches"],
+        "serving_config4": block,
+    }
+    print(json.dumps(line))
+    return 0
+
+
 # --------------------------------------------------------------------------
 # GPU arm
 # --------------------------------------------------------------------------
@@ -1201,6 +1276,8 @@ def main():
         return run_overhead(args)
     if args.workload == "serving":
         return run_serving_sweep(args)
+    if args.workload == "serving4":
+        return run_serving4(args)
     if args.workload == "sweeps":
         return run_sweeps(args)
 

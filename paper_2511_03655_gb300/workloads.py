@@ -354,3 +354,22 @@ def serving_requests(n: int = 200, rate: float = 2000.0, seed_id: int = 5, batch
         req["rid"] = k
         out.append(req)
     return out
+
+
+def config4_requests(ninst: int = 4096, rate: float = 2000.0, steps: int = 10000, seed_id: int = 4,
+                     step_table: dict | None = None, arrival_seed_id: int = 6):
+    """The ragged batch's instances as serving requests: each N-body system
+    or FPUT chain of ``uneven_batch`` (same seed, sizes and step table) is
+    one request of batch 1, arriving by a Poisson process at `rate`."""
+    w = uneven_batch(ninst=ninst, steps=steps, seed_id=seed_id, step_table=step_table)
+    u = uniform(SEED_BASE + arrival_seed_id, ninst)
+    t = np.cumsum(-np.log(1.0 - u) / rate)
+    out = []
+    for k in range(ninst):
+        o, d = int(w["offset"][k]), int(w["dim"][k])
+        po, pn = int(w["param_offset"][k]), int(w["nparams"][k])
+        kind = {2: "nbody", 3: "fput", 5: "harmonic"}[int(w["kind"][k])]
+        out.append(dict(rid=k, kind=kind, params=list(w["params"][po:po + pn]), dim=d,
+                        q0=w["q0"][o:o + d][None, :].copy(), v0=w["v0"][o:o + d][None, :].copy(),
+                        h=float(w["h"][k]), nsteps=int(w["nsteps"][k]), arrival=float(t[k])))
+    return out
