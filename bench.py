@@ -121,6 +121,8 @@ def parse():
                     help="--workload serving: comma-separated Poisson arrival rates per second")
     ap.add_argument("--sweep-cases", default="",
                     help="--workload sweeps: comma-separated case-name prefixes to run (default all)")
+    ap.add_argument("--serve-policy", default="fifo",
+                    help="serving4: fifo, or sjf:N (shortest job first, at most N requests active)")
     ap.add_argument("--plain-sample", type=int, default=32,
                     help="serving4: requests the plain per-request form serves back to back")
     ap.add_argument("--no-sublines", action="store_true",
@@ -1223,7 +1225,8 @@ def run_serving4(args):
     window = max(d["arrival"] for d in descs) - min(d["arrival"] for d in descs)
     total = sum(d["nsteps"] for d in descs)
     reqs = serve.make_requests(copy.deepcopy(descs))
-    srv = serve.Server(mix=args.mix)
+    policy, _, cap = args.serve_policy.partition(":")
+    srv = serve.Server(mix=args.mix, policy=policy, max_active=int(cap) if cap else 1 << 20)
     st = srv.run(reqs).summary()
     srv.close()
     idx = np.unique(np.linspace(0, len(descs) - 1, min(args.plain_sample, len(descs))).astype(int))
@@ -1234,7 +1237,8 @@ def run_serving4(args):
     sp = serve.run_plain(pr, mix=args.mix).summary()
     same = all(np.array_equal(reqs[i].q, p_.q) and np.array_equal(reqs[i].v, p_.v)
                and np.array_equal(reqs[i].iters, p_.iters) for i, p_ in zip(idx, pr))
-    block = {"requests": len(descs), "rate_per_s": rate, "arrival_window_s": window, "traj_steps": total,
+    block = {"requests": len(descs), "rate_per_s": rate, "policy": args.serve_policy,
+             "arrival_window_s": window, "traj_steps": total,
              "offered_traj_steps_s": total / max(window, 1e-9), "continuous_batching": st,
              "fp64_roof_frac": st["flops_per_s"] / (peak * 1e12),
              "status_nonzero": int(sum(int((r.status != 0).sum()) for r in reqs)),
