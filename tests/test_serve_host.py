@@ -80,3 +80,23 @@ def test_serving_requests_cover_the_stated_ranges():
     assert min(nb) >= 3 and max(nb) <= 64
     for d in descs:
         ragged.bucket_label(serve.KIND_IDS[d["kind"]], d["dim"])  # every request has a pool
+
+
+def test_config4_requests_are_the_ragged_batch():
+    """The config-4 serving load: one batch-1 request per instance of the
+    ragged batch, with that instance's kind, size, parameters, state, step
+    and horizon; Poisson arrivals increasing; the same bits on every call."""
+    w = workloads.uneven_batch(ninst=12, steps=50)
+    reqs = workloads.config4_requests(ninst=12, steps=50)
+    again = workloads.config4_requests(ninst=12, steps=50)
+    arr = np.array([r["arrival"] for r in reqs])
+    assert (np.diff(arr) > 0).all() and arr[0] > 0
+    for k, r in enumerate(reqs):
+        o, d = int(w["offset"][k]), int(w["dim"][k])
+        po, pn = int(w["param_offset"][k]), int(w["nparams"][k])
+        assert r["kind"] == {2: "nbody", 3: "fput"}[int(w["kind"][k])] and r["dim"] == d
+        assert np.array_equal(r["q0"], w["q0"][o:o + d][None, :]) and r["q0"].shape == (1, d)
+        assert np.array_equal(r["v0"], w["v0"][o:o + d][None, :])
+        assert r["params"] == list(w["params"][po:po + pn])
+        assert r["h"] == w["h"][k] and r["nsteps"] == 50 and r["rid"] == k
+        assert r["arrival"] == again[k]["arrival"] and np.array_equal(r["q0"], again[k]["q0"])
