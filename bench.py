@@ -121,6 +121,8 @@ def parse():
                     help="--workload serving: comma-separated Poisson arrival rates per second")
     ap.add_argument("--sweep-cases", default="",
                     help="--workload sweeps: comma-separated case-name prefixes to run (default all)")
+    ap.add_argument("--serve-tick", type=float, default=0.03,
+                    help="serving, serving4: wanted duration of a serving tick in seconds")
     ap.add_argument("--serve-policy", default="fifo",
                     help="serving4: fifo, or sjf:N (shortest job first, at most N requests active)")
     ap.add_argument("--plain-sample", type=int, default=32,
@@ -503,7 +505,7 @@ SERVE_DIST = ("config-5 distribution: families Kepler ensemble, 6-body ensemble,
               "logU[1e2,1e5] steps")
 
 
-def serving_window(serve, workloads, n, rate, mix, peak_tflops, plain=True):
+def serving_window(serve, workloads, n, rate, mix, peak_tflops, plain=True, tick_s=0.03):
     """The first `n` Poisson arrivals at `rate` per second from the config-5
     distribution, served to completion by the continuous-batching loop (and
     by the plain per-request form): p50 / p99 latency, served and offered
@@ -514,7 +516,7 @@ def serving_window(serve, workloads, n, rate, mix, peak_tflops, plain=True):
     window = max(d["arrival"] for d in descs) - min(d["arrival"] for d in descs)
     offered = sum(d["q0"].shape[0] * d["nsteps"] for d in descs) / max(window, 1e-9)
     reqs = serve.make_requests(copy.deepcopy(descs))
-    srv = serve.Server(mix=mix)
+    srv = serve.Server(mix=mix, target_tick_s=tick_s)
     st = srv.run(reqs).summary()
     srv.close()
     out = {"requests": n, "rate_per_s": rate, "arrival_window_s": window,
@@ -1184,7 +1186,7 @@ def run_serving_sweep(args):
     rows = []
     for rate in (float(x) for x in args.serve_rates.split(",")):
         rows.append(serving_window(serve, workloads, args.serve_requests, rate, args.mix, peak,
-                                   plain=False))
+                                   plain=False, tick_s=args.serve_tick))
     top = rows[-1]["continuous_batching"]
     line = {
         "metric": METRIC, "value": top["throughput_traj_steps_s"], "unit": "traj-steps/s", "n_gpus": 1,
@@ -1226,7 +1228,8 @@ def run_serving4(args):
     total = sum(d["nsteps"] for d in descs)
     reqs = serve.make_requests(copy.deepcopy(descs))
     policy, _, cap = args.serve_policy.partition(":")
-    srv = serve.Server(mix=args.mix, policy=policy, max_active=int(cap) if cap else 1 << 20)
+    srv = serve.Server(mix=args.mix, policy=policy, max_active=int(cap) if cap else 1 << 20,
+                       target_tick_s=args.serve_tick)
     st = srv.run(reqs).summary()
     srv.close()
     idx = np.unique(np.linspace(0, len(descs) - 1, min(args.plain_sample, len(descs))).astype(int))

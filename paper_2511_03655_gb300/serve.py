@@ -606,7 +606,7 @@ class Server:
     previous tick."""
 
     def __init__(self, pool_bytes: int = 1 << 30, max_active: int = 1 << 20, device=None,
-                 policy: str = "fifo", mix: int = 1, target_tick_s: float = 0.01):
+                 policy: str = "fifo", mix: int = 1, target_tick_s: float = 0.03):
         if policy not in ("fifo", "sjf"):
             raise ValueError(policy)
         self.policy = policy
