@@ -150,6 +150,30 @@ def test_kepler_single_full_run(torch_cuda):
     integ.close()
 
 
+@pytest.mark.parametrize("mix", [0, 1, 2])
+def test_kepler_single_against_the_closed_form(torch_cuda, mix):
+    """Config 1 against Kepler's closed form (Kepler's equation solved in
+    high precision, tests/closed_forms.py): after 100 periods the exact orbit
+    is back at periapsis.  The oracle ends 1.9e-12 (q) and 4.4e-12 (v) from
+    it, roundoff accumulated linearly over 20,000 steps; each stage mixing
+    must end within 1e-11."""
+    import math
+
+    from paper_2511_03655_gb300 import irkgl
+    from tests import closed_forms
+    torch = torch_cuda
+    w = workloads.kepler_single()
+    integ = irkgl.Integrator(irkgl.RHS_KEPLER, [1.0], 2, float(w["h"][0]), mix=mix)
+    out = integ.integrate(dev(torch, w["q0"]), dev(torch, w["v0"]), nsteps_all=20000)
+    torch.cuda.synchronize()
+    qe, ve = closed_forms.kepler_state(0.5, 20000 * float(w["h"][0]))
+    assert abs(20000 * float(w["h"][0]) - 100 * 2 * math.pi) < 1e-10
+    assert np.abs(out.q.cpu().numpy()[0] - np.array([float(x) for x in qe])).max() <= 1e-11
+    assert np.abs(out.v.cpu().numpy()[0] - np.array([float(x) for x in ve])).max() <= 1e-11
+    assert out.status.item() == 0 and out.dH_max.item() <= 1e-13
+    integ.close()
+
+
 @pytest.mark.parametrize("lpt", [1, 2, 8])
 def test_kepler_ensemble_slice(torch_cuda, lpt):
     """2,048 orbits of the ensemble (e in [0, 0.9)), two periods each, one
